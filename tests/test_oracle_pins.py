@@ -1,0 +1,410 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: a closed form, an
+independent algebraic route (the Casida sum over poles), an exact discrete identity, a
+printed parameter set, or brute force. Citations name the paper's sections/equation labels.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gwc_oracle as G
+from oracle import sop as S
+from paper_2412_17132_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EV = synth.HARTREE_EV
+
+
+# ----------------------------------------------------------------------------------------
+# Imaginary-axis grid (Sec. "Computational Details": modified Gauss-Legendre grid)
+# ----------------------------------------------------------------------------------------
+
+
+def test_gl_grid_is_exact_for_lorentzian_kernel():
+    # int_0^inf dxi a/(a^2+xi^2) = pi/2 sgn(a); with xi0 = a the mapped integrand is 1/(1+x^2) on (-1,1)
+    xi, w = G.modified_gl_grid(32, 1.0)
+    assert abs(np.sum(w / (1.0 + xi**2)) - math.pi / 2) < 1e-14
+    xi, w = G.modified_gl_grid(200, 1.0)
+    for a in (0.05, 0.7, 3.0, 11.0):
+        assert abs(np.sum(w * a / (a * a + xi**2)) - math.pi / 2) < 2e-4
+
+
+# ----------------------------------------------------------------------------------------
+# P1: chi0 on the imaginary axis is real symmetric negative semidefinite; ||Pi(i0)|| = 2
+# ----------------------------------------------------------------------------------------
+
+
+def test_chi0_imaginary_axis_nsd(tiny_mol):
+    s = G.System.from_molecule(tiny_mol)
+    for xi in (0.0, 0.1, 1.0, 7.5, 40.0):
+        pi = G.chi0(s.o_ov, s.delta, 1j * xi)
+        assert np.all(pi.imag == 0.0)
+        p = pi.real
+        assert np.max(np.abs(p - p.T)) <= 1e-15 * np.max(np.abs(p))
+        ev = np.linalg.eigvalsh(p)
+        assert ev[-1] <= 1e-12 * np.max(np.abs(ev))
+    n0 = np.linalg.eigvalsh(-G.chi0(s.o_ov, s.delta, 0.0).real)[-1]
+    assert abs(n0 - 2.0) < 1e-12
+
+
+def test_chi0_brute_force_sum_over_pairs():
+    # Pi_PQ(z) as the literal double loop over occupied i and virtual a with D = 2[1/(z-D)-1/(z+D)]
+    m = synth.small(n_states=9, n_occ=3, n_aux=5, seed=11)
+    s = G.System.from_molecule(m)
+    z = 1.3 + 0.02j
+    pi = G.chi0(s.o_ov, s.delta, z)
+    ref = np.zeros((5, 5), dtype=complex)
+    n_v = m.n_states - m.n_occ
+    for i in range(m.n_occ):
+        for a in range(n_v):
+            dl = m.eps[m.n_occ + a] - m.eps[i]
+            d = 2.0 / (z - dl) - 2.0 / (z + dl)
+            col = m.o_ov[:, i * n_v + a]
+            ref += d * np.outer(col, col)
+    assert np.max(np.abs(pi - ref)) < 1e-14
+
+
+# ----------------------------------------------------------------------------------------
+# P2: contour deformation == sum over poles (Eqs. rpa_casida, density_shifts, W_spectral,
+# sigma_spectral vs Eqs. cd_terms, cd_imaginary, cd_residue)
+# ----------------------------------------------------------------------------------------
+
+
+@pytest.fixture(scope="module")
+def small_sop():
+    m = synth.small(n_states=16, n_occ=4, n_core=1, n_aux=12, seed=5, n_high=2)
+    s = G.System.from_molecule(m, n_im=32)
+    om, xpy = S.casida_sop(s.o_ov, s.delta)
+    rho = np.array([S.transition_moments(s.o_ov, xpy, s.o_core[mm, 0]) for mm in range(m.n_states)])
+    return m, s, om, xpy, rho
+
+
+def test_casida_energies_match_ri_form(small_sop):
+    # Omega^2 = eig(Delta^2 + 4 Delta^1/2 K Delta^1/2): the symmetric reduction of the Casida problem
+    m, s, om, _, _ = small_sop
+    k = s.o_ov.T @ s.o_ov
+    sq = np.sqrt(s.delta)
+    c = np.diag(s.delta**2) + 4.0 * sq[:, None] * k * sq[None, :]
+    ref = np.sqrt(np.linalg.eigvalsh(c))
+    assert np.max(np.abs(np.sort(om) - ref)) < 1e-10 * ref.max()
+
+
+@pytest.mark.parametrize("z", [0.37 + 0.01j, 2.5 + 1e-3j, 10.2 + 1e-3j, 0.7j, 15.0j, 0.0])
+def test_w_ri_solve_equals_sum_over_poles(small_sop, z):
+    m, s, om, _, rho = small_sop
+    pi = G.chi0(s.o_ov, s.delta, z)
+    w_ri = G.screened_wc(pi, s.o_core[:, 0, :].T)
+    w_sp = np.array([S.w_sop(rho[mm], om, z) for mm in range(m.n_states)])
+    assert np.max(np.abs(w_ri - w_sp)) <= 1e-10 * max(1e-3, np.max(np.abs(w_sp)))
+
+
+def test_w_ri_equals_sop_on_tiny(tiny_mol):
+    s = G.System.from_molecule(tiny_mol)
+    om, xpy = S.casida_sop(s.o_ov, s.delta)
+    for mm in (0, 3, 7, 30, 59):
+        rho = S.transition_moments(s.o_ov, xpy, s.o_core[mm, 0])
+        for z in (0.2 + 1e-3j, 9.9 + 1e-3j, 1.5j):
+            w_ri = G.screened_wc(G.chi0(s.o_ov, s.delta, z), s.o_core[mm, 0][:, None])[0]
+            w_sp = S.w_sop(rho, om, z)
+            assert abs(w_ri - w_sp) <= 1e-9 * max(1e-4, abs(w_sp))
+
+
+def test_sigma_cd_converges_to_closed_form(small_sop):
+    # CD with quadrature vs the same CD expression with the exact imaginary-axis integral:
+    # the only difference is quadrature error, which must shrink with more nodes.
+    m, _, om, _, rho = small_sop
+    eps_f = G.fermi_level(m.eps, m.n_occ)
+    ws = [m.eps[0] - 0.9, m.eps[0] - 0.31, m.eps[0] + 0.05, m.eps[0]]
+    errs = {}
+    for n_im in (32, 200, 800):
+        s = G.System.from_molecule(m, n_im=n_im)
+        e = 0.0
+        for w in ws:
+            cd = s.sigma_c(float(w))[0][0]
+            ref = S.sigma_c_cd_closed_form(m.eps, eps_f, rho, om, float(w), m.eta)
+            e = max(e, abs(cd - ref))
+        errs[n_im] = e
+    assert errs[800] < errs[32]
+    assert errs[800] < 1e-6
+    assert errs[200] < 1e-4
+
+
+def test_sigma_cd_matches_time_ordered_sop(small_sop):
+    # Eq. sigma_spectral (time-ordered +-i eta per pole) vs CD: differ by the anti-resonant eta
+    # placement, bounded by sum rho^2 eta/(x+Omega)^2, plus quadrature error.
+    m, _, om, _, rho = small_sop
+    s = G.System.from_molecule(m, n_im=800)
+    eps_f = s.eps_f
+    for w in (m.eps[0] - 0.9, m.eps[0] - 0.31, m.eps[0] + 0.05):
+        cd = s.sigma_c(float(w))[0][0]
+        sp = S.sigma_c_sop(m.eps, eps_f, rho, om, float(w), m.eta)
+        bound = sum(np.sum(rho[mm] ** 2 * 2 * m.eta / (abs(m.eps[mm] - w) + om) ** 2) for mm in range(m.n_states))
+        assert abs(cd - sp) <= bound + 1e-6
+
+
+def test_im_sigma_only_from_residues(tiny_mol):
+    # Eq. cd_sigma_imaginary: I_n is real, so Im Sigma^c = Im R_n
+    s = G.System.from_molecule(tiny_mol)
+    w = float(tiny_mol.omega[123])
+    sig, _ = s.sigma_c(w)
+    r, _ = s.residue_term(w)
+    assert np.all(np.isreal(s.imag_axis_term(w)))
+    assert abs(sig[0].imag - r[0].imag) == 0.0
+
+
+def test_sigma_continuous_at_residue_threshold(small_sop):
+    # Theta(0) = 1/2 makes Sigma^c continuous at w = eps_m (both one-sided limits agree)
+    m, s, _, _, _ = small_sop
+    e = float(m.eps[2])
+    lo = s.sigma_c(e - 1e-9)[0][0]
+    mid = s.sigma_c(e)[0][0]
+    hi = s.sigma_c(e + 1e-9)[0][0]
+    assert abs(lo - mid) < 1e-6 and abs(hi - mid) < 1e-6
+
+
+# ----------------------------------------------------------------------------------------
+# P4: the G_dH W0 QP solution is eps_n + dH_n (Eqs. hedin_shift, hedin_sigma_spectral, QPGWC)
+# ----------------------------------------------------------------------------------------
+
+
+def test_qp_lands_on_hedin_closed_form(tiny_mol):
+    s = G.System.from_molecule(tiny_mol)
+    eqp, dh, it = s.qp_solve()
+    assert abs(eqp[0] - (tiny_mol.eps[0] + dh[0])) * EV < 1e-3
+    assert it[0] < 50
+
+
+def test_qp_closed_form_small_multi_core():
+    m = synth.small(n_states=20, n_occ=5, n_core=2, n_aux=14, seed=9)
+    s = G.System.from_molecule(m, n_im=16, vxc=np.array([-0.3, -0.25]))
+    eqp, dh, _ = s.qp_solve()
+    sx = s.sigma_x()
+    for c in range(2):
+        assert abs(eqp[c] - (m.eps[c] + dh[c])) * EV < 1e-3
+        # dH contains the static part Sigma^x - v^xc
+        assert abs(dh[c] - (s.sigma_c_core(c, float(m.eps[c])).real + sx[c] - s.vxc[c])) < 1e-12
+
+
+# ----------------------------------------------------------------------------------------
+# P3/P5/P6: cumulant spectrum (Eqs. landau_cumulant_truncated, cumulant_propagator_fourier,
+# eq:AGWC; Poisson satellites of the minimal model)
+# ----------------------------------------------------------------------------------------
+
+
+def _single_pole_beta(n_w, omega_sat, mass):
+    w = np.linspace(-1.2, 0.2, n_w)
+    j = int(np.argmin(np.abs(w - (-omega_sat))))
+    w = w - (w[j] + omega_sat)  # put node j exactly at -Omega
+    wq = G.trapezoid_weights(w)
+    im = np.zeros(n_w)
+    im[j] = math.pi * mass / wq[j]
+    return w, im
+
+
+def test_cumulant_single_pole_is_exact():
+    om = 0.5
+    w, im = _single_pole_beta(301, om, 0.02)
+    t = np.linspace(0, 300, 1001)
+    ct = G.cumulant_ct(w, np.abs(im) / math.pi, t)
+    gam = 0.02 / om**2
+    ref = gam * (np.exp(1j * om * t) - 1.0)
+    assert np.max(np.abs(ct - ref)) < 1e-13
+
+
+def _poisson_closed_form(gam, om, eta, n, dt, qmax=60):
+    # X_j = dt e^{-gam} sum_q gam^q/q! [sum_k r_q^k - 1/2], r_q = exp((i(nu_j + q Om) - eta) dt)
+    k = np.arange(n)
+    nu = 2 * math.pi * np.where(k < n // 2, k, k - n) / (n * dt)
+    x = np.zeros(n, dtype=complex)
+    for q in range(qmax):
+        r = np.exp((1j * (nu + q * om) - eta) * dt)
+        geo = (1.0 - r**n) / (1.0 - r) - 0.5
+        x += gam**q / math.factorial(q) * geo
+    x *= dt * math.exp(-gam)
+    order = np.argsort(nu, kind="stable")
+    return nu[order], x.real[order] / math.pi
+
+
+@pytest.mark.parametrize("ratio", json.load(open(os.path.join(GOLDEN, "model_ratios.json")))["rho_over_omega"])
+def test_spectrum_poisson_closed_form(ratio):
+    om, eta, n, t_max = 0.5, 1e-3, 1 << 14, 2000.0
+    gam = ratio**2
+    w, im = _single_pole_beta(401, om, gam * om**2)
+    nu, a = G.gwc_spectrum(w, im, eta, n, t_max)
+    nu2, ref = _poisson_closed_form(gam, om, eta, n, t_max / n)
+    assert np.max(np.abs(nu - nu2)) == 0.0
+    assert np.max(np.abs(a - ref)) < 1e-9 * np.max(ref)
+
+
+def test_spectrum_fft_equals_direct_dft():
+    w, im = _single_pole_beta(101, 0.3, 0.01)
+    nu, a = G.gwc_spectrum(w, im, 2e-3, 256, 300.0)
+    nu2, a2 = G.gwc_spectrum(w, im, 2e-3, 256, 300.0, direct=True)
+    assert np.max(np.abs(a - a2)) < 1e-12 * np.max(np.abs(a))
+
+
+def test_sum_rule_is_one():
+    # sum_j A_j dnu = Re e^{C~(0)} = 1 for any beta (discrete identity of the transform)
+    rng = np.random.default_rng(4)
+    w = np.linspace(-1.0, 0.2, 300)
+    im = np.where(w < 0, rng.uniform(0, 0.05, w.size), 0.0)
+    for n, t_max in ((4096, 500.0), (1 << 16, 2000.0)):
+        nu, a = G.gwc_spectrum(w, im, 1e-3, n, t_max)
+        assert abs(np.sum(a) * (nu[1] - nu[0]) - 1.0) < 1e-10
+
+
+def test_poisson_positions_and_weights_ch4():
+    # Table 1 CH4 cc-pVTZ: Omega = 13.91 eV, rho = 0.3352 eV -> gamma = (rho/Omega)^2 = 5.8e-4 (weak
+    # coupling); satellites at eps^QP - k Omega with weights e^-g g^k/k! (minimal-model discussion)
+    row = json.load(open(os.path.join(GOLDEN, "ch4_table1.json")))["rows"][0]
+    om = row["Omega_sat1_eV"] / EV
+    gam = (row["rho_c1s_c1s_eV"] / row["Omega_sat1_eV"]) ** 2
+    assert abs(gam - 5.807e-4) < 1e-6
+    eta, n, t_max = 1e-3, 1 << 19, 32000.0  # dnu = eta/5
+    w, im = _single_pole_beta(801, om, gam * om**2)
+    nu, a = G.gwc_spectrum(w, im, eta, n, t_max)
+    peaks = G.find_peaks(nu, a, rel_threshold=1e-5)
+    pos = sorted(p for p, _ in peaks)
+    assert abs(pos[-1]) * EV < 0.01  # QP peak at eps^QP
+    assert abs(pos[-2] + om) * EV < 0.01  # first satellite at eps^QP - Omega
+    dnu = nu[1] - nu[0]
+    for k in (0, 1):
+        lo, hi = -k * om - 0.1, -k * om + 0.1
+        win = (nu > lo) & (nu < hi)
+        area = np.sum(a[win]) * dnu
+        # mass of the Poisson series of Lorentzians (width eta) centred at -q Omega inside the window
+        ref = sum(
+            math.exp(-gam) * gam**q / math.factorial(q) * (math.atan((hi + q * om) / eta) - math.atan((lo + q * om) / eta)) / math.pi
+            for q in range(6)
+        )
+        assert abs(area - ref) < 2e-3 * gam**k
+
+
+# ----------------------------------------------------------------------------------------
+# P8: three-level core-hole model (Sec. minimal model; Cederbaum et al.)
+# ----------------------------------------------------------------------------------------
+
+
+def three_level(omega, rho, eps_c=-10.0, eps_o=-0.5, eta=1e-3):
+    dl = 0.9 * omega  # bare valence excitation eps_v - eps_o
+    kappa = math.sqrt((omega**2 - dl**2) / (4 * dl))
+    rt = math.sqrt(rho**2 * omega / (2 * kappa**2 * dl))
+    eps = np.array([eps_c, eps_o, eps_o + dl])
+    o_ov = np.array([[0.0, kappa]])  # (c,v) omitted (CVS), (o,v) = kappa
+    o_core = np.array([[[rt]], [[0.0]], [[0.0]]])
+    return G.System(eps, 2, [0], o_ov, o_core, eta, n_im=200), dl, kappa, rt
+
+
+@pytest.mark.parametrize("ratio", [0.05, 0.5, 1.0])
+def test_three_level_w_closed_form(ratio):
+    om = 0.5
+    s, dl, kappa, rt = three_level(om, ratio * om)
+    big = math.sqrt(dl**2 + 4 * dl * kappa**2)
+    assert abs(big - om) < 1e-14
+    for z in (0.2 + 1e-3j, 0.5 + 1e-3j, 1.3j):
+        w = G.screened_wc(G.chi0(s.o_ov, s.delta, z), s.o_core[0, 0][:, None])[0]
+        ref = (ratio * om) ** 2 * 2 * om / (z * z - om * om)
+        assert abs(w - ref) < 1e-12 * max(1.0, abs(ref))
+
+
+def test_three_level_spectrum_is_poisson():
+    om, ratio, eta = 0.5, 0.5, 1e-3
+    s, _, _, _ = three_level(om, ratio * om, eta=eta)
+    ec = float(s.eps[0])
+    w_abs = np.linspace(ec - 1.0, ec + 0.1, 2201)
+    dec = np.array([s.sigma_c(float(w))[1][0] for w in w_abs])
+    eqp, dh, _ = s.qp_solve()
+    nu, a = G.gwc_spectrum(w_abs - ec, dec, eta, 1 << 18, 25000.0)
+    peaks = sorted(G.find_peaks(nu, a, rel_threshold=1e-4))
+    pos = [p for p, _ in peaks]
+    # QP peak at 0 (relative to eps^QP), satellites at -k Omega, k = 1, 2, 3
+    for k in range(4):
+        assert min(abs(p + k * om) for p in pos) * EV < 0.01
+    # cumulant weight gamma = rho^2/Omega^2 (Lorentzian-broadened pole carries ~all the mass)
+    beta = np.abs(dec) / math.pi
+    wr = w_abs - ec
+    wq = G.trapezoid_weights(wr)
+    keep = wr != 0
+    gam_num = np.sum((wq * beta)[keep] / wr[keep] ** 2)
+    # closed-form Im W^c of the model on the same grid: rho^2 Im[2 Omega/((x + i eta)^2 - Omega^2)], x = -w
+    x = -wr
+    im_ref = np.where(x > 0, (ratio * om) ** 2 * (2 * om / ((x + 1j * eta) ** 2 - om**2)).imag, 0.0)
+    gam_ref = np.sum((wq * np.abs(im_ref) / math.pi)[keep] / wr[keep] ** 2)
+    assert abs(gam_num - gam_ref) < 1e-9 * gam_ref
+    # and gamma -> rho^2/Omega^2 up to the finite-eta Lorentzian tails (relative O(eta/Omega log))
+    assert abs(gam_num - ratio**2) < 0.03 * ratio**2
+    assert abs(eqp[0] - (ec + dh[0])) * EV < 1e-3
+
+
+# ----------------------------------------------------------------------------------------
+# P7: first-order approximation (Eq. im_sigma_satellites) for weak, smooth coupling
+# ----------------------------------------------------------------------------------------
+
+
+def test_first_order_satellite_shape():
+    # The quadrature grid must resolve the damping (d omega << eta), otherwise e^{C~} is a comb of
+    # separate grid lines; here d omega = eta/10.
+    eta = 1e-2
+    w = np.linspace(-3.0, 0.0, 3001)
+    gam_target = 2e-3
+    beta = np.exp(-((w + 1.2) ** 2) / (2 * 0.25**2))
+    wq = G.trapezoid_weights(w)
+    keep = w != 0
+    beta *= gam_target / np.sum((wq * beta)[keep] / w[keep] ** 2)
+    nu, a = G.gwc_spectrum(w, math.pi * beta, eta, 1 << 15, 2500.0)  # e^{-eta t_max} negligible
+    z = math.exp(-gam_target)
+    sel = (nu > -2.0) & (nu < -0.6)
+    # Z [delta(nu) + beta(nu)/nu^2], the delta broadened into the damping Lorentzian of width eta
+    approx = z * (eta / math.pi / (nu[sel] ** 2 + eta**2) + np.interp(nu[sel], w, beta) / nu[sel] ** 2)
+    # residual: second order (gamma) and the eta-Lorentzian smoothing of beta, ~1% here
+    assert np.max(np.abs(a[sel] - approx)) < 0.015 * np.max(approx)
+
+
+# ----------------------------------------------------------------------------------------
+# P9: decoupling (Eqs. sigma_spectral_decoupled, cd_sigma_imaginary_decoupled)
+# ----------------------------------------------------------------------------------------
+
+
+def test_decoupling_exact_without_off_diagonal_moments():
+    m = synth.small(n_states=18, n_occ=4, n_core=1, n_aux=10, seed=21)
+    o_core = m.o_core.copy()
+    o_core[1:, 0, :] = 0.0  # O^P_{m,c} = 0 for m != c
+    s = G.System(m.eps, m.n_occ, m.core_idx, m.o_ov, o_core, m.eta, n_im=16)
+    for w in np.linspace(m.eps[0] - 0.9, m.eps[0] + 0.1, 7):
+        sig, dec = s.sigma_c(float(w))
+        assert abs(sig[0].imag - dec[0]) <= 1e-15 * max(1.0, abs(dec[0]))
+
+
+def test_correlation_satellites_appear_with_high_virtuals(tiny_mol):
+    # with the 3-40 Ha virtuals the full Im Sigma carries structure the decoupled one lacks
+    s = G.System.from_molecule(tiny_mol)
+    ws = tiny_mol.omega[::20]
+    full = np.array([s.sigma_c(float(w))[0][0].imag for w in ws])
+    dec = np.array([s.sigma_c(float(w))[1][0] for w in ws])
+    assert np.max(np.abs(full - dec)) > 1e-6
+
+
+# ----------------------------------------------------------------------------------------
+# Exchange (Eq. sigma_x): brute force over (n i | i n) with (mn|kl) = sum_P O^P_mn O^P_kl
+# ----------------------------------------------------------------------------------------
+
+
+def test_sigma_x_brute_force():
+    m = synth.small(n_states=10, n_occ=4, n_core=2, n_aux=6, seed=2)
+    s = G.System.from_molecule(m)
+    for c in range(2):
+        ref = 0.0
+        for i in range(m.n_occ):
+            ref -= sum(m.o_core[i, c, p] * m.o_core[i, c, p] for p in range(6))
+        assert abs(s.sigma_x()[c] - ref) < 1e-14 * abs(ref)
+
+
+def test_peak_finder_on_parabola():
+    nu = np.linspace(-1, 1, 201)
+    a = 1.0 - (nu - 0.0123) ** 2
+    (p, h), = G.find_peaks(nu, a)
+    assert abs(p - 0.0123) < 1e-12 and abs(h - 1.0) < 1e-12
