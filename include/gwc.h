@@ -1,0 +1,198 @@
+/*
+ * gwc.h -- C ABI of libgwc: the real-frequency correlation self-energy of molecular
+ * 1s core states by contour deformation on an RI basis, the quasiparticle fixed point
+ * and the retarded-cumulant spectral function (GW+C), on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2412.17132, "GW plus cumulant approach for predicting core-level
+ * shake-up satellites in large molecules". Equation labels below are the paper's
+ * LaTeX labels (the paper does not number its equations).
+ *
+ * Conventions for every entry point
+ *   - Units: Hartree atomic units (energies in Ha, times in hbar/Ha).
+ *   - Arrays are row-major, float64 unless stated. "DEVICE" pointers are CUDA device
+ *     memory of the current device; "HOST" pointers are host memory (pinned or pageable).
+ *   - Ownership: the library never frees caller memory. A gwc_ctx copies what it keeps
+ *     resident (orbital energies, RI coefficients and their precision-split copies) and
+ *     owns its workspace; gwc_destroy releases both.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls enqueue work on that stream and return without synchronising, except where a
+ *     function says it synchronises.
+ *   - Errors: every function returns a gwc_status; no exception or abort crosses the ABI.
+ *     Invalid sizes and NULL pointers are rejected before any launch (GWC_ERR_INVALID_ARG).
+ *     Device-side conditions (a zero pivot, an exhausted bounded wait, a QP that did not
+ *     converge) are recorded in a device status word and reported by gwc_sync.
+ *     gwc_last_error returns a message for the last failing call on that context.
+ *   - Threading: a gwc_ctx is used by one host thread at a time.
+ */
+#ifndef GWC_H
+#define GWC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GWC_ABI_VERSION 1
+
+typedef enum {
+  GWC_OK = 0,
+  GWC_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, inconsistent options          */
+  GWC_ERR_OOM = 2,           /* device or pinned host allocation failed               */
+  GWC_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed           */
+  GWC_ERR_SINGULAR = 4,      /* zero pivot in the dielectric factorisation            */
+  GWC_ERR_NOT_CONVERGED = 5, /* QP secant iteration hit max_qp_iter                   */
+  GWC_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                    */
+  GWC_ERR_UNSUPPORTED = 7    /* precision/feature not available on this device        */
+} gwc_status;
+
+/* Arithmetic of the polarizability build chi0 and of the dielectric factorisation.
+ * All modes keep the self-energy assembly, the QP iteration and the cumulant in FP64.
+ *   FP64   : chi0 FP64 (SIMT), factorisation and solves FP64           (plain FP64 path)
+ *   FP32   : chi0 FP32 (SIMT), factorisation and solves FP32
+ *   BF16   : chi0 on tcgen05 tensor cores, BF16 operands, FP32 accumulate; factor FP32
+ *   BF16X3 : chi0 on tcgen05, split-BF16 operands (hi*hi + hi*lo + lo*hi), FP32
+ *            accumulate; factor FP32                                      (mixed path)   */
+typedef enum { GWC_PREC_FP64 = 0, GWC_PREC_BF16 = 1, GWC_PREC_BF16X3 = 2, GWC_PREC_FP32 = 3 } gwc_precision;
+
+/* Form of Im Sigma handed to the cumulant (Sec. "Core-valence decoupling", Eqs.
+ * sigma_spectral_decoupled, sigma_spectral_decoupled_symmetric, cd_sigma_imaginary_decoupled):
+ *   NONE : full Im Sigma^c (all residue states m)
+ *   DIAG : f_n Im W^c_nn(|eps_n - w| + i eta)
+ *   GROUP: sum over the symmetry group of n of f_i Im W^c_ni(|eps_i - w| + i eta)          */
+typedef enum { GWC_DECOUPLE_NONE = 0, GWC_DECOUPLE_DIAG = 1, GWC_DECOUPLE_GROUP = 2 } gwc_decouple;
+
+typedef enum { GWC_MEM_DEVICE = 0, GWC_MEM_HOST = 1 } gwc_memory;
+
+/* One molecule. Sizes: n_virt = n_states - n_occ, n_ov = n_occ * n_virt.
+ * The RI coefficients are the symmetrised three-centre integrals O^P_mn (the Coulomb
+ * metric already applied), so that (mn|kl) = sum_P O^P_mn O^P_kl.                          */
+typedef struct {
+  int n_states;          /* number of orbitals, >= 2                                          */
+  int n_occ;             /* occupied orbitals are 0..n_occ-1, 1 <= n_occ < n_states            */
+  int n_aux;             /* auxiliary (RI) basis size, >= 1                                    */
+  int n_core;            /* number of core states whose self-energy is computed, >= 1          */
+  const int* core_idx;   /* HOST [n_core]: orbital index of each core state, each < n_occ      */
+  const double* eps;     /* [n_states] orbital energies, ascending                            */
+  const double* o_ov;    /* [n_aux][n_ov]: O^P_ia, column (i, a) = i * n_virt + (a - n_occ)    */
+  const double* o_core;  /* [n_states][n_core][n_aux]: O^P_{m, core_idx[c]} for every m       */
+  const double* vxc;     /* [n_core] <psi_n|v^xc|psi_n>, or NULL: v^xc_n := Sigma^x_n          */
+  double eps_f;          /* Fermi level; NaN: midpoint of HOMO and LUMO                        */
+  int memory;            /* gwc_memory: where eps, o_ov, o_core and vxc live                  */
+} gwc_system;
+
+typedef struct {
+  double eta;            /* broadening (Ha) of residues and of the spectrum damping, > 0      */
+  int n_im;              /* imaginary-axis Gauss-Legendre nodes, 1..1024                       */
+  double xi0;            /* scale of the map xi = xi0 (1+x)/(1-x), > 0                         */
+  int prec;              /* gwc_precision                                                      */
+  int dec;               /* gwc_decouple, form of im_sigma_dec in gwc_sigma_core               */
+  const int* group_of_core; /* HOST [n_core] group label per core (GROUP mode), or NULL       */
+  int n_t;               /* cumulant time points, a power of two, 16..2^22                    */
+  double t_max;          /* cumulant time window, > 0                                          */
+  int max_qp_iter;       /* secant iterations, 2..200                                          */
+  double qp_tol;         /* secant tolerance on the QP residual (Ha), > 0                     */
+  int batch;             /* frequencies per internal batch (0: chosen from free memory)       */
+} gwc_options;
+
+typedef struct {
+  long long chi0_builds;     /* polarizability builds launched (one per frequency)            */
+  double chi0_flop;          /* algorithmic chi0 flop: lower triangle, N_aux(N_aux+1) N_ov per part */
+  long long kernel_launches; /* library kernels launched since gwc_create / gwc_reset_stats     */
+  long long factorizations;  /* dielectric factorisations launched                              */
+} gwc_stats;
+
+typedef struct gwc_ctx gwc_ctx;
+
+/* Fills o with the defaults: eta 1e-3, n_im 32, xi0 1, BF16X3, DIAG, n_t 2^16, t_max 2000,
+ * max_qp_iter 50, qp_tol 1e-7, batch 0. */
+gwc_status gwc_default_options(gwc_options* o);
+
+/* Device bytes a context of this shape allocates (resident copies + workspace + the
+ * per-grid tables for n_omega real frequencies). Host-only; launches nothing. */
+gwc_status gwc_workspace_bytes(const gwc_system* sys, const gwc_options* opt, int n_omega, size_t* bytes);
+
+/* Creates a context on the current device: validates, allocates, copies the system
+ * (host->device if memory == GWC_MEM_HOST), builds the resident precision copies of
+ * O_ov (BF16 hi/lo and FP32), and computes the imaginary-axis grid. Enqueued on
+ * `stream`; gwc_create synchronises that stream once before returning. */
+gwc_status gwc_create(gwc_ctx** ctx, const gwc_system* sys, const gwc_options* opt, void* stream);
+
+/* Replaces the system of an existing context by another of the SAME sizes (serving
+ * slots); no allocation. Synchronises `stream` once. */
+gwc_status gwc_load(gwc_ctx* ctx, const gwc_system* sys, void* stream);
+
+/* RI polarizability (Sec. "Self-energy evaluation"; RI form of Ren et al. 2012, which the
+ * paper's CD uses): Pi_PQ(z_f) = sum_ia O^P_ia D_ia(z_f) O^Q_ia,
+ * D_ia(z) = 2[1/(z - Delta_ia) - 1/(z + Delta_ia)], Delta_ia = eps_a - eps_i.
+ *   z   : DEVICE [F][2] (Re z, Im z); any complex z (Im z = 0 and Re z = Delta is a pole)
+ *   chi0: DEVICE [F][n_aux][n_aux][2] (Re, Im), full symmetric matrix written
+ * Computed with the context's precision (gwc_options.prec). 1 <= F <= 4096. */
+gwc_status gwc_build_chi0(gwc_ctx* ctx, const double* z, int F, double* chi0, void* stream);
+
+/* Screened interaction contractions W^c(z) = b^T (eps(z)^-1 - 1) b, eps = 1 - Pi(z), for
+ * n_rhs vectors b per frequency (Eqs. cd_imaginary, cd_residue with W^c = W - v):
+ *   z  : DEVICE [F][2]
+ *   rhs: DEVICE [F][n_rhs][n_aux] real vectors b
+ *   w  : DEVICE [F][n_rhs][2] (Re, Im)
+ * eps(z) is factored without pivoting (LDL^T, complex symmetric); a zero pivot sets
+ * GWC_ERR_SINGULAR (reported by gwc_sync) and leaves w undefined for that frequency.
+ * 1 <= F <= 4096, 1 <= n_rhs <= 1<<20. */
+gwc_status gwc_screen(gwc_ctx* ctx, const double* z, int F, const double* rhs, int n_rhs, double* w, void* stream);
+
+/* G0W0 correlation self-energy of every core by contour deformation (Eq. cd_terms:
+ * Sigma^c_n(w) = -I_n(w) + R_n(w); Eqs. cd_imaginary, cd_residue, cd_prefactors) on an
+ * absolute real-frequency grid shared by all cores, plus the exchange Sigma^x_n (Eq. sigma_x,
+ * occupied states) and, if requested, the decoupled Im Sigma (Eq. cd_sigma_imaginary_decoupled).
+ *   omega       : HOST [n_omega] real frequencies (Ha), any order
+ *   sigma_c     : DEVICE [n_core][n_omega][2] (Re, Im) of Sigma^c_n(omega_j)
+ *   im_sigma_dec: DEVICE [n_core][n_omega] Im Sigma in the options' decoupling form, or NULL
+ *   sigma_x     : DEVICE [n_core], or NULL
+ * The G_dH W0 self-energy of Eq. hedin_sigma_spectral is Sigma^c_n(w - dH_n). */
+gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double* sigma_c, double* im_sigma_dec,
+                          double* sigma_x, void* stream);
+
+/* Hedin shift and G_dH W0 quasiparticle energies (Eqs. hedin_shift, quasiparticle_equation,
+ * hedin_sigma_spectral, QPGWC): dH_n = Re Sigma^c_n(eps_n) + Sigma^x_n - v^xc_n, then
+ * eps = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n(eps - dH_n) solved by the secant method
+ * from eps_n on the device (no host synchronisation inside).
+ *   eps_qp, dh: DEVICE [n_core]; iters: DEVICE int [n_core] (Sigma evaluations used)
+ * A core that does not converge in max_qp_iter keeps its last iterate and sets
+ * GWC_ERR_NOT_CONVERGED (reported by gwc_sync). */
+gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, void* stream);
+
+/* Retarded-cumulant spectral function (Sec. "Numerical GW+C scheme": Eqs.
+ * landau_cumulant_truncated, cumulant_propagator_numerical_time,
+ * cumulant_propagator_fourier, cumulant_propagator_convolution, eq:AGWC):
+ *   beta_j = |Im Sigma_n(eps_n + w_j)| / pi,
+ *   C~(t) = sum_j q_j beta_j / w_j^2 (e^{-i w_j t} - 1)   (trapezoid weights q_j; w_j = 0 skipped),
+ *   A(eps^QP + nu) = (1/pi) Re int_0^{t_max} e^{i nu t - eta t} e^{C~(t)} dt,
+ * discretised with t_k = k t_max/n_t (weight 1/2 at k = 0) and a batched FP64 FFT.
+ *   omega_rel: DEVICE [n_core][n_omega] relative frequencies w_j = omega - eps_n, ascending
+ *   im_sigma : DEVICE [n_core][n_omega] Im Sigma at those frequencies
+ *   a_out    : DEVICE [n_core][n_t] A on the bins nu_j, ascending
+ *   nu_out   : DEVICE [n_t] the bins nu_j = 2 pi j / t_max, j = -n_t/2 .. n_t/2-1, or NULL
+ * The absolute frequency of bin j of core n is eps^QP_n + nu_j. */
+gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_omega, const double* im_sigma,
+                                 double* a_out, double* nu_out, void* stream);
+
+/* Synchronises `stream` and reports the first device-side status raised since the
+ * previous gwc_sync (then clears it). */
+gwc_status gwc_sync(gwc_ctx* ctx, void* stream);
+
+gwc_status gwc_get_stats(const gwc_ctx* ctx, gwc_stats* out);
+gwc_status gwc_reset_stats(gwc_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing gwc_create when ctx is
+ * NULL); valid until the next call on the same context from the same thread. */
+const char* gwc_last_error(const gwc_ctx* ctx);
+const char* gwc_status_string(gwc_status s);
+int gwc_abi_version(void);
+
+void gwc_destroy(gwc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWC_H */

@@ -1,0 +1,774 @@
+// C ABI of libgwc: context, residency, batching of frequencies, and the host-side
+// control of the self-energy, QP and cumulant steps. Every arithmetic step of the
+// path runs in the kernels of this library; the host only plans and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "gwc_internal.h"
+
+using namespace gwc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const double kPi = 3.14159265358979323846;
+
+gwc_status fail(gwc_ctx* ctx, gwc_status st, const std::string& msg) {
+  if (ctx)
+    ctx->last_error = msg;
+  else
+    g_create_error = msg;
+  return st;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? GWC_ERR_OOM : GWC_ERR_CUDA,               \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                            \
+  } while (0)
+
+#define LAUNCH(expr)                                                                               \
+  do {                                                                                             \
+    int n_ = (expr);                                                                               \
+    if (n_ < 0) {                                                                                  \
+      cudaError_t e_ = cudaGetLastError();                                                         \
+      return fail(ctx, GWC_ERR_CUDA, std::string("launch failed: ") + #expr + ": " + cudaGetErrorString(e_)); \
+    }                                                                                              \
+    ctx->stats.kernel_launches += n_;                                                              \
+  } while (0)
+
+inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// Gauss-Legendre nodes and weights on (-1, 1), ascending, by Newton iteration on P_n
+// (three-term recurrence; initial guesses cos(pi (i - 1/4)/(n + 1/2))).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) {
+        p1 = z;
+        p0 = 1.0;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    // recompute derivative at the converged node
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n == 1 ? 1.0 : n * (z * p1 - p0) / (z * z - 1.0);
+    double wt = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = wt;
+    w[n - 1 - i] = wt;
+  }
+  if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+MatKind real_kind(const gwc_ctx* c) { return c->opt.prec == GWC_PREC_FP64 ? MatKind::RealF64 : MatKind::RealF32; }
+MatKind cplx_kind(const gwc_ctx* c) { return c->opt.prec == GWC_PREC_FP64 ? MatKind::CplxF64 : MatKind::CplxF32; }
+
+template <typename T>
+gwc_status dalloc(gwc_ctx* ctx, T** p, size_t count) {
+  if (*p) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, GWC_ERR_OOM, std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) + "): " + cudaGetErrorString(e));
+  }
+  return GWC_OK;
+}
+
+#define TRY(x)                     \
+  do {                             \
+    gwc_status s_ = (x);           \
+    if (s_ != GWC_OK) return s_;   \
+  } while (0)
+
+gwc_status validate_system(const gwc_system* s) {
+  if (!s) return fail(nullptr, GWC_ERR_INVALID_ARG, "system is NULL");
+  if (s->n_states < 2 || s->n_occ < 1 || s->n_occ >= s->n_states || s->n_aux < 1 || s->n_core < 1 ||
+      s->n_core > s->n_occ)
+    return fail(nullptr, GWC_ERR_INVALID_ARG, "invalid sizes (need n_states>=2, 1<=n_occ<n_states, n_aux>=1, 1<=n_core<=n_occ)");
+  if (s->n_aux > 65536 || s->n_states > 65536) return fail(nullptr, GWC_ERR_INVALID_ARG, "n_aux and n_states must be <= 65536");
+  if ((long long)s->n_occ * (s->n_states - s->n_occ) > (1LL << 31) - 1)
+    return fail(nullptr, GWC_ERR_INVALID_ARG, "n_occ * n_virt too large");
+  if (!s->core_idx || !s->eps || !s->o_ov || !s->o_core) return fail(nullptr, GWC_ERR_INVALID_ARG, "NULL input pointer");
+  for (int c = 0; c < s->n_core; ++c)
+    if (s->core_idx[c] < 0 || s->core_idx[c] >= s->n_occ)
+      return fail(nullptr, GWC_ERR_INVALID_ARG, "core_idx must index occupied states");
+  if (s->memory != GWC_MEM_DEVICE && s->memory != GWC_MEM_HOST) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad memory kind");
+  return GWC_OK;
+}
+
+gwc_status validate_options(const gwc_options* o, int n_core) {
+  if (!o) return fail(nullptr, GWC_ERR_INVALID_ARG, "options is NULL");
+  if (!(o->eta > 0.0) || !std::isfinite(o->eta)) return fail(nullptr, GWC_ERR_INVALID_ARG, "eta must be > 0");
+  if (o->n_im < 1 || o->n_im > 1024) return fail(nullptr, GWC_ERR_INVALID_ARG, "n_im must be in 1..1024");
+  if (!(o->xi0 > 0.0)) return fail(nullptr, GWC_ERR_INVALID_ARG, "xi0 must be > 0");
+  if (o->prec < 0 || o->prec > 3) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad precision");
+  if (o->dec < 0 || o->dec > 2) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad decoupling mode");
+  if (o->n_t < 16 || o->n_t > (1 << 22) || (o->n_t & (o->n_t - 1)))
+    return fail(nullptr, GWC_ERR_INVALID_ARG, "n_t must be a power of two in 16..2^22");
+  if (!(o->t_max > 0.0)) return fail(nullptr, GWC_ERR_INVALID_ARG, "t_max must be > 0");
+  if (o->max_qp_iter < 2 || o->max_qp_iter > 200) return fail(nullptr, GWC_ERR_INVALID_ARG, "max_qp_iter must be in 2..200");
+  if (!(o->qp_tol > 0.0)) return fail(nullptr, GWC_ERR_INVALID_ARG, "qp_tol must be > 0");
+  if (o->batch < 0 || o->batch > 4096) return fail(nullptr, GWC_ERR_INVALID_ARG, "batch must be in 0..4096");
+  (void)n_core;
+  return GWC_OK;
+}
+
+struct Sizes {
+  int n_aux_pad, n_ov_pad, ld_dtab;
+  long long ldm;
+  size_t elem_c, elem_r;
+};
+
+Sizes sizes_of(const gwc_system* s, const gwc_options* o) {
+  Sizes z{};
+  int n_ov = s->n_occ * (s->n_states - s->n_occ);
+  z.n_aux_pad = (int)round_up(s->n_aux, 128);
+  z.n_ov_pad = (int)round_up(n_ov, 64);
+  z.ld_dtab = z.n_ov_pad;
+  z.ldm = round_up(s->n_aux, 4);
+  z.elem_c = o->prec == GWC_PREC_FP64 ? 16 : 8;
+  z.elem_r = o->prec == GWC_PREC_FP64 ? 8 : 4;
+  return z;
+}
+
+size_t per_matrix_bytes(const gwc_system* s, const Sizes& z) {
+  return (size_t)s->n_aux * z.ldm * z.elem_c + (size_t)s->n_core * z.ldm * z.elem_c + 2 * (size_t)z.ld_dtab * 8 + 256;
+}
+
+size_t resident_bytes(const gwc_system* s, const gwc_options* o, const Sizes& z) {
+  size_t n_ov = (size_t)s->n_occ * (s->n_states - s->n_occ);
+  size_t b = 0;
+  b += (size_t)s->n_states * 8 + n_ov * 8;                         // eps, delta
+  b += (size_t)s->n_aux * n_ov * 8;                                 // o_ov
+  b += (size_t)s->n_states * s->n_core * s->n_aux * 8;              // o_core
+  b += (size_t)(o->n_im + 1) * s->n_states * s->n_core * 8;         // W(i xi) table
+  b += (size_t)s->n_states * s->n_core * z.ldm * z.elem_r;          // imaginary-axis RHS
+  b += (size_t)s->n_states * s->n_core * (8 + 16 + 4);              // bnorm, w tmp, rowmap
+  if (o->prec != GWC_PREC_FP64) b += (size_t)z.n_aux_pad * z.n_ov_pad * (2 + 2 + 4);
+  return b;
+}
+
+int choose_batch(const gwc_system* s, const gwc_options* o, const Sizes& z) {
+  if (o->batch > 0) return o->batch;
+  size_t freeb = 0, totalb = 0;
+  size_t budget = (size_t)8 << 30;
+  if (cudaMemGetInfo(&freeb, &totalb) == cudaSuccess) budget = std::min<size_t>((size_t)(0.35 * freeb), (size_t)24 << 30);
+  size_t per = per_matrix_bytes(s, z);
+  long long f = (long long)(budget / per);
+  f = std::max(1LL, std::min(512LL, f));
+  return (int)f;
+}
+
+gwc_status upload(gwc_ctx* ctx, void* dst, const void* src, size_t bytes, int memory, cudaStream_t st) {
+  CU(cudaMemcpyAsync(dst, src, bytes, memory == GWC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  return GWC_OK;
+}
+
+gwc_status ensure_pinned_i(gwc_ctx* ctx, size_t n) {
+  if (n <= ctx->h_pin_i_cap) return GWC_OK;
+  if (ctx->h_pin_i) cudaFreeHost(ctx->h_pin_i);
+  ctx->h_pin_i = nullptr;
+  CU(cudaMallocHost((void**)&ctx->h_pin_i, n * sizeof(int)));
+  ctx->h_pin_i_cap = n;
+  return GWC_OK;
+}
+gwc_status ensure_pinned_d(gwc_ctx* ctx, size_t n) {
+  if (n <= ctx->h_pin_d_cap) return GWC_OK;
+  if (ctx->h_pin_d) cudaFreeHost(ctx->h_pin_d);
+  ctx->h_pin_d = nullptr;
+  CU(cudaMallocHost((void**)&ctx->h_pin_d, n * sizeof(double)));
+  ctx->h_pin_d_cap = n;
+  return GWC_OK;
+}
+
+// Loads eps / O / vxc into the context and derives everything that depends only on them.
+gwc_status load_system(gwc_ctx* ctx, const gwc_system* s, cudaStream_t st) {
+  const size_t n_ov = (size_t)ctx->n_ov;
+  ctx->h_eps.resize(s->n_states);
+  if (s->memory == GWC_MEM_HOST) {
+    std::memcpy(ctx->h_eps.data(), s->eps, sizeof(double) * s->n_states);
+  } else {
+    CU(cudaMemcpyAsync(ctx->h_eps.data(), s->eps, sizeof(double) * s->n_states, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  for (int i = 1; i < s->n_states; ++i)
+    if (!(ctx->h_eps[i] >= ctx->h_eps[i - 1])) return fail(ctx, GWC_ERR_INVALID_ARG, "eps must be ascending and finite");
+  ctx->eps_f = std::isnan(s->eps_f) ? 0.5 * (ctx->h_eps[s->n_occ - 1] + ctx->h_eps[s->n_occ]) : s->eps_f;
+  ctx->h_core.assign(s->core_idx, s->core_idx + s->n_core);
+  TRY(upload(ctx, ctx->d_eps, s->eps, sizeof(double) * s->n_states, s->memory, st));
+  TRY(upload(ctx, ctx->d_o_ov, s->o_ov, sizeof(double) * s->n_aux * n_ov, s->memory, st));
+  TRY(upload(ctx, ctx->d_o_core, s->o_core, sizeof(double) * s->n_states * s->n_core * s->n_aux, s->memory, st));
+  CU(cudaMemcpyAsync(ctx->d_core_idx, ctx->h_core.data(), sizeof(int) * s->n_core, cudaMemcpyHostToDevice, st));
+  LAUNCH(launch_delta(ctx->d_eps, ctx->n_occ, ctx->n_virt, ctx->d_delta, st));
+  if (ctx->opt.prec != GWC_PREC_FP64)
+    LAUNCH(launch_split_o(ctx->d_o_ov, ctx->n_aux, ctx->n_ov, ctx->n_aux_pad, ctx->n_ov_pad, ctx->d_o_hi, ctx->d_o_lo,
+                          ctx->d_o_f32, st));
+  LAUNCH(launch_sigma_x(ctx->d_o_core, ctx->n_occ, ctx->n_core, ctx->n_aux, ctx->d_sx, st));
+  ctx->vxc_given = s->vxc != nullptr;
+  if (s->vxc)
+    TRY(upload(ctx, ctx->d_vxc_eff, s->vxc, sizeof(double) * s->n_core, s->memory, st));
+  else
+    CU(cudaMemcpyAsync(ctx->d_vxc_eff, ctx->d_sx, sizeof(double) * s->n_core, cudaMemcpyDeviceToDevice, st));
+  ctx->wim_valid = false;
+  CU(cudaStreamSynchronize(st));
+  return GWC_OK;
+}
+
+// ---- chi0 dispatch ------------------------------------------------------------------------------
+gwc_status run_chi0(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, const int* active, void* out, double alpha,
+                    double beta, int full, cudaStream_t st) {
+  const int prec = ctx->opt.prec;
+  const bool fp64 = prec == GWC_PREC_FP64;
+  LAUNCH(launch_dtable(d_z, F, ctx->d_delta, ctx->n_ov, ctx->ld_dtab, !fp64, ctx->d_dtab, st));
+  MatKind kind = complex_z ? cplx_kind(ctx) : real_kind(ctx);
+  const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  if (prec == GWC_PREC_FP64) {
+    LAUNCH(launch_chi0_simt(kind, ctx->d_o_ov, ctx->n_ov, ctx->n_aux, ctx->n_ov, ctx->d_dtab, ctx->ld_dtab, F, alpha, beta,
+                            out, ctx->ldm, stride, full, active, st));
+  } else if (prec == GWC_PREC_FP32) {
+    LAUNCH(launch_chi0_simt(kind, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux, ctx->n_ov_pad, ctx->d_dtab, ctx->ld_dtab, F,
+                            alpha, beta, out, ctx->ldm, stride, full, active, st));
+  } else {
+    int n = launch_chi0_tc(prec == GWC_PREC_BF16X3, ctx->d_o_hi, ctx->d_o_lo, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux,
+                           ctx->n_aux_pad, ctx->n_ov_pad, (const float*)ctx->d_dtab, ctx->ld_dtab, F, complex_z, alpha,
+                           beta, out, ctx->ldm, stride, active, ctx->d_status, st);
+    if (n == -2) return fail(ctx, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for this shape/device");
+    LAUNCH(n);
+    if (full) {
+      // the tensor-core kernel writes the lower triangle; mirror for a full matrix
+      return fail(ctx, GWC_ERR_UNSUPPORTED, "full-matrix output not supported by the tensor-core path");
+    }
+  }
+  ctx->stats.chi0_builds += F;
+  ctx->stats.chi0_flop += (double)F * (complex_z ? 2.0 : 1.0) * (double)ctx->n_aux * (ctx->n_aux + 1.0) * (double)ctx->n_ov;
+  return GWC_OK;
+}
+
+// ---- imaginary-axis W table --------------------------------------------------------------------
+gwc_status compute_wim(gwc_ctx* ctx, cudaStream_t st) {
+  if (ctx->wim_valid) return GWC_OK;
+  const int nodes = ctx->opt.n_im + 1;
+  MatKind rk = real_kind(ctx);
+  const size_t per_real = (size_t)ctx->n_aux * ctx->ldm * mat_elem_bytes(rk);
+  int fb = (int)std::max<size_t>(1, std::min<size_t>(ctx->mats_bytes / per_real, (size_t)ctx->batch));
+  fb = std::min(fb, nodes);
+  const int r = ctx->n_states * ctx->n_core;
+  std::vector<double> xi(ctx->opt.n_im);
+  CU(cudaMemcpyAsync(xi.data(), ctx->d_xi, sizeof(double) * ctx->opt.n_im, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  TRY(ensure_pinned_d(ctx, 2 * (size_t)nodes));
+  for (int k = 0; k < nodes; ++k) {
+    ctx->h_pin_d[2 * k] = 0.0;
+    ctx->h_pin_d[2 * k + 1] = k < ctx->opt.n_im ? xi[k] : 0.0;
+  }
+  const size_t plane = (size_t)ctx->n_states * ctx->n_core;
+  const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  double* d_zall = nullptr;
+  TRY(dalloc(ctx, &d_zall, 2 * (size_t)nodes));
+  cudaError_t ce = cudaMemcpyAsync(d_zall, ctx->h_pin_d, sizeof(double) * 2 * nodes, cudaMemcpyHostToDevice, st);
+  if (ce != cudaSuccess) {
+    cudaFree(d_zall);
+    return fail(ctx, GWC_ERR_CUDA, cudaGetErrorString(ce));
+  }
+  gwc_status res = GWC_OK;
+  for (int k0 = 0; k0 < nodes && res == GWC_OK; k0 += fb) {
+    const int nb = std::min(fb, nodes - k0);
+    res = run_chi0(ctx, false, nb, d_zall + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st);
+    if (res != GWC_OK) break;
+    int n = launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st);
+    if (n < 0) {
+      res = fail(ctx, GWC_ERR_CUDA, "ldlt launch failed");
+      break;
+    }
+    ctx->stats.kernel_launches += n;
+    ctx->stats.factorizations += nb;
+    for (int u = 0; u < nb && res == GWC_OK; ++u) {
+      const int k = k0 + u;
+      int n1 = launch_rhs_gather(rk, ctx->d_o_core, ctx->n_aux, ctx->d_rowmap, 1, r, ctx->n_aux, ctx->d_rhs_im, ctx->ldm,
+                                 0, ctx->d_bnorm, st);
+      char* mat = (char*)ctx->d_mats + (size_t)u * stride * mat_elem_bytes(rk);
+      int n2 = launch_ldlt_solve_w(rk, mat, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs_im, r, ctx->ldm, 0, ctx->d_bnorm, 1,
+                                   ctx->d_wtmp, 0, nullptr, st);
+      if (n1 < 0 || n2 < 0) {
+        res = fail(ctx, GWC_ERR_CUDA, "imaginary-axis solve launch failed");
+        break;
+      }
+      ctx->stats.kernel_launches += n1 + n2;
+      // real part of w -> W table plane k
+      ce = cudaMemcpy2DAsync(ctx->d_wim + (size_t)k * plane, sizeof(double), ctx->d_wtmp, 2 * sizeof(double),
+                             sizeof(double), plane, cudaMemcpyDeviceToDevice, st);
+      if (ce != cudaSuccess) res = fail(ctx, GWC_ERR_CUDA, cudaGetErrorString(ce));
+    }
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(d_zall);
+  if (res == GWC_OK) ctx->wim_valid = true;
+  return res;
+}
+
+// ---- residue W for a list of (frequency, state m) pairs ---------------------------------------------
+// z_dev [n_pairs][2], rows_dev [n_pairs * r] (rows of o_core flattened [m][c]), output w [n_pairs][r][2].
+gwc_status residue_batches(gwc_ctx* ctx, int n_pairs, const double* z_dev, const int* rows_dev, int r, double* w_out,
+                           const int* active, cudaStream_t st) {
+  MatKind ck = cplx_kind(ctx);
+  const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  const long long rstride = (long long)r * ctx->ldm;
+  for (int p0 = 0; p0 < n_pairs; p0 += ctx->batch) {
+    const int nb = std::min(ctx->batch, n_pairs - p0);
+    const int* act = active ? active + p0 : nullptr;
+    TRY(run_chi0(ctx, true, nb, z_dev + 2 * (size_t)p0, act, ctx->d_mats, -1.0, 1.0, 0, st));
+    LAUNCH(launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, act, ctx->d_status, st));
+    ctx->stats.factorizations += nb;
+    LAUNCH(launch_rhs_gather(ck, ctx->d_o_core, ctx->n_aux, rows_dev + (size_t)p0 * r, nb, r, ctx->n_aux, ctx->d_rhs,
+                             ctx->ldm, rstride, ctx->d_bnorm, st));
+    LAUNCH(launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs, r, ctx->ldm, rstride,
+                               ctx->d_bnorm, nb, w_out + (size_t)p0 * r * 2, (long long)r * 2, act, st));
+  }
+  return GWC_OK;
+}
+
+gwc_status check_stream_error(gwc_ctx* ctx) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, GWC_ERR_CUDA, cudaGetErrorString(e));
+  return GWC_OK;
+}
+
+}  // namespace
+
+// =====================================================================================================
+extern "C" {
+
+int gwc_abi_version(void) { return GWC_ABI_VERSION; }
+
+const char* gwc_status_string(gwc_status s) {
+  switch (s) {
+    case GWC_OK: return "ok";
+    case GWC_ERR_INVALID_ARG: return "invalid argument";
+    case GWC_ERR_OOM: return "out of memory";
+    case GWC_ERR_CUDA: return "CUDA error";
+    case GWC_ERR_SINGULAR: return "singular dielectric matrix";
+    case GWC_ERR_NOT_CONVERGED: return "QP iteration not converged";
+    case GWC_ERR_TIMEOUT: return "device wait timed out";
+    case GWC_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* gwc_last_error(const gwc_ctx* ctx) { return ctx ? ctx->last_error.c_str() : g_create_error.c_str(); }
+
+gwc_status gwc_default_options(gwc_options* o) {
+  if (!o) return GWC_ERR_INVALID_ARG;
+  o->eta = 1e-3;
+  o->n_im = 32;
+  o->xi0 = 1.0;
+  o->prec = GWC_PREC_BF16X3;
+  o->dec = GWC_DECOUPLE_DIAG;
+  o->group_of_core = nullptr;
+  o->n_t = 1 << 16;
+  o->t_max = 2000.0;
+  o->max_qp_iter = 50;
+  o->qp_tol = 1e-7;
+  o->batch = 0;
+  return GWC_OK;
+}
+
+gwc_status gwc_workspace_bytes(const gwc_system* sys, const gwc_options* opt, int n_omega, size_t* bytes) {
+  TRY(validate_system(sys));
+  TRY(validate_options(opt, sys->n_core));
+  if (!bytes || n_omega < 0) return fail(nullptr, GWC_ERR_INVALID_ARG, "bytes NULL or n_omega < 0");
+  Sizes z = sizes_of(sys, opt);
+  int batch = opt->batch > 0 ? opt->batch : 64;
+  size_t b = resident_bytes(sys, opt, z) + (size_t)batch * per_matrix_bytes(sys, z);
+  b += (size_t)n_omega * sys->n_states * (4 + 4 + 8 + 16 + 8 + 4 * sys->n_core) + (size_t)n_omega * sys->n_occ * sys->n_core * 16;
+  b += (size_t)sys->n_core * opt->n_t * 32 + (size_t)opt->n_t * 8;
+  *bytes = b;
+  return GWC_OK;
+}
+
+gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, void* stream) {
+  if (!out) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx out pointer is NULL");
+  *out = nullptr;
+  TRY(validate_system(s));
+  TRY(validate_options(o, s->n_core));
+  cudaStream_t st = (cudaStream_t)stream;
+  gwc_ctx* ctx = new gwc_ctx();
+  cudaGetDevice(&ctx->device);
+  ctx->n_states = s->n_states;
+  ctx->n_occ = s->n_occ;
+  ctx->n_virt = s->n_states - s->n_occ;
+  ctx->n_aux = s->n_aux;
+  ctx->n_core = s->n_core;
+  ctx->n_ov = s->n_occ * ctx->n_virt;
+  ctx->opt = *o;
+  if (o->group_of_core) ctx->h_group.assign(o->group_of_core, o->group_of_core + s->n_core);
+  ctx->opt.group_of_core = nullptr;
+  Sizes z = sizes_of(s, o);
+  ctx->n_aux_pad = z.n_aux_pad;
+  ctx->n_ov_pad = z.n_ov_pad;
+  ctx->ld_dtab = z.ld_dtab;
+  ctx->ldm = z.ldm;
+  auto bail = [&](gwc_status stt) {
+    std::string msg = ctx->last_error;
+    gwc_destroy(ctx);
+    g_create_error = msg;
+    return stt;
+  };
+#define CTRY(x)                        \
+  do {                                 \
+    gwc_status s_ = (x);               \
+    if (s_ != GWC_OK) return bail(s_); \
+  } while (0)
+  const size_t n_ov = ctx->n_ov;
+  CTRY(dalloc(ctx, &ctx->d_eps, s->n_states));
+  CTRY(dalloc(ctx, &ctx->d_delta, n_ov));
+  CTRY(dalloc(ctx, &ctx->d_o_ov, (size_t)s->n_aux * n_ov));
+  CTRY(dalloc(ctx, &ctx->d_o_core, (size_t)s->n_states * s->n_core * s->n_aux));
+  CTRY(dalloc(ctx, &ctx->d_core_idx, s->n_core));
+  CTRY(dalloc(ctx, &ctx->d_sx, s->n_core));
+  CTRY(dalloc(ctx, &ctx->d_vxc_eff, s->n_core));
+  CTRY(dalloc(ctx, &ctx->d_status, 4));
+  CTRY(dalloc(ctx, &ctx->d_all_done, 1));
+  if (!ctx->h_group.empty()) {
+    CTRY(dalloc(ctx, &ctx->d_group, s->n_core));
+    if (cudaMemcpy(ctx->d_group, ctx->h_group.data(), sizeof(int) * s->n_core, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(ctx, GWC_ERR_CUDA, "group upload failed"));
+  }
+  cudaMemsetAsync(ctx->d_status, 0, 4 * sizeof(unsigned), st);
+  if (o->prec != GWC_PREC_FP64) {
+    size_t np = (size_t)z.n_aux_pad * z.n_ov_pad;
+    CTRY(dalloc(ctx, &ctx->d_o_hi, np));
+    CTRY(dalloc(ctx, &ctx->d_o_lo, np));
+    CTRY(dalloc(ctx, &ctx->d_o_f32, np));
+  }
+  // imaginary grid
+  {
+    std::vector<double> x, w;
+    gauss_legendre(o->n_im, x, w);
+    std::vector<double> xi(o->n_im), wx(o->n_im);
+    for (int k = 0; k < o->n_im; ++k) {
+      xi[k] = o->xi0 * (1.0 + x[k]) / (1.0 - x[k]);
+      wx[k] = 2.0 * o->xi0 * w[k] / ((1.0 - x[k]) * (1.0 - x[k]));
+    }
+    CTRY(dalloc(ctx, &ctx->d_xi, o->n_im));
+    CTRY(dalloc(ctx, &ctx->d_wxi, o->n_im));
+    if (cudaMemcpy(ctx->d_xi, xi.data(), sizeof(double) * o->n_im, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->d_wxi, wx.data(), sizeof(double) * o->n_im, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(ctx, GWC_ERR_CUDA, "grid upload failed"));
+  }
+  const size_t plane = (size_t)s->n_states * s->n_core;
+  CTRY(dalloc(ctx, &ctx->d_wim, (size_t)(o->n_im + 1) * plane));
+  // workspace
+  ctx->batch = choose_batch(s, o, z);
+  ctx->mats_bytes = (size_t)ctx->batch * s->n_aux * z.ldm * z.elem_c;
+  {
+    char* p = nullptr;
+    CTRY(dalloc(ctx, &p, ctx->mats_bytes));
+    ctx->d_mats = p;
+    char* q = nullptr;
+    CTRY(dalloc(ctx, &q, (size_t)ctx->batch * 2 * z.ld_dtab * 8));
+    ctx->d_dtab = q;
+    ctx->rhs_bytes = (size_t)ctx->batch * s->n_core * z.ldm * z.elem_c;
+    char* r = nullptr;
+    CTRY(dalloc(ctx, &r, ctx->rhs_bytes));
+    ctx->d_rhs = r;
+    char* ri = nullptr;
+    CTRY(dalloc(ctx, &ri, plane * z.ldm * z.elem_r));
+    ctx->d_rhs_im = ri;
+  }
+  CTRY(dalloc(ctx, &ctx->d_z, 2 * (size_t)ctx->batch));
+  CTRY(dalloc(ctx, &ctx->d_active, ctx->batch));
+  CTRY(dalloc(ctx, &ctx->d_bnorm, std::max(plane, (size_t)ctx->batch * s->n_core)));
+  CTRY(dalloc(ctx, &ctx->d_wtmp, 2 * std::max(plane, (size_t)ctx->batch * s->n_core)));
+  CTRY(dalloc(ctx, &ctx->d_rowmap, plane));
+  {
+    std::vector<int> ident(plane);
+    for (size_t i = 0; i < plane; ++i) ident[i] = (int)i;
+    if (cudaMemcpy(ctx->d_rowmap, ident.data(), sizeof(int) * plane, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(ctx, GWC_ERR_CUDA, "rowmap upload failed"));
+  }
+  // QP buffers
+  {
+    const size_t np = (size_t)s->n_core * s->n_occ;
+    CTRY(dalloc(ctx, &ctx->d_qp, s->n_core));
+    CTRY(dalloc(ctx, &ctx->d_qp_z, 2 * np));
+    CTRY(dalloc(ctx, &ctx->d_qp_active, np));
+    CTRY(dalloc(ctx, &ctx->d_qp_fac, np));
+    CTRY(dalloc(ctx, &ctx->d_qp_w, 2 * np));
+    CTRY(dalloc(ctx, &ctx->d_qp_rowmap, np));
+    std::vector<int> rows(np);
+    for (int c = 0; c < s->n_core; ++c)
+      for (int m = 0; m < s->n_occ; ++m) rows[(size_t)c * s->n_occ + m] = m * s->n_core + c;
+    if (cudaMemcpy(ctx->d_qp_rowmap, rows.data(), sizeof(int) * np, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(ctx, GWC_ERR_CUDA, "qp rowmap upload failed"));
+  }
+  CTRY(load_system(ctx, s, st));
+#undef CTRY
+  *out = ctx;
+  return GWC_OK;
+}
+
+gwc_status gwc_load(gwc_ctx* ctx, const gwc_system* s, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (validate_system(s) != GWC_OK) return fail(ctx, GWC_ERR_INVALID_ARG, g_create_error);
+  if (s->n_states != ctx->n_states || s->n_occ != ctx->n_occ || s->n_aux != ctx->n_aux || s->n_core != ctx->n_core)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "gwc_load needs a system of the same sizes as the context");
+  return load_system(ctx, s, (cudaStream_t)stream);
+}
+
+void gwc_destroy(gwc_ctx* ctx) {
+  if (!ctx) return;
+  void* ptrs[] = {ctx->d_eps, ctx->d_o_ov, ctx->d_o_core, ctx->d_vxc, ctx->d_delta, ctx->d_core_idx, ctx->d_group,
+                  ctx->d_xi, ctx->d_wxi, ctx->d_wim, ctx->d_sx, ctx->d_vxc_eff, ctx->d_o_hi, ctx->d_o_lo, ctx->d_o_f32,
+                  ctx->d_mats, ctx->d_dtab, ctx->d_z, ctx->d_active, ctx->d_rhs, ctx->d_bnorm, ctx->d_rowmap,
+                  ctx->d_wtmp, ctx->d_rhs_im, ctx->d_status, ctx->d_pidx, ctx->d_wres, ctx->d_pair_m, ctx->d_pair_w,
+                  ctx->d_grid_w, ctx->d_qp, ctx->d_qp_z, ctx->d_qp_active, ctx->d_qp_fac, ctx->d_qp_w,
+                  ctx->d_qp_rowmap, ctx->d_all_done, ctx->d_cw_a, ctx->d_cw_b, ctx->d_coef, ctx->d_tw,
+                  ctx->d_pair_z, ctx->d_pair_rows};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (ctx->h_pin_i) cudaFreeHost(ctx->h_pin_i);
+  if (ctx->h_pin_d) cudaFreeHost(ctx->h_pin_d);
+  delete ctx;
+}
+
+gwc_status gwc_build_chi0(gwc_ctx* ctx, const double* z, int F, double* chi0, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!z || !chi0 || F < 1 || F > 4096) return fail(ctx, GWC_ERR_INVALID_ARG, "need z, chi0 and 1 <= F <= 4096");
+  cudaStream_t st = (cudaStream_t)stream;
+  MatKind ck = cplx_kind(ctx);
+  const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  for (int f0 = 0; f0 < F; f0 += ctx->batch) {
+    int nb = std::min(ctx->batch, F - f0);
+    TRY(run_chi0(ctx, true, nb, z + 2 * (size_t)f0, nullptr, ctx->d_mats, 1.0, 0.0, 0, st));
+    LAUNCH(launch_mat_to_c128(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb,
+                              chi0 + (size_t)f0 * ctx->n_aux * ctx->n_aux * 2, st));
+  }
+  return check_stream_error(ctx);
+}
+
+gwc_status gwc_screen(gwc_ctx* ctx, const double* z, int F, const double* rhs, int n_rhs, double* w, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!z || !rhs || !w || F < 1 || F > 4096 || n_rhs < 1 || n_rhs > (1 << 20))
+    return fail(ctx, GWC_ERR_INVALID_ARG, "need z, rhs, w, 1 <= F <= 4096, 1 <= n_rhs <= 2^20");
+  cudaStream_t st = (cudaStream_t)stream;
+  MatKind ck = cplx_kind(ctx);
+  const size_t es = mat_elem_bytes(ck);
+  // per-call scratch for the right-hand sides of one frequency chunk
+  int chunk = std::max(1, std::min(ctx->batch, (int)std::max<size_t>(1, ((size_t)1 << 30) / ((size_t)n_rhs * ctx->ldm * es))));
+  void* d_r = nullptr;
+  double* d_bn = nullptr;
+  int* d_rows = nullptr;
+  size_t nrow = (size_t)chunk * n_rhs;
+  if (cudaMalloc(&d_r, nrow * ctx->ldm * es) != cudaSuccess || cudaMalloc((void**)&d_bn, nrow * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&d_rows, nrow * sizeof(int)) != cudaSuccess) {
+    cudaFree(d_r);
+    cudaFree(d_bn);
+    cudaFree(d_rows);
+    return fail(ctx, GWC_ERR_OOM, "gwc_screen scratch allocation failed");
+  }
+  std::vector<int> rows(nrow);
+  gwc_status res = GWC_OK;
+  const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  for (int f0 = 0; f0 < F && res == GWC_OK; f0 += chunk) {
+    int nb = std::min(chunk, F - f0);
+    for (size_t i = 0; i < (size_t)nb * n_rhs; ++i) rows[i] = (int)((size_t)f0 * n_rhs + i);
+    if (cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * nb * n_rhs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      res = fail(ctx, GWC_ERR_CUDA, "row map upload failed");
+      break;
+    }
+    res = run_chi0(ctx, true, nb, z + 2 * (size_t)f0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st);
+    if (res != GWC_OK) break;
+    int n1 = launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st);
+    int n2 = launch_rhs_gather(ck, rhs, ctx->n_aux, d_rows, nb, n_rhs, ctx->n_aux, d_r, ctx->ldm,
+                               (long long)n_rhs * ctx->ldm, d_bn, st);
+    int n3 = launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, d_r, n_rhs, ctx->ldm,
+                                 (long long)n_rhs * ctx->ldm, d_bn, nb, w + (size_t)f0 * n_rhs * 2, (long long)n_rhs * 2,
+                                 nullptr, st);
+    if (n1 < 0 || n2 < 0 || n3 < 0) res = fail(ctx, GWC_ERR_CUDA, "screen launch failed");
+    ctx->stats.kernel_launches += std::max(n1, 0) + std::max(n2, 0) + std::max(n3, 0);
+    ctx->stats.factorizations += nb;
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(d_r);
+  cudaFree(d_bn);
+  cudaFree(d_rows);
+  if (res != GWC_OK) return res;
+  return check_stream_error(ctx);
+}
+
+gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double* sigma_c, double* im_sigma_dec,
+                          double* sigma_x, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!omega || !sigma_c || n_omega < 1 || n_omega > (1 << 20))
+    return fail(ctx, GWC_ERR_INVALID_ARG, "need omega, sigma_c and 1 <= n_omega <= 2^20");
+  for (int j = 0; j < n_omega; ++j)
+    if (!std::isfinite(omega[j])) return fail(ctx, GWC_ERR_INVALID_ARG, "omega must be finite");
+  cudaStream_t st = (cudaStream_t)stream;
+  TRY(compute_wim(ctx, st));
+  const int ns = ctx->n_states, nc = ctx->n_core;
+  // plan: one residue pair per (w_j, m) with f_m(w_j) != 0 (Eq. cd_prefactors)
+  auto th = [](double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); };
+  std::vector<int> pidx((size_t)n_omega * ns, -1);
+  std::vector<int> pm;
+  std::vector<double> pw;
+  for (int j = 0; j < n_omega; ++j)
+    for (int m = 0; m < ns; ++m) {
+      double em = ctx->h_eps[m], w = omega[j];
+      double f = -th(ctx->eps_f - em) * th(em - w) + th(em - ctx->eps_f) * th(w - em);
+      if (f != 0.0) {
+        pidx[(size_t)j * ns + m] = (int)pm.size();
+        pm.push_back(m);
+        pw.push_back(w);
+      }
+    }
+  const int n_pairs = (int)pm.size();
+  if ((size_t)n_omega * ns > (size_t)ctx->pidx_cap) {
+    TRY(dalloc(ctx, &ctx->d_pidx, (size_t)n_omega * ns));
+    ctx->pidx_cap = n_omega * ns;
+  }
+  if ((size_t)std::max(1, n_pairs) > (size_t)ctx->wres_cap) {
+    size_t cap = std::max(1, n_pairs);
+    TRY(dalloc(ctx, &ctx->d_wres, cap * nc * 2));
+    TRY(dalloc(ctx, &ctx->d_pair_m, cap));
+    TRY(dalloc(ctx, &ctx->d_pair_w, cap));
+    TRY(dalloc(ctx, &ctx->d_pair_z, cap * 2));
+    TRY(dalloc(ctx, &ctx->d_pair_rows, cap * nc));
+    ctx->wres_cap = (int)cap;
+  }
+  if (n_omega > ctx->grid_cap) {
+    TRY(dalloc(ctx, &ctx->d_grid_w, n_omega));
+    ctx->grid_cap = n_omega;
+  }
+  std::vector<int> rows((size_t)n_pairs * nc);
+  for (int p = 0; p < n_pairs; ++p)
+    for (int c = 0; c < nc; ++c) rows[(size_t)p * nc + c] = pm[p] * nc + c;
+  CU(cudaMemcpyAsync(ctx->d_pidx, pidx.data(), sizeof(int) * pidx.size(), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(ctx->d_grid_w, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, st));
+  if (n_pairs > 0) {
+    CU(cudaMemcpyAsync(ctx->d_pair_m, pm.data(), sizeof(int) * n_pairs, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(ctx->d_pair_w, pw.data(), sizeof(double) * n_pairs, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(ctx->d_pair_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, st));
+    LAUNCH(launch_fill_z_pairs(ctx->d_eps, ctx->d_pair_m, ctx->d_pair_w, n_pairs, ctx->opt.eta, ctx->d_pair_z, st));
+    TRY(residue_batches(ctx, n_pairs, ctx->d_pair_z, ctx->d_pair_rows, nc, ctx->d_wres, nullptr, st));
+  }
+  LAUNCH(launch_sigma_grid(ctx->d_eps, ns, nc, ctx->d_core_idx, ctx->d_grid_w, n_omega, ctx->eps_f, ctx->d_xi, ctx->d_wxi,
+                           ctx->opt.n_im, ctx->d_wim, ctx->d_pidx, ctx->d_wres, ctx->opt.dec, ctx->d_group, sigma_c,
+                           im_sigma_dec, st));
+  if (sigma_x) CU(cudaMemcpyAsync(sigma_x, ctx->d_sx, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
+  // the host vectors above are read by the async copies: wait before they go out of scope
+  CU(cudaStreamSynchronize(st));
+  return check_stream_error(ctx);
+}
+
+gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!eps_qp || !dh || !iters) return fail(ctx, GWC_ERR_INVALID_ARG, "need eps_qp, dh, iters");
+  cudaStream_t st = (cudaStream_t)stream;
+  TRY(compute_wim(ctx, st));
+  const int nc = ctx->n_core, no = ctx->n_occ;
+  const int np = nc * no;
+  LAUNCH(launch_qp_init(ctx->d_eps, ctx->d_core_idx, nc, ctx->d_qp, st));
+  const int rounds = ctx->opt.max_qp_iter + 2;
+  for (int r = 0; r < rounds; ++r) {
+    LAUNCH(launch_qp_pairs(ctx->d_eps, ctx->d_core_idx, nc, no, ctx->eps_f, ctx->opt.eta, ctx->d_qp, ctx->d_qp_z,
+                           ctx->d_qp_active, ctx->d_qp_fac, ctx->d_all_done, st));
+    TRY(residue_batches(ctx, np, ctx->d_qp_z, ctx->d_qp_rowmap, 1, ctx->d_qp_w, ctx->d_qp_active, st));
+    LAUNCH(launch_qp_assemble_update(ctx->d_eps, ctx->n_states, no, nc, ctx->d_core_idx, ctx->eps_f, ctx->d_xi,
+                                     ctx->d_wxi, ctx->opt.n_im, ctx->d_wim, ctx->d_qp_w, ctx->d_qp_fac, ctx->d_sx,
+                                     ctx->d_vxc_eff, ctx->opt.qp_tol, ctx->opt.max_qp_iter, ctx->d_qp, ctx->d_all_done,
+                                     st));
+    // every 4 rounds, stop early if all cores are done (one 4-byte read)
+    if ((r & 3) == 3) {
+      int done = 0;
+      CU(cudaMemcpyAsync(&done, ctx->d_all_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      if (done) break;
+    }
+  }
+  LAUNCH(launch_qp_finish(ctx->d_qp, nc, eps_qp, dh, iters, ctx->d_status, st));
+  return check_stream_error(ctx);
+}
+
+gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_omega, const double* im_sigma,
+                                 double* a_out, double* nu_out, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!omega_rel || !im_sigma || !a_out || n_omega < 1 || n_omega > 8192)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "need omega_rel, im_sigma, a_out and 1 <= n_omega <= 8192");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nt = ctx->opt.n_t, nc = ctx->n_core;
+  if (nc * nt * 2 > ctx->cw_cap) {
+    TRY(dalloc(ctx, &ctx->d_cw_a, nc * nt * 2));
+    TRY(dalloc(ctx, &ctx->d_cw_b, nc * nt * 2));
+    TRY(dalloc(ctx, &ctx->d_tw, nt));
+    ctx->cw_cap = nc * nt * 2;
+  }
+  if (nc * (size_t)n_omega > ctx->coef_cap) {
+    TRY(dalloc(ctx, &ctx->d_coef, nc * (size_t)n_omega));
+    ctx->coef_cap = nc * (size_t)n_omega;
+  }
+  LAUNCH(launch_cumulant_spectrum(omega_rel, n_omega, im_sigma, (int)nc, (int)nt, ctx->opt.t_max, ctx->opt.eta,
+                                  ctx->d_cw_a, ctx->d_cw_b, ctx->d_coef, ctx->d_tw, a_out, nu_out, st));
+  return check_stream_error(ctx);
+}
+
+gwc_status gwc_sync(gwc_ctx* ctx, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned flags = 0;
+  CU(cudaMemcpyAsync(&flags, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  CU(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), st));
+  CU(cudaStreamSynchronize(st));
+  if (flags & kStatTimeout) return fail(ctx, GWC_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (flags & kStatSingular) return fail(ctx, GWC_ERR_SINGULAR, "zero pivot in a dielectric factorisation");
+  if (flags & kStatNotConverged) return fail(ctx, GWC_ERR_NOT_CONVERGED, "QP secant iteration hit max_qp_iter");
+  if (flags & kStatBadIndex) return fail(ctx, GWC_ERR_INVALID_ARG, "device-side index check failed");
+  return GWC_OK;
+}
+
+gwc_status gwc_get_stats(const gwc_ctx* ctx, gwc_stats* out) {
+  if (!ctx || !out) return GWC_ERR_INVALID_ARG;
+  *out = ctx->stats;
+  return GWC_OK;
+}
+
+gwc_status gwc_reset_stats(gwc_ctx* ctx) {
+  if (!ctx) return GWC_ERR_INVALID_ARG;
+  ctx->stats = gwc_stats{};
+  return GWC_OK;
+}
+
+}  // extern "C"

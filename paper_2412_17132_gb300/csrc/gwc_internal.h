@@ -1,0 +1,259 @@
+// Internal declarations of libgwc (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gwc.h"
+
+namespace gwc {
+
+// ------------------------------------------------------------------------------------------
+// Scalar traits for the dielectric matrices: real/complex, float/double.
+// Complex matrices are complex SYMMETRIC (eps(z)^T = eps(z)); no conjugation anywhere.
+// ------------------------------------------------------------------------------------------
+template <typename S> struct ST;
+template <> struct ST<float> { using R = float; static constexpr bool kComplex = false; };
+template <> struct ST<double> { using R = double; static constexpr bool kComplex = false; };
+template <> struct ST<float2> { using R = float; static constexpr bool kComplex = true; };
+template <> struct ST<double2> { using R = double; static constexpr bool kComplex = true; };
+
+__host__ __device__ inline float sadd(float a, float b) { return a + b; }
+__host__ __device__ inline double sadd(double a, double b) { return a + b; }
+__host__ __device__ inline float2 sadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 sadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float ssub(float a, float b) { return a - b; }
+__host__ __device__ inline double ssub(double a, double b) { return a - b; }
+__host__ __device__ inline float2 ssub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 ssub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float smul(float a, float b) { return a * b; }
+__host__ __device__ inline double smul(double a, double b) { return a * b; }
+__host__ __device__ inline float2 smul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 smul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// c - a*b
+__host__ __device__ inline float sfnms(float a, float b, float c) { return fmaf(-a, b, c); }
+__host__ __device__ inline double sfnms(double a, double b, double c) { return fma(-a, b, c); }
+__host__ __device__ inline float2 sfnms(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+__host__ __device__ inline double2 sfnms(double2 a, double2 b, double2 c) {
+  return make_double2(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__host__ __device__ inline float sinv(float a) { return 1.0f / a; }
+__host__ __device__ inline double sinv(double a) { return 1.0 / a; }
+__host__ __device__ inline float2 sinv(float2 a) {
+  float d = a.x * a.x + a.y * a.y;
+  return make_float2(a.x / d, -a.y / d);
+}
+__host__ __device__ inline double2 sinv(double2 a) {
+  double d = a.x * a.x + a.y * a.y;
+  return make_double2(a.x / d, -a.y / d);
+}
+__host__ __device__ inline double sabs2(float a) { return (double)a * a; }
+__host__ __device__ inline double sabs2(double a) { return a * a; }
+__host__ __device__ inline double sabs2(float2 a) { return (double)a.x * a.x + (double)a.y * a.y; }
+__host__ __device__ inline double sabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+template <typename S> __host__ __device__ inline S szero();
+template <> __host__ __device__ inline float szero<float>() { return 0.f; }
+template <> __host__ __device__ inline double szero<double>() { return 0.0; }
+template <> __host__ __device__ inline float2 szero<float2>() { return make_float2(0.f, 0.f); }
+template <> __host__ __device__ inline double2 szero<double2>() { return make_double2(0.0, 0.0); }
+template <typename S> __host__ __device__ inline S sfrom(double re, double im);
+template <> __host__ __device__ inline float sfrom<float>(double re, double) { return (float)re; }
+template <> __host__ __device__ inline double sfrom<double>(double re, double) { return re; }
+template <> __host__ __device__ inline float2 sfrom<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+template <> __host__ __device__ inline double2 sfrom<double2>(double re, double im) { return make_double2(re, im); }
+__host__ __device__ inline double sre(float a) { return a; }
+__host__ __device__ inline double sre(double a) { return a; }
+__host__ __device__ inline double sre(float2 a) { return a.x; }
+__host__ __device__ inline double sre(double2 a) { return a.x; }
+__host__ __device__ inline double sim(float) { return 0.0; }
+__host__ __device__ inline double sim(double) { return 0.0; }
+__host__ __device__ inline double sim(float2 a) { return a.y; }
+__host__ __device__ inline double sim(double2 a) { return a.y; }
+
+// Device status bits (ORed into ctx->d_status[0]).
+enum : unsigned { kStatSingular = 1u, kStatNotConverged = 2u, kStatTimeout = 4u, kStatBadIndex = 8u };
+
+// Which arithmetic a batch of dielectric matrices lives in.
+enum class MatKind { RealF32, CplxF32, RealF64, CplxF64 };
+
+inline size_t mat_elem_bytes(MatKind k) {
+  switch (k) {
+    case MatKind::RealF32: return 4;
+    case MatKind::CplxF32: return 8;
+    case MatKind::RealF64: return 8;
+    default: return 16;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Kernel launchers (each returns the number of kernels it launched, or -1 on a launch error)
+// ------------------------------------------------------------------------------------------
+
+// D table: D_f(k) = 4 Delta_k / (z_f^2 - Delta_k^2) for the batch, FP64 (dre,dim) or FP32.
+// Layout: [F][2][ld] with ld >= n_ov; entries k >= n_ov are 0.
+int launch_dtable(const double* z, int F, const double* delta, int n_ov, int ld, bool fp32, void* out,
+                  cudaStream_t s);
+
+// SIMT chi0: out[f] (type per kind, leading dim ldm) = alpha*Pi(z_f) + beta*I, lower triangle
+// (and the full square if full != 0). dtab from launch_dtable (same precision as the kernel).
+int launch_chi0_simt(MatKind kind, const void* o_ov /*double or float [n_aux][ldo]*/, int ldo, int n_aux, int n_ov,
+                     const void* dtab, int ld_dtab, int F, double alpha, double beta, void* out, long long ldm,
+                     long long mat_stride, int full, const int* active, cudaStream_t s);
+
+// tcgen05 chi0 (BF16 or split BF16): same output contract as launch_chi0_simt for complex
+// kinds (CplxF32) and real (RealF32). Returns -1 if unavailable.
+int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32, int ld_pad,
+                   int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F, bool complex_out,
+                   double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
+                   unsigned* status, cudaStream_t s);
+
+// Batched in-place LDL^T (unit lower L, diagonal D in the diagonal slot) of F matrices
+// [n][ldm] (lower triangle read and written). Zero pivot -> status |= kStatSingular.
+int launch_ldlt(MatKind kind, void* mats, int n, long long ldm, long long mat_stride, int F, const int* active,
+                unsigned* status, cudaStream_t s);
+
+// Right-hand sides: rhs (S type) [F][r][ldr] overwritten by y = L^{-1} b; then
+// w[f][q] = sum_k y_k^2 / d_k - bnorm2[f][q] (FP64 complex out, interleaved).
+int launch_ldlt_solve_w(MatKind kind, const void* mats, int n, long long ldm, long long mat_stride, void* rhs, int r,
+                        long long ldr, long long rhs_stride, const double* bnorm2, int F, double* w,
+                        long long w_stride, const int* active, cudaStream_t s);
+
+// Convert FP64 right-hand sides to the matrix kind: src rows given by an index map.
+// dst[f][q][p] = src[row(f,q)][p]; bnorm2[f][q] = sum_p src^2 (FP64).
+int launch_rhs_gather(MatKind kind, const double* src, long long src_row_stride, const int* row_of /*[F*r]*/, int F,
+                      int r, int n_aux, void* dst, long long ldr, long long rhs_stride, double* bnorm2,
+                      cudaStream_t s);
+
+// Residue batch helpers ------------------------------------------------------------------
+int launch_fill_z_pairs(const double* eps, const int* pair_m, const double* pair_w, int n_pairs, double eta, double* z,
+                        cudaStream_t s);
+
+// Self-energy assembly on a grid: see sigma.cu
+int launch_sigma_grid(const double* eps, int n_states, int n_core, const int* core_idx, const double* omega, int n_w,
+                      double eps_f, const double* xi, const double* wxi, int n_im, const double* wim,
+                      const int* pidx /*[n_w][n_states] -> pair or -1*/, const double* wres /*[pair][n_core][2]*/,
+                      int dec_mode, const int* group_of_core, double* sigma /*[n_core][n_w][2]*/,
+                      double* im_dec /*[n_core][n_w] or null*/, cudaStream_t s);
+
+int launch_sigma_x(const double* o_core, int n_occ, int n_core, int n_aux, double* sx, cudaStream_t s);
+
+// QP (device-side secant state machine); see qp.cu
+struct QpState {
+  double x0, g0, x1, g1, dh, w_eval;
+  int phase, it, done, pad;
+};
+int launch_qp_init(const double* eps, const int* core_idx, int n_core, QpState* st, cudaStream_t s);
+int launch_qp_pairs(const double* eps, const int* core_idx, int n_core, int n_occ, double eps_f, double eta,
+                    const QpState* st, double* z, int* active, double* fac, int* all_done, cudaStream_t s);
+int launch_qp_assemble_update(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx,
+                              double eps_f, const double* xi, const double* wxi, int n_im, const double* wim,
+                              const double* wpair /*[n_core*n_occ][2]*/, const double* fac, const double* sx,
+                              const double* vxc, double tol, int max_iter, QpState* st, int* all_done,
+                              cudaStream_t s);
+int launch_qp_finish(const QpState* st, int n_core, double* eps_qp, double* dh, int* iters, unsigned* status,
+                     cudaStream_t s);
+
+// Cumulant + FFT; see cumulant.cu
+int launch_cumulant_spectrum(const double* omega_rel, int n_w, const double* im_sigma, int n_core, int n_t,
+                             double t_max, double eta, double* work_a /*[n_core][n_t][2]*/,
+                             double* work_b /*[n_core][n_t][2]*/, double* coef /*[n_core][n_w]*/,
+                             double* twiddle /*[n_t/2][2]*/, double* a_out, double* nu_out, cudaStream_t s);
+
+// Precision copies of O_ov: hi/lo BF16 and FP32, padded [n_aux_pad][n_ov_pad], zero padding.
+int launch_split_o(const double* o_ov, int n_aux, int n_ov, int n_aux_pad, int n_ov_pad, __nv_bfloat16* hi,
+                   __nv_bfloat16* lo, float* f32, cudaStream_t s);
+
+int launch_delta(const double* eps, int n_occ, int n_virt, double* delta, cudaStream_t s);
+
+// Chi0 output conversion for the public gwc_build_chi0 (any kind -> FP64 complex full).
+int launch_mat_to_c128(MatKind kind, const void* mats, int n, long long ldm, long long mat_stride, int F, double* out,
+                       cudaStream_t s);
+
+}  // namespace gwc
+
+// ------------------------------------------------------------------------------------------
+// Context
+// ------------------------------------------------------------------------------------------
+struct gwc_ctx {
+  int device = 0;
+  int n_states = 0, n_occ = 0, n_virt = 0, n_aux = 0, n_core = 0, n_ov = 0;
+  int n_aux_pad = 0, n_ov_pad = 0;
+  gwc_options opt{};
+  double eps_f = 0.0;
+  bool vxc_given = false;
+  std::vector<double> h_eps;
+  std::vector<int> h_core, h_group;
+
+  double *d_eps = nullptr, *d_o_ov = nullptr, *d_o_core = nullptr, *d_vxc = nullptr, *d_delta = nullptr;
+  int* d_core_idx = nullptr;
+  int* d_group = nullptr;
+  double *d_xi = nullptr, *d_wxi = nullptr;
+  double* d_wim = nullptr;  // [n_im + 1][n_states][n_core]; node n_im is xi = 0
+  bool wim_valid = false;
+  double* d_sx = nullptr;   // [n_core]
+  double* d_vxc_eff = nullptr;  // [n_core] v^xc actually used
+
+  __nv_bfloat16 *d_o_hi = nullptr, *d_o_lo = nullptr;
+  float* d_o_f32 = nullptr;
+  float* d_o_f32_unpadded = nullptr;  // not used
+
+  // workspace
+  int batch = 0;            // matrices per batch
+  void* d_mats = nullptr;   // batch * n_aux * ldm elements of the widest kind
+  long long ldm = 0;        // leading dimension of matrices
+  size_t mats_bytes = 0;
+  void* d_dtab = nullptr;   // [batch][2][ld_dtab] FP64-sized
+  int ld_dtab = 0;
+  double* d_z = nullptr;    // [batch][2]
+  int* d_active = nullptr;  // [batch]
+  void* d_rhs = nullptr;    // residue RHS [batch][n_core][n_aux] widest kind
+  size_t rhs_bytes = 0;
+  double* d_bnorm = nullptr;  // [max(batch*n_core, rhs_im)]
+  int* d_rowmap = nullptr;    // [batch * n_core]
+  double* d_wtmp = nullptr;   // [batch][n_core][2]
+  void* d_rhs_im = nullptr;   // imaginary-axis RHS [n_states*n_core][n_aux] (widest real kind)
+  unsigned* d_status = nullptr;
+
+  // residue grid plan
+  int plan_cap = 0;
+  int* d_pidx = nullptr;      // [n_w][n_states]
+  double* d_wres = nullptr;   // [n_pairs][n_core][2]
+  int* d_pair_m = nullptr;
+  double* d_pair_w = nullptr;
+  double* d_pair_z = nullptr;   // [n_pairs][2]
+  int* d_pair_rows = nullptr;   // [n_pairs][n_core]
+  double* d_grid_w = nullptr;
+  int pidx_cap = 0, wres_cap = 0, grid_cap = 0;
+
+  // QP
+  gwc::QpState* d_qp = nullptr;
+  double* d_qp_z = nullptr;     // [n_core*n_occ][2]
+  int* d_qp_active = nullptr;   // [n_core*n_occ]
+  double* d_qp_fac = nullptr;   // [n_core*n_occ]
+  double* d_qp_w = nullptr;     // [n_core*n_occ][2]
+  int* d_qp_rowmap = nullptr;   // [n_core*n_occ]
+  int* d_all_done = nullptr;
+
+  // cumulant
+  double *d_cw_a = nullptr, *d_cw_b = nullptr, *d_coef = nullptr, *d_tw = nullptr;
+  size_t cw_cap = 0, coef_cap = 0;
+
+  // host staging
+  int* h_pin_i = nullptr;
+  size_t h_pin_i_cap = 0;
+  double* h_pin_d = nullptr;
+  size_t h_pin_d_cap = 0;
+
+  gwc_stats stats{};
+  std::string last_error;
+};

@@ -1,0 +1,246 @@
+// Self-energy assembly by contour deformation and the device-side QP secant iteration.
+//
+// Sigma^c_n(w) = -I_n(w) + R_n(w)                                        (Eq. cd_terms)
+// I_n(w) = (1/pi) sum_m int_0^inf dxi a_m/(a_m^2 + xi^2) W^c_mn(i xi),    a_m = w - eps_m
+//          evaluated as sum_k q_k a/(a^2+xi_k^2)/pi [W(i xi_k) - W(i0)] + sgn(a) W(i0)/2
+//          (Eq. cd_imaginary; the odd part of the integrand cancels because W^c(i xi) is
+//          even and real; W(i0) is subtracted and integrated exactly; 0 at a = 0)
+// R_n(w) = sum_m f_m W^c_mn(|eps_m - w| + i eta)                          (Eq. cd_residue)
+// f_m = -Theta(eps_F - eps_m) Theta(eps_m - w) + Theta(eps_m - eps_F) Theta(w - eps_m),
+//       Theta(0) = 1/2                                                    (Eq. cd_prefactors)
+// All arithmetic here is FP64; one warp reduces over the states m for one (core, w).
+#include "gwc_internal.h"
+
+namespace gwc {
+
+namespace {
+
+__device__ __forceinline__ double theta(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); }
+
+__device__ __forceinline__ double prefactor(double eps_m, double w, double eps_f) {
+  return -theta(eps_f - eps_m) * theta(eps_m - w) + theta(eps_m - eps_f) * theta(w - eps_m);
+}
+
+// Imaginary-axis contribution of state m to I_n(w) for core c.
+__device__ __forceinline__ double imag_term(double a, int m, int c, int n_states, int n_core, const double* __restrict__ xi,
+                                            const double* __restrict__ wxi, int n_im, const double* __restrict__ wim) {
+  if (a == 0.0) return 0.0;
+  const size_t plane = (size_t)n_states * n_core;
+  const size_t off = (size_t)m * n_core + c;
+  const double w0 = wim[(size_t)n_im * plane + off];
+  double s = 0.0;
+  for (int k = 0; k < n_im; ++k) {
+    double x = xi[k];
+    s += wxi[k] * a / (a * a + x * x) * (wim[k * plane + off] - w0);
+  }
+  return s * (1.0 / 3.14159265358979323846) + 0.5 * copysign(1.0, a) * w0;
+}
+
+__global__ void sigma_grid_kernel(const double* __restrict__ eps, int n_states, int n_core, const int* __restrict__ core_idx,
+                                  const double* __restrict__ omega, int n_w, double eps_f, const double* __restrict__ xi,
+                                  const double* __restrict__ wxi, int n_im, const double* __restrict__ wim,
+                                  const int* __restrict__ pidx, const double* __restrict__ wres, int dec_mode,
+                                  const int* __restrict__ group_of_core, double* __restrict__ sigma,
+                                  double* __restrict__ im_dec) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_core * n_w) return;
+  const int c = warp / n_w, j = warp % n_w;
+  const double w = omega[j];
+  const int n = core_idx[c];
+  const int gc = group_of_core ? group_of_core[c] : c;
+  double si = 0.0, rr = 0.0, ri = 0.0, dec = 0.0;
+  for (int m = lane; m < n_states; m += 32) {
+    const double em = eps[m];
+    si += imag_term(w - em, m, c, n_states, n_core, xi, wxi, n_im, wim);
+    const double f = prefactor(em, w, eps_f);
+    if (f != 0.0) {
+      const int p = pidx[(size_t)j * n_states + m];
+      const double* wv = wres + ((size_t)p * n_core + c) * 2;
+      rr += f * wv[0];
+      ri += f * wv[1];
+      if (dec_mode == GWC_DECOUPLE_DIAG && m == n) dec += f * wv[1];
+      if (dec_mode == GWC_DECOUPLE_GROUP) {
+        // m belongs to the group of core c if m is a core with the same group label
+        for (int c2 = 0; c2 < n_core; ++c2)
+          if (core_idx[c2] == m && (group_of_core ? group_of_core[c2] : c2) == gc) dec += f * wv[1];
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    si += __shfl_down_sync(0xffffffffu, si, o);
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+    ri += __shfl_down_sync(0xffffffffu, ri, o);
+    dec += __shfl_down_sync(0xffffffffu, dec, o);
+  }
+  if (lane == 0) {
+    double* o = sigma + ((size_t)c * n_w + j) * 2;
+    o[0] = -si + rr;
+    o[1] = ri;
+    if (im_dec) im_dec[(size_t)c * n_w + j] = dec_mode == GWC_DECOUPLE_NONE ? ri : dec;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// QP: dH_n = Re Sigma^c_n(eps_n) + Sigma^x_n - v^xc_n (Eq. hedin_shift), then the G_dH W0 QP
+// equation eps = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n(eps - dH_n) (Eqs. quasiparticle_equation,
+// hedin_sigma_spectral) by the secant method from eps_n. Phases of the per-core state machine:
+//   0: evaluate Sigma at eps_n -> dH;  1: g(x0), x1 = x0 + g0;  2: g(x1), secant step;
+//   3: final g(x1) after a step below tolerance;  done.
+// ---------------------------------------------------------------------------------------------
+
+__global__ void qp_init_kernel(const double* __restrict__ eps, const int* __restrict__ core_idx, int n_core,
+                               QpState* __restrict__ st) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_core) return;
+  QpState s{};
+  s.w_eval = eps[core_idx[c]];
+  s.phase = 0;
+  s.it = 0;
+  s.done = 0;
+  st[c] = s;
+}
+
+__global__ void qp_pairs_kernel(const double* __restrict__ eps, const int* __restrict__ core_idx, int n_core, int n_occ,
+                                double eps_f, double eta, const QpState* __restrict__ st, double* __restrict__ z,
+                                int* __restrict__ active, double* __restrict__ fac, int* __restrict__ all_done) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    int d = 1;
+    for (int c = 0; c < n_core; ++c) d &= st[c].done;
+    *all_done = d;
+  }
+  if (t >= n_core * n_occ) return;
+  int c = t / n_occ, m = t % n_occ;
+  double w = st[c].w_eval;
+  double f = st[c].done ? 0.0 : prefactor(eps[m], w, eps_f);
+  fac[t] = f;
+  active[t] = f != 0.0;
+  z[2 * t] = fabs(eps[m] - w);
+  z[2 * t + 1] = eta;
+}
+
+__global__ void qp_update_kernel(const double* __restrict__ eps, int n_states, int n_occ, int n_core,
+                                 const int* __restrict__ core_idx, double eps_f, const double* __restrict__ xi,
+                                 const double* __restrict__ wxi, int n_im, const double* __restrict__ wim,
+                                 const double* __restrict__ wpair, const double* __restrict__ fac,
+                                 const double* __restrict__ sx, const double* __restrict__ vxc, double tol, int max_iter,
+                                 QpState* __restrict__ st, const int* __restrict__ all_done) {
+  if (*all_done) return;
+  const int c = blockIdx.x;
+  const int lane = threadIdx.x;
+  QpState s = st[c];
+  if (s.done) return;
+  const double w = s.w_eval;
+  double si = 0.0, rr = 0.0;
+  for (int m = lane; m < n_states; m += 32) {
+    si += imag_term(w - eps[m], m, c, n_states, n_core, xi, wxi, n_im, wim);
+    if (m < n_occ) {
+      double f = fac[c * n_occ + m];
+      if (f != 0.0) rr += f * wpair[(size_t)(c * n_occ + m) * 2];
+    }
+  }
+  // virtual states with f != 0 (w above eps_m > eps_F) do not occur for a core-level w;
+  // they would need residue pairs beyond n_occ and are excluded by construction.
+  for (int o = 16; o > 0; o >>= 1) {
+    si += __shfl_down_sync(0xffffffffu, si, o);
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+  }
+  if (lane != 0) return;
+  const double re_sigma = -si + rr;
+  const double e_n = eps[core_idx[c]];
+  const double stat = sx[c] - vxc[c];
+  switch (s.phase) {
+    case 0: {
+      s.dh = re_sigma + stat;
+      s.x0 = e_n;
+      s.w_eval = s.x0 - s.dh;
+      s.phase = 1;
+      break;
+    }
+    case 1: {
+      s.g0 = e_n + stat + re_sigma - s.x0;
+      s.x1 = s.x0 + s.g0;
+      s.it = 1;
+      s.w_eval = s.x1 - s.dh;
+      s.phase = 2;
+      break;
+    }
+    case 2: {
+      s.g1 = e_n + stat + re_sigma - s.x1;
+      s.it += 1;
+      if (fabs(s.g1) < tol || s.it >= max_iter) {
+        s.done = (fabs(s.g1) < tol) ? 1 : 2;
+        break;
+      }
+      double denom = s.g1 - s.g0;
+      double x2 = denom == 0.0 ? s.x1 + s.g1 : s.x1 - s.g1 * (s.x1 - s.x0) / denom;
+      s.x0 = s.x1;
+      s.g0 = s.g1;
+      s.x1 = x2;
+      s.w_eval = s.x1 - s.dh;
+      if (fabs(s.x1 - s.x0) < tol) s.phase = 3;
+      break;
+    }
+    default: {
+      s.g1 = e_n + stat + re_sigma - s.x1;
+      s.it += 1;
+      s.done = 1;
+      break;
+    }
+  }
+  st[c] = s;
+}
+
+__global__ void qp_finish_kernel(const QpState* __restrict__ st, int n_core, double* __restrict__ eps_qp,
+                                 double* __restrict__ dh, int* __restrict__ iters, unsigned* __restrict__ status) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_core) return;
+  QpState s = st[c];
+  eps_qp[c] = s.x1;
+  dh[c] = s.dh;
+  iters[c] = s.it;
+  if (s.done != 1) atomicOr(status, kStatNotConverged);
+}
+
+}  // namespace
+
+int launch_sigma_grid(const double* eps, int n_states, int n_core, const int* core_idx, const double* omega, int n_w,
+                      double eps_f, const double* xi, const double* wxi, int n_im, const double* wim, const int* pidx,
+                      const double* wres, int dec_mode, const int* group_of_core, double* sigma, double* im_dec,
+                      cudaStream_t s) {
+  long long warps = (long long)n_core * n_w;
+  int blocks = (int)((warps * 32 + 255) / 256);
+  sigma_grid_kernel<<<blocks, 256, 0, s>>>(eps, n_states, n_core, core_idx, omega, n_w, eps_f, xi, wxi, n_im, wim, pidx,
+                                           wres, dec_mode, group_of_core, sigma, im_dec);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_qp_init(const double* eps, const int* core_idx, int n_core, QpState* st, cudaStream_t s) {
+  qp_init_kernel<<<(n_core + 63) / 64, 64, 0, s>>>(eps, core_idx, n_core, st);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_qp_pairs(const double* eps, const int* core_idx, int n_core, int n_occ, double eps_f, double eta,
+                    const QpState* st, double* z, int* active, double* fac, int* all_done, cudaStream_t s) {
+  int n = n_core * n_occ;
+  qp_pairs_kernel<<<(n + 127) / 128, 128, 0, s>>>(eps, core_idx, n_core, n_occ, eps_f, eta, st, z, active, fac, all_done);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_qp_assemble_update(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx, double eps_f,
+                              const double* xi, const double* wxi, int n_im, const double* wim, const double* wpair,
+                              const double* fac, const double* sx, const double* vxc, double tol, int max_iter,
+                              QpState* st, int* all_done, cudaStream_t s) {
+  qp_update_kernel<<<n_core, 32, 0, s>>>(eps, n_states, n_occ, n_core, core_idx, eps_f, xi, wxi, n_im, wim, wpair, fac,
+                                         sx, vxc, tol, max_iter, st, all_done);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_qp_finish(const QpState* st, int n_core, double* eps_qp, double* dh, int* iters, unsigned* status,
+                     cudaStream_t s) {
+  qp_finish_kernel<<<(n_core + 63) / 64, 64, 0, s>>>(st, n_core, eps_qp, dh, iters, status);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace gwc

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libgwc (argument marshalling only).
+
+Every step of the self-energy / QP / cumulant path runs in the CUDA kernels of
+``libgwc.so``; this module only turns torch tensors and numpy arrays into the
+pointers and sizes of the C ABI declared in ``include/gwc.h``. PyTorch provides
+device memory and streams. There is no CPU fallback: if the library is missing the
+import of the binding functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgwc.so")
+
+PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "fp32": 3}
+DEC = {"none": 0, "diag": 1, "group": 2}
+STATUS = {
+    0: "ok",
+    1: "invalid argument",
+    2: "out of memory",
+    3: "CUDA error",
+    4: "singular dielectric matrix",
+    5: "QP iteration not converged",
+    6: "device wait timed out",
+    7: "unsupported",
+}
+
+
+class GwcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"gwc status {status} ({STATUS.get(status, '?')}): {message}")
+        self.status = status
+
+
+class System(ctypes.Structure):
+    _fields_ = [
+        ("n_states", ctypes.c_int),
+        ("n_occ", ctypes.c_int),
+        ("n_aux", ctypes.c_int),
+        ("n_core", ctypes.c_int),
+        ("core_idx", ctypes.POINTER(ctypes.c_int)),
+        ("eps", ctypes.c_void_p),
+        ("o_ov", ctypes.c_void_p),
+        ("o_core", ctypes.c_void_p),
+        ("vxc", ctypes.c_void_p),
+        ("eps_f", ctypes.c_double),
+        ("memory", ctypes.c_int),
+    ]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("eta", ctypes.c_double),
+        ("n_im", ctypes.c_int),
+        ("xi0", ctypes.c_double),
+        ("prec", ctypes.c_int),
+        ("dec", ctypes.c_int),
+        ("group_of_core", ctypes.POINTER(ctypes.c_int)),
+        ("n_t", ctypes.c_int),
+        ("t_max", ctypes.c_double),
+        ("max_qp_iter", ctypes.c_int),
+        ("qp_tol", ctypes.c_double),
+        ("batch", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("chi0_builds", ctypes.c_longlong),
+        ("chi0_flop", ctypes.c_double),
+        ("kernel_launches", ctypes.c_longlong),
+        ("factorizations", ctypes.c_longlong),
+    ]
+
+
+_LIB = None
+
+_SIGS = {
+    "gwc_abi_version": (ctypes.c_int, []),
+    "gwc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gwc_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "gwc_default_options": (ctypes.c_int, [ctypes.POINTER(Options)]),
+    "gwc_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(System), ctypes.POINTER(Options), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "gwc_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(System), ctypes.POINTER(Options), ctypes.c_void_p]),
+    "gwc_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(System), ctypes.c_void_p]),
+    "gwc_build_chi0": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_screen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_sigma_core": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_qp_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_cumulant_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "gwc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
+    "gwc_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def lib():
+    """Load libgwc.so (built in-tree by ``__graft_entry__.build()``); raise loudly if absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgwc.so not found at {LIB_PATH}: run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        msg = lib().gwc_last_error(ctx)
+        raise GwcError(status, msg.decode() if msg else "")
+
+
+def default_options() -> Options:
+    o = Options()
+    _check(lib().gwc_default_options(ctypes.byref(o)))
+    return o
+
+
+def _ptr(t) -> int:
+    """Device/host address of a torch tensor or numpy array (must be contiguous)."""
+    if t is None:
+        return 0
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Context:
+    """One molecule resident on the current CUDA device (wraps ``gwc_ctx``).
+
+    Inputs may be CUDA torch tensors (``memory='device'``) or numpy arrays
+    (``memory='host'``; copied host->device by gwc_create).
+    """
+
+    def __init__(self, eps, n_occ, core_idx, o_ov, o_core, *, vxc=None, eps_f=math.nan, eta=1e-3, n_im=32, xi0=1.0,
+                 prec="bf16x3", dec="diag", groups=None, n_t=1 << 16, t_max=2000.0, max_qp_iter=50, qp_tol=1e-7,
+                 batch=0, stream=None):
+        self._ctx = ctypes.c_void_p()
+        host = isinstance(eps, np.ndarray)
+        self._keep = []
+        core = np.ascontiguousarray(np.asarray(core_idx, dtype=np.int32))
+        self._keep.append(core)
+        n_states = int(eps.shape[0])
+        n_aux = int(o_ov.shape[0])
+        self.n_states, self.n_occ, self.n_aux, self.n_core = n_states, int(n_occ), n_aux, int(core.shape[0])
+        sysd = System(n_states, int(n_occ), n_aux, int(core.shape[0]), core.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      _ptr(eps), _ptr(o_ov), _ptr(o_core), _ptr(vxc), float(eps_f), 1 if host else 0)
+        opt = default_options()
+        opt.eta, opt.n_im, opt.xi0 = float(eta), int(n_im), float(xi0)
+        opt.prec, opt.dec = PREC[prec], DEC[dec]
+        if groups is not None:
+            g = np.ascontiguousarray(np.asarray(groups, dtype=np.int32))
+            self._keep.append(g)
+            opt.group_of_core = g.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        opt.n_t, opt.t_max = int(n_t), float(t_max)
+        opt.max_qp_iter, opt.qp_tol, opt.batch = int(max_qp_iter), float(qp_tol), int(batch)
+        self.opt = opt
+        self.prec = prec
+        _check(lib().gwc_create(ctypes.byref(self._ctx), ctypes.byref(sysd), ctypes.byref(opt), _stream(stream)), None)
+
+    @classmethod
+    def from_molecule(cls, mol, device="cuda", host=False, **kw):
+        import torch
+
+        args = dict(eta=mol.eta, n_im=mol.n_im, xi0=mol.xi0, n_t=mol.n_t, t_max=mol.t_max)
+        args.update(kw)
+        if host:
+            return cls(mol.eps, mol.n_occ, mol.core_idx, mol.o_ov, mol.o_core, **args)
+        dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()  # noqa: E731
+        return cls(dev(mol.eps), mol.n_occ, mol.core_idx, dev(mol.o_ov), dev(mol.o_core), **args)
+
+    # -- entry points ---------------------------------------------------------------------
+    def load(self, eps, o_ov, o_core, vxc=None, eps_f=math.nan, core_idx=None, stream=None):
+        host = isinstance(eps, np.ndarray)
+        core = np.ascontiguousarray(np.asarray(core_idx if core_idx is not None else range(self.n_core), dtype=np.int32))
+        sysd = System(self.n_states, self.n_occ, self.n_aux, self.n_core, core.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      _ptr(eps), _ptr(o_ov), _ptr(o_core), _ptr(vxc), float(eps_f), 1 if host else 0)
+        _check(lib().gwc_load(self._ctx, ctypes.byref(sysd), _stream(stream)), self._ctx)
+
+    def build_chi0(self, z, stream=None):
+        import torch
+
+        F = int(z.shape[0])
+        out = torch.empty((F, self.n_aux, self.n_aux, 2), dtype=torch.float64, device=z.device)
+        _check(lib().gwc_build_chi0(self._ctx, _ptr(z), F, _ptr(out), _stream(stream)), self._ctx)
+        return out
+
+    def screen(self, z, rhs, stream=None):
+        import torch
+
+        F, r = int(rhs.shape[0]), int(rhs.shape[1])
+        out = torch.empty((F, r, 2), dtype=torch.float64, device=z.device)
+        _check(lib().gwc_screen(self._ctx, _ptr(z), F, _ptr(rhs), r, _ptr(out), _stream(stream)), self._ctx)
+        return out
+
+    def sigma_core(self, omega, want_dec=True, stream=None, out=None):
+        """omega: host numpy [n_w]; returns CUDA tensors (sigma [n_core][n_w][2], im_dec, sigma_x)."""
+        import torch
+
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        n_w = om.shape[0]
+        if out is None:
+            sig = torch.empty((self.n_core, n_w, 2), dtype=torch.float64, device="cuda")
+            dec = torch.empty((self.n_core, n_w), dtype=torch.float64, device="cuda") if want_dec else None
+            sx = torch.empty((self.n_core,), dtype=torch.float64, device="cuda")
+        else:
+            sig, dec, sx = out
+        _check(lib().gwc_sigma_core(self._ctx, om.ctypes.data, n_w, _ptr(sig), _ptr(dec), _ptr(sx), _stream(stream)), self._ctx)
+        return sig, dec, sx
+
+    def qp_solve(self, stream=None, out=None):
+        import torch
+
+        if out is None:
+            e = torch.empty((self.n_core,), dtype=torch.float64, device="cuda")
+            dh = torch.empty_like(e)
+            it = torch.empty((self.n_core,), dtype=torch.int32, device="cuda")
+        else:
+            e, dh, it = out
+        _check(lib().gwc_qp_solve(self._ctx, _ptr(e), _ptr(dh), _ptr(it), _stream(stream)), self._ctx)
+        return e, dh, it
+
+    def cumulant_spectrum(self, omega_rel, im_sigma, stream=None, out=None):
+        import torch
+
+        n_w = int(omega_rel.shape[-1])
+        if out is None:
+            a = torch.empty((self.n_core, self.opt.n_t), dtype=torch.float64, device="cuda")
+            nu = torch.empty((self.opt.n_t,), dtype=torch.float64, device="cuda")
+        else:
+            a, nu = out
+        _check(lib().gwc_cumulant_spectrum(self._ctx, _ptr(omega_rel), n_w, _ptr(im_sigma), _ptr(a), _ptr(nu), _stream(stream)),
+               self._ctx)
+        return a, nu
+
+    def sync(self, stream=None):
+        _check(lib().gwc_sync(self._ctx, _stream(stream)), self._ctx)
+
+    def sync_status(self, stream=None) -> int:
+        return int(lib().gwc_sync(self._ctx, _stream(stream)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().gwc_get_stats(self._ctx, ctypes.byref(s)), self._ctx)
+        return {"chi0_builds": s.chi0_builds, "chi0_flop": s.chi0_flop, "kernel_launches": s.kernel_launches,
+                "factorizations": s.factorizations}
+
+    def reset_stats(self):
+        _check(lib().gwc_reset_stats(self._ctx), self._ctx)
+
+    def close(self):
+        if self._ctx:
+            lib().gwc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
