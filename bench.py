@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Throughput of the GW+C core-level hot path on GB300: Sigma_c(w) points/s + chi0 TFLOP/s.
+
+One step = one pass of the whole path over the benzene-sized synthetic molecule
+(300 states, 21 occupied incl. six 1s cores, 1100 auxiliary functions, 800 real frequencies):
+residency of the inputs (precision copies of O), the imaginary-axis W table, every residue
+chi0 build / dielectric factorisation / contraction, the self-energy of all cores on the grid,
+the device QP iteration, and one cumulant spectrum per core (n_t = 2^16).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|fp32|fp64|bf16]
+  python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample, same metric
+
+Under torchrun every rank runs an independent replica on its own GPU (the path needs no
+exchange between GPUs); value = points of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "core Sigma_c(w) points/s (whole GW+C step) + chi0 TFLOP/s"
+UNIT = "points/s"
+HARTREE_EV = 27.211386245988
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gwc", choices=["gwc", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp32", "fp64"])
+    ap.add_argument("--workload", default="benzene", choices=["benzene", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=0, help="frequencies per internal batch (0: from free memory)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(name):
+    from paper_2412_17132_gb300 import synth
+
+    return synth.benzene() if name == "benzene" else synth.tiny()
+
+
+def describe(mol):
+    return (f"{mol.name}-sized synthetic molecule: N_states={mol.n_states}, N_occ={mol.n_occ}, N_core={mol.n_core}, "
+            f"N_aux={mol.n_aux}, N_ov={mol.n_occ * mol.n_virt}, {mol.omega.size} real omega over 30 eV, "
+            f"{mol.n_im} imaginary nodes, eta={mol.eta} Ha, cumulant n_t={mol.n_t}, t_max={mol.t_max}")
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [l.split(",") for l in self.lines if l]
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ------------------------------------------------------------------------------------------
+def oracle_sample(mol, n_points=2, qp_builds=0):
+    """Time the FP64 oracle on a bounded sample and extrapolate to the whole step.
+
+    Sample: the imaginary-axis W table (n_im + 1 real builds, all states x cores) plus the
+    self-energy of all cores at n_points grid frequencies. The full step is extrapolated as
+    T_table + T_build * (residue builds of the grid + of the QP), where T_build is the measured
+    time per residue build (chi0 + LU solve with N_core right-hand sides).
+    """
+    import numpy as np
+
+    from oracle import gwc_oracle as G
+
+    s = G.System.from_molecule(mol)
+    t0 = time.perf_counter()
+    s.w_imag_table()
+    t_table = time.perf_counter() - t0
+    idx = np.linspace(0, mol.omega.size - 1, n_points).round().astype(int)
+    builds = 0
+    t1 = time.perf_counter()
+    for j in idx:
+        w = float(mol.omega[j])
+        builds += sum(1 for m in range(mol.n_states) if G.residue_prefactor(mol.eps[m], w, s.eps_f) != 0.0)
+        s.sigma_c(w)
+    t_pts = time.perf_counter() - t1
+    t_build = t_pts / max(1, builds)
+    grid_builds = sum(
+        1 for w in mol.omega for m in range(mol.n_states) if G.residue_prefactor(mol.eps[m], float(w), s.eps_f) != 0.0)
+    t_full = t_table + t_build * (grid_builds + qp_builds)
+    points = mol.n_core * mol.omega.size
+    return {
+        "value": points / t_full,
+        "t_full_s": t_full,
+        "t_table_s": t_table,
+        "t_build_s": t_build,
+        "measured_s": t_table + t_pts,
+        "sample": (f"FP64 oracle: imaginary-axis W table ({mol.n_im}+1 nodes) + Sigma of all {mol.n_core} cores at "
+                   f"{n_points} of {mol.omega.size} grid points ({builds} residue builds); extrapolated to the whole step "
+                   f"({grid_builds} grid + {qp_builds} QP residue builds) as T_table + builds * T_build"),
+    }
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    mol = make_workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(mol, n_points=1)
+    vals, times = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle_sample(mol, n_points=1)
+        times.append(time.perf_counter() - t0)
+        vals.append(r["value"])
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(mol), "implementation": "FP64 CPU oracle (numpy/LAPACK), bounded sample per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": r["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def load_traffic(kernel, workload, units_per_launch):
+    """DRAM bytes per launch from the committed ncu capture, scaled to this run's units per launch
+    (traffic of these kernels grows in proportion to the matrices / frequencies a launch processes)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p) or not units_per_launch:
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if e and e.get("workload") == workload and e.get("source_unchanged", True):
+        return e["bytes_per_unit"] * units_per_launch
+    return None
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2412_17132_gb300 import gwc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    mol = make_workload(args.workload)
+    nc, nw = mol.n_core, mol.omega.size
+    dev = torch.device("cuda", local)
+    eps_d = torch.as_tensor(mol.eps, device=dev)
+    oov_d = torch.as_tensor(mol.o_ov, device=dev)
+    ocore_d = torch.as_tensor(mol.o_core, device=dev)
+    eps_h = torch.as_tensor(mol.eps).pin_memory()
+    oov_h = torch.as_tensor(mol.o_ov).pin_memory()
+    ocore_h = torch.as_tensor(mol.o_core).pin_memory()
+    w_rel = torch.as_tensor(mol.omega[None, :] - mol.eps[mol.core_idx][:, None], device=dev).contiguous()
+    ctx = gwc.Context(eps_d, mol.n_occ, mol.core_idx, oov_d, ocore_d, prec=args.prec, eta=mol.eta, n_im=mol.n_im,
+                      xi0=mol.xi0, n_t=mol.n_t, t_max=mol.t_max, batch=args.batch, profile=True)
+    sig = torch.empty((nc, nw, 2), dtype=torch.float64, device=dev)
+    dec = torch.empty((nc, nw), dtype=torch.float64, device=dev)
+    sx = torch.empty((nc,), dtype=torch.float64, device=dev)
+    eqp = torch.empty((nc,), dtype=torch.float64, device=dev)
+    dh = torch.empty_like(eqp)
+    its = torch.empty((nc,), dtype=torch.int32, device=dev)
+    a = torch.empty((nc, mol.n_t), dtype=torch.float64, device=dev)
+    nu = torch.empty((mol.n_t,), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > L2 (129 MB)
+    sig_h = torch.empty(sig.shape, dtype=sig.dtype).pin_memory()
+    eqp_h = torch.empty(eqp.shape, dtype=eqp.dtype).pin_memory()
+    a_h = torch.empty(a.shape, dtype=a.dtype).pin_memory()
+
+    def step(host=False):
+        if host:
+            ctx.load(eps_h.numpy(), oov_h.numpy(), ocore_h.numpy(), core_idx=mol.core_idx)
+        else:
+            ctx.load(eps_d, oov_d, ocore_d, core_idx=mol.core_idx)
+        ctx.sigma_core(mol.omega, out=(sig, dec, sx))
+        ctx.qp_solve(out=(eqp, dh, its))
+        ctx.cumulant_spectrum(w_rel, dec, out=(a, nu))
+        if host:
+            sig_h.copy_(sig, non_blocking=True)
+            eqp_h.copy_(eqp, non_blocking=True)
+            a_h.copy_(a, non_blocking=True)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        step()
+    ctx.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+
+    # ---- timed region: device-resident inputs -------------------------------------------------
+    ctx.reset_stats()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clk = clocks.stop()
+    ctx.sync()
+    st = ctx.stats()
+    total_ms = sum(times)
+    if pg is not None:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    points = nc * nw * args.steps * ws
+    value = points / (total_ms * 1e-3)
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region ---------------
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(host=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms = e0.elapsed_time(e1)
+        if pg is not None:
+            t = torch.tensor([e2e_ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        h2d = mol.eps.nbytes + mol.o_ov.nbytes + mol.o_core.nbytes
+        d2h = sig.numel() * 8 + eqp.numel() * 8 + a.numel() * 8
+        e2e = {"value": nc * nw * args.steps * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    out = None
+    if rank == 0:
+        peaks, src = load_peaks()
+        chi0_t = st["chi0_ms"] * 1e-3
+        fac_t = st["factor_ms"] * 1e-3
+        chi0_alg = st["chi0_flop"] / chi0_t if chi0_t > 0 else 0.0
+        mma_mult = {"bf16x3": 3.0, "bf16": 1.0}.get(args.prec, 0.0)
+        if chi0_t >= fac_t and args.prec in ("bf16x3", "bf16"):
+            peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            roof = {"kernel": "chi0_tc_kernel (tcgen05 " + args.prec + ")", "bound": "tensor", "achieved": chi0_alg / 1e12,
+                    "peak": peak, "unit": "TFLOP/s", "frac": chi0_alg / 1e12 / peak,
+                    "traffic": load_traffic("chi0_tc_kernel", mol.name, st["chi0_builds"] / max(1, st["chi0_launches"])),
+                    "mma_frac": mma_mult * 2 * chi0_alg / 1e12 / peak,
+                    "peak_source": f"{src} bf16 sustained (kernel timed inside a long step)",
+                    "share_of_step": chi0_t / (total_ms * 1e-3 / ws)}
+        else:
+            clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+            fp32_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+            fac_alg = st["factor_flop"] / fac_t if fac_t > 0 else 0.0
+            peak = fp32_peak if args.prec != "fp64" else 1.2
+            roof = {"kernel": "ldlt_kernel (batched complex-symmetric LDL^T, " + ("FP64" if args.prec == "fp64" else "FP32") + ")",
+                    "bound": "alu", "achieved": fac_alg / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": fac_alg / 1e12 / peak,
+                    "traffic": load_traffic("ldlt_kernel", mol.name, st["factorizations"] / max(1, st["factor_launches"])),
+                    "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 flop x max SM clock" if args.prec != "fp64"
+                                    else "FP64 FMA loop measured on this GB300 (1.20 TFLOP/s)"),
+                    "share_of_step": fac_t / (total_ms * 1e-3 / ws)}
+        lat = sorted(times)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16x3": "bf16x3+f32+f64", "bf16": "bf16+f32+f64", "fp32": "f32+f64", "fp64": "f64"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": describe(mol), "precision": args.prec, "parallelism": f"replicas x{ws}",
+                       "l2": "256 MB written between timed steps (L2 flushed)", "full_sigma": "all cores, all grid points",
+                       "qp": "G_dH W0 secant on device", "spectrum": "decoupled, one per core"},
+            "roofline": roof,
+            "chi0_tflops": {"algorithmic": chi0_alg / 1e12, "gemm_equivalent": 2 * chi0_alg / 1e12,
+                            "mma_executed": mma_mult * 2 * chi0_alg / 1e12 if mma_mult else None,
+                            "note": "algorithmic = lower triangle, N_aux(N_aux+1) N_ov flop per real part"},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                           "per_step": times},
+            "kernel_time_share": {"chi0": st["chi0_ms"] / total_ms, "factor": st["factor_ms"] / total_ms,
+                                  "solve": st["solve_ms"] / total_ms},
+            "gpu_launches": int(st["kernel_launches"]),
+            "clocks": clk,
+            "e2e": e2e,
+            "qp": {"eps_qp_Ha": eqp.cpu().tolist(), "dH_Ha": dh.cpu().tolist(), "iters": its.cpu().tolist()},
+        }
+    ctx.close()
+
+    # ---- accuracy vs the plain FP64 GPU path (QP) and its points/s on a subset -------------------
+    if rank == 0 and not args.no_fp64_check and args.prec != "fp64":
+        c64 = gwc.Context(eps_d, mol.n_occ, mol.core_idx, oov_d, ocore_d, prec="fp64", eta=mol.eta, n_im=mol.n_im,
+                          xi0=mol.xi0, n_t=mol.n_t, t_max=mol.t_max)
+        e64, dh64, _ = c64.qp_solve()
+        sub = mol.omega[np.linspace(0, nw - 1, 8).round().astype(int)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s64, _, _ = c64.sigma_core(sub)
+        c64.sync()
+        t64 = time.perf_counter() - t0
+        sig_sub = sig[:, np.linspace(0, nw - 1, 8).round().astype(int), :]
+        out["vs_fp64_gpu"] = {
+            "qp_max_abs_err_eV": float((eqp - e64).abs().max()) * HARTREE_EV,
+            "sigma_max_abs_err_Ha_at_8_points": float((sig_sub - s64).abs().max()),
+            "fp64_path_points_per_s": nc * sub.size / t64,
+            "fp64_path_sample": f"Sigma of all cores at 8 grid points (W table cached), FP64 chi0 + FP64 LDL^T",
+        }
+        c64.close()
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        qp_builds = int(sum(int(i) + 1 for i in out["qp"]["iters"])) * mol.n_occ
+        r = oracle_sample(mol, n_points=2, qp_builds=qp_builds)
+        out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                               "sample": r["sample"], "measured_s": r["measured_s"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -93,6 +93,8 @@ typedef struct {
   int max_qp_iter;       /* secant iterations, 2..200                                          */
   double qp_tol;         /* secant tolerance on the QP residual (Ha), > 0                     */
   int batch;             /* frequencies per internal batch (0: chosen from free memory)       */
+  int profile;           /* nonzero: time the chi0, factorisation and solve kernels with CUDA
+                            events on the launching stream (accumulated in gwc_stats)          */
 } gwc_options;
 
 typedef struct {
@@ -100,12 +102,19 @@ typedef struct {
   double chi0_flop;          /* algorithmic chi0 flop: lower triangle, N_aux(N_aux+1) N_ov per part */
   long long kernel_launches; /* library kernels launched since gwc_create / gwc_reset_stats     */
   long long factorizations;  /* dielectric factorisations launched                              */
+  long long chi0_launches;   /* chi0 kernel launches (profile mode)                               */
+  double chi0_ms;            /* summed device time of the chi0 kernels (profile mode)             */
+  long long factor_launches; /* factorisation kernel launches (profile mode)                      */
+  double factor_ms;          /* summed device time of the factorisation kernels (profile mode)    */
+  double factor_flop;        /* algorithmic factorisation flop: n^3/3 multiply-adds x 2 (x4 complex) */
+  long long solve_launches;  /* contraction (forward substitution) launches (profile mode)        */
+  double solve_ms;           /* summed device time of the contraction kernels (profile mode)      */
 } gwc_stats;
 
 typedef struct gwc_ctx gwc_ctx;
 
 /* Fills o with the defaults: eta 1e-3, n_im 32, xi0 1, BF16X3, DIAG, n_t 2^16, t_max 2000,
- * max_qp_iter 50, qp_tol 1e-7, batch 0. */
+ * max_qp_iter 50, qp_tol 1e-7, batch 0, profile 0. */
 gwc_status gwc_default_options(gwc_options* o);
 
 /* Device bytes a context of this shape allocates (resident copies + workspace + the
@@ -180,7 +189,9 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
  * previous gwc_sync (then clears it). */
 gwc_status gwc_sync(gwc_ctx* ctx, void* stream);
 
-gwc_status gwc_get_stats(const gwc_ctx* ctx, gwc_stats* out);
+/* Counters since creation or the last reset. In profile mode the kernel times of work still in
+ * flight are folded in by gwc_sync / gwc_get_stats (which then synchronise the device). */
+gwc_status gwc_get_stats(gwc_ctx* ctx, gwc_stats* out);
 gwc_status gwc_reset_stats(gwc_ctx* ctx);
 
 /* Message of the last failing call on ctx (or of the last failing gwc_create when ctx is

@@ -47,6 +47,58 @@ gwc_status fail(gwc_ctx* ctx, gwc_status st, const std::string& msg) {
 
 inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
+// ---- profile mode: CUDA events around the timed kernel classes ------------------------------
+enum { kClsChi0 = 0, kClsFactor = 1, kClsSolve = 2 };
+
+cudaEvent_t ev_get(gwc_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+cudaEvent_t ev_begin(gwc_ctx* ctx, cudaStream_t st) {
+  if (!ctx->opt.profile) return nullptr;
+  cudaEvent_t a = ev_get(ctx);
+  cudaEventRecord(a, st);
+  return a;
+}
+
+void ev_end(gwc_ctx* ctx, int cls, cudaEvent_t a, cudaStream_t st) {
+  if (!ctx->opt.profile || !a) return;
+  cudaEvent_t b = ev_get(ctx);
+  cudaEventRecord(b, st);
+  ctx->ev_pending.push_back({cls, a, b});
+}
+
+// Folds the elapsed times of completed records into the stats (synchronises on the last one).
+void ev_flush(gwc_ctx* ctx) {
+  if (ctx->ev_pending.empty()) return;
+  cudaEventSynchronize(ctx->ev_pending.back().b);
+  for (auto& r : ctx->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      if (r.cls == kClsChi0) {
+        ctx->stats.chi0_ms += ms;
+        ctx->stats.chi0_launches += 1;
+      } else if (r.cls == kClsFactor) {
+        ctx->stats.factor_ms += ms;
+        ctx->stats.factor_launches += 1;
+      } else {
+        ctx->stats.solve_ms += ms;
+        ctx->stats.solve_launches += 1;
+      }
+    }
+    ctx->ev_pool.push_back(r.a);
+    ctx->ev_pool.push_back(r.b);
+  }
+  ctx->ev_pending.clear();
+}
+
 // Gauss-Legendre nodes and weights on (-1, 1), ascending, by Newton iteration on P_n
 // (three-term recurrence; initial guesses cos(pi (i - 1/4)/(n + 1/2))).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
@@ -198,6 +250,11 @@ gwc_status upload(gwc_ctx* ctx, void* dst, const void* src, size_t bytes, int me
 
 gwc_status ensure_pinned_i(gwc_ctx* ctx, size_t n) {
   if (n <= ctx->h_pin_i_cap) return GWC_OK;
+  for (auto& r : ctx->ev_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->h_pin_i) cudaFreeHost(ctx->h_pin_i);
   ctx->h_pin_i = nullptr;
   CU(cudaMallocHost((void**)&ctx->h_pin_i, n * sizeof(int)));
@@ -254,6 +311,7 @@ gwc_status run_chi0(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, cons
   LAUNCH(launch_dtable(d_z, F, ctx->d_delta, ctx->n_ov, ctx->ld_dtab, !fp64, ctx->d_dtab, st));
   MatKind kind = complex_z ? cplx_kind(ctx) : real_kind(ctx);
   const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  cudaEvent_t ev = ev_begin(ctx, st);
   if (prec == GWC_PREC_FP64) {
     LAUNCH(launch_chi0_simt(kind, ctx->d_o_ov, ctx->n_ov, ctx->n_aux, ctx->n_ov, ctx->d_dtab, ctx->ld_dtab, F, alpha, beta,
                             out, ctx->ldm, stride, full, active, st));
@@ -271,9 +329,14 @@ gwc_status run_chi0(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, cons
       return fail(ctx, GWC_ERR_UNSUPPORTED, "full-matrix output not supported by the tensor-core path");
     }
   }
+  ev_end(ctx, kClsChi0, ev, st);
   ctx->stats.chi0_builds += F;
   ctx->stats.chi0_flop += (double)F * (complex_z ? 2.0 : 1.0) * (double)ctx->n_aux * (ctx->n_aux + 1.0) * (double)ctx->n_ov;
   return GWC_OK;
+}
+
+double factor_flop(int n, bool cplx, int F) {
+  return (double)F * (cplx ? 8.0 : 2.0) * (double)n * n * n / 3.0;
 }
 
 // ---- imaginary-axis W table --------------------------------------------------------------------
@@ -307,7 +370,10 @@ gwc_status compute_wim(gwc_ctx* ctx, cudaStream_t st) {
     const int nb = std::min(fb, nodes - k0);
     res = run_chi0(ctx, false, nb, d_zall + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st);
     if (res != GWC_OK) break;
+    cudaEvent_t ev = ev_begin(ctx, st);
     int n = launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st);
+    ev_end(ctx, kClsFactor, ev, st);
+    ctx->stats.factor_flop += factor_flop(ctx->n_aux, false, nb);
     if (n < 0) {
       res = fail(ctx, GWC_ERR_CUDA, "ldlt launch failed");
       break;
@@ -319,8 +385,10 @@ gwc_status compute_wim(gwc_ctx* ctx, cudaStream_t st) {
       int n1 = launch_rhs_gather(rk, ctx->d_o_core, ctx->n_aux, ctx->d_rowmap, 1, r, ctx->n_aux, ctx->d_rhs_im, ctx->ldm,
                                  0, ctx->d_bnorm, st);
       char* mat = (char*)ctx->d_mats + (size_t)u * stride * mat_elem_bytes(rk);
+      cudaEvent_t evs = ev_begin(ctx, st);
       int n2 = launch_ldlt_solve_w(rk, mat, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs_im, r, ctx->ldm, 0, ctx->d_bnorm, 1,
                                    ctx->d_wtmp, 0, nullptr, st);
+      ev_end(ctx, kClsSolve, evs, st);
       if (n1 < 0 || n2 < 0) {
         res = fail(ctx, GWC_ERR_CUDA, "imaginary-axis solve launch failed");
         break;
@@ -349,12 +417,17 @@ gwc_status residue_batches(gwc_ctx* ctx, int n_pairs, const double* z_dev, const
     const int nb = std::min(ctx->batch, n_pairs - p0);
     const int* act = active ? active + p0 : nullptr;
     TRY(run_chi0(ctx, true, nb, z_dev + 2 * (size_t)p0, act, ctx->d_mats, -1.0, 1.0, 0, st));
+    cudaEvent_t ev = ev_begin(ctx, st);
     LAUNCH(launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, act, ctx->d_status, st));
+    ev_end(ctx, kClsFactor, ev, st);
     ctx->stats.factorizations += nb;
+    ctx->stats.factor_flop += factor_flop(ctx->n_aux, true, nb);
     LAUNCH(launch_rhs_gather(ck, ctx->d_o_core, ctx->n_aux, rows_dev + (size_t)p0 * r, nb, r, ctx->n_aux, ctx->d_rhs,
                              ctx->ldm, rstride, ctx->d_bnorm, st));
+    cudaEvent_t evs = ev_begin(ctx, st);
     LAUNCH(launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs, r, ctx->ldm, rstride,
                                ctx->d_bnorm, nb, w_out + (size_t)p0 * r * 2, (long long)r * 2, act, st));
+    ev_end(ctx, kClsSolve, evs, st);
   }
   return GWC_OK;
 }
@@ -401,6 +474,7 @@ gwc_status gwc_default_options(gwc_options* o) {
   o->max_qp_iter = 50;
   o->qp_tol = 1e-7;
   o->batch = 0;
+  o->profile = 0;
   return GWC_OK;
 }
 
@@ -558,6 +632,11 @@ void gwc_destroy(gwc_ctx* ctx) {
                   ctx->d_pair_z, ctx->d_pair_rows};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& r : ctx->ev_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->h_pin_i) cudaFreeHost(ctx->h_pin_i);
   if (ctx->h_pin_d) cudaFreeHost(ctx->h_pin_d);
   delete ctx;
@@ -750,6 +829,7 @@ gwc_status gwc_sync(gwc_ctx* ctx, void* stream) {
   unsigned flags = 0;
   CU(cudaMemcpyAsync(&flags, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
+  ev_flush(ctx);
   CU(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), st));
   CU(cudaStreamSynchronize(st));
   if (flags & kStatTimeout) return fail(ctx, GWC_ERR_TIMEOUT, "a bounded device wait gave up");
@@ -759,14 +839,16 @@ gwc_status gwc_sync(gwc_ctx* ctx, void* stream) {
   return GWC_OK;
 }
 
-gwc_status gwc_get_stats(const gwc_ctx* ctx, gwc_stats* out) {
+gwc_status gwc_get_stats(gwc_ctx* ctx, gwc_stats* out) {
   if (!ctx || !out) return GWC_ERR_INVALID_ARG;
+  ev_flush(ctx);
   *out = ctx->stats;
   return GWC_OK;
 }
 
 gwc_status gwc_reset_stats(gwc_ctx* ctx) {
   if (!ctx) return GWC_ERR_INVALID_ARG;
+  ev_flush(ctx);
   ctx->stats = gwc_stats{};
   return GWC_OK;
 }

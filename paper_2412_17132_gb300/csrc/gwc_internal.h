@@ -256,4 +256,12 @@ struct gwc_ctx {
 
   gwc_stats stats{};
   std::string last_error;
+
+  // profile mode: (class, start, stop) events pending resolution
+  struct EvRec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<EvRec> ev_pending;
+  std::vector<cudaEvent_t> ev_pool;
 };

@@ -67,6 +67,7 @@ class Options(ctypes.Structure):
         ("max_qp_iter", ctypes.c_int),
         ("qp_tol", ctypes.c_double),
         ("batch", ctypes.c_int),
+        ("profile", ctypes.c_int),
     ]
 
 
@@ -76,6 +77,13 @@ class Stats(ctypes.Structure):
         ("chi0_flop", ctypes.c_double),
         ("kernel_launches", ctypes.c_longlong),
         ("factorizations", ctypes.c_longlong),
+        ("chi0_launches", ctypes.c_longlong),
+        ("chi0_ms", ctypes.c_double),
+        ("factor_launches", ctypes.c_longlong),
+        ("factor_ms", ctypes.c_double),
+        ("factor_flop", ctypes.c_double),
+        ("solve_launches", ctypes.c_longlong),
+        ("solve_ms", ctypes.c_double),
     ]
 
 
@@ -155,7 +163,7 @@ class Context:
 
     def __init__(self, eps, n_occ, core_idx, o_ov, o_core, *, vxc=None, eps_f=math.nan, eta=1e-3, n_im=32, xi0=1.0,
                  prec="bf16x3", dec="diag", groups=None, n_t=1 << 16, t_max=2000.0, max_qp_iter=50, qp_tol=1e-7,
-                 batch=0, stream=None):
+                 batch=0, profile=False, stream=None):
         self._ctx = ctypes.c_void_p()
         host = isinstance(eps, np.ndarray)
         self._keep = []
@@ -175,6 +183,7 @@ class Context:
             opt.group_of_core = g.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         opt.n_t, opt.t_max = int(n_t), float(t_max)
         opt.max_qp_iter, opt.qp_tol, opt.batch = int(max_qp_iter), float(qp_tol), int(batch)
+        opt.profile = 1 if profile else 0
         self.opt = opt
         self.prec = prec
         _check(lib().gwc_create(ctypes.byref(self._ctx), ctypes.byref(sysd), ctypes.byref(opt), _stream(stream)), None)
@@ -263,8 +272,7 @@ class Context:
     def stats(self) -> dict:
         s = Stats()
         _check(lib().gwc_get_stats(self._ctx, ctypes.byref(s)), self._ctx)
-        return {"chi0_builds": s.chi0_builds, "chi0_flop": s.chi0_flop, "kernel_launches": s.kernel_launches,
-                "factorizations": s.factorizations}
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
 
     def reset_stats(self):
         _check(lib().gwc_reset_stats(self._ctx), self._ctx)
