@@ -185,6 +185,28 @@ gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, vo
 gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_omega, const double* im_sigma,
                                  double* a_out, double* nu_out, void* stream);
 
+/* Cumulant spectral function that allocates nothing (the paper has no counterpart: this is
+ * a deployment variant of gwc_cumulant_spectrum with the same arithmetic and output layout).
+ * For callers that cannot call cudaMalloc: a serving thread that shares the GPU with another
+ * framework's caching allocator or works under a fixed device-memory budget, where an
+ * allocation or free can synchronise the device or exceed the budget, or a caller without a
+ * gwc_ctx. It needs no context; all sizes are arguments.
+ *   omega_rel, im_sigma: DEVICE [n_core][n_omega]; a_out: DEVICE [n_core][n_t]; nu_out: DEVICE [n_t] or NULL
+ * Scratch lives in one static device array of the library (about 10.5 MB, held on every GPU
+ * that loads libgwc until the process exits); limits: n_core*n_t <= GWC_NOALLOC_MAX_WORK,
+ * n_core*n_omega <= GWC_NOALLOC_MAX_COEF, n_t a power of two in 16..2^18, n_omega <= 8192.
+ * Larger sizes return GWC_ERR_INVALID_ARG (message in gwc_last_error(NULL)) before any launch.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. All calls share the array: calls that
+ * overlap on the GPU (other streams, unsynchronised threads) race and must be serialised.
+ * Every scratch element a call reads is written earlier in the same call, so stale contents
+ * of a previous call never reach the output. */
+#define GWC_NOALLOC_MAX_WORK (1 << 18)
+#define GWC_NOALLOC_MAX_COEF (1 << 16)
+gwc_status gwc_cumulant_spectrum_noalloc(const double* omega_rel, int n_omega, const double* im_sigma, int n_core,
+                                         int n_t, double t_max, double eta, double* a_out, double* nu_out,
+                                         void* stream);
+
 /* Synchronises `stream` and reports the first device-side status raised since the
  * previous gwc_sync (then clears it). */
 gwc_status gwc_sync(gwc_ctx* ctx, void* stream);

@@ -440,6 +440,10 @@ gwc_status check_stream_error(gwc_ctx* ctx) {
 
 }  // namespace
 
+namespace gwc {
+void set_noctx_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace gwc
+
 // =====================================================================================================
 extern "C" {
 

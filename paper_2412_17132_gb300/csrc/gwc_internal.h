@@ -169,6 +169,9 @@ int launch_cumulant_spectrum(const double* omega_rel, int n_w, const double* im_
                              double* work_b /*[n_core][n_t][2]*/, double* coef /*[n_core][n_w]*/,
                              double* twiddle /*[n_t/2][2]*/, double* a_out, double* nu_out, cudaStream_t s);
 
+// Sets the message returned by gwc_last_error(NULL) (calls without a context).
+void set_noctx_error(const char* msg);
+
 // Precision copies of O_ov: hi/lo BF16 and FP32, padded [n_aux_pad][n_ov_pad], zero padding.
 int launch_split_o(const double* o_ov, int n_aux, int n_ov, int n_aux_pad, int n_ov_pad, __nv_bfloat16* hi,
                    __nv_bfloat16* lo, float* f32, cudaStream_t s);

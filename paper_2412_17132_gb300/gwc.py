@@ -106,6 +106,9 @@ _SIGS = {
     "gwc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "gwc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "gwc_destroy": (None, [ctypes.c_void_p]),
+    "gwc_cumulant_spectrum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                                      ctypes.c_void_p]),
 }
 
 
@@ -152,6 +155,15 @@ def _stream(stream=None) -> int:
 
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream
+
+
+def cumulant_spectrum_noalloc(omega_rel, im_sigma, n_t, t_max, eta, a_out, nu_out=None, stream=None):
+    """gwc_cumulant_spectrum_noalloc: no context and no allocation by the library; the caller
+    passes device tensors omega_rel/im_sigma [n_core][n_omega] and a_out [n_core][n_t]."""
+    n_core, n_w = int(omega_rel.shape[0]), int(omega_rel.shape[1])
+    _check(lib().gwc_cumulant_spectrum_noalloc(_ptr(omega_rel), n_w, _ptr(im_sigma), n_core, int(n_t), float(t_max),
+                                               float(eta), _ptr(a_out), _ptr(nu_out), _stream(stream)), None)
+    return a_out, nu_out
 
 
 class Context:
