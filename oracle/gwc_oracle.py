@@ -242,14 +242,20 @@ class System:
             out[c] = self.sigma_c_core(c, float(self.eps[n])).real + sx[c] - vxc[c]
         return out
 
-    def qp_solve(self, tol=1e-7, max_iter=50):
+    def qp_solve(self, tol=1e-7, max_iter=50, cores=None):
         """Solve eps = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n(eps - dH_n) by the secant method
-        from eps_n (G_dH W0 QP equation). Returns (eps_qp, dH, iterations)."""
+        from eps_n (G_dH W0 QP equation). Returns (eps_qp, dH, iterations); with `cores` given
+        only those cores are solved (the other entries are NaN / 0)."""
         sx, vxc = self.sigma_x(), self.v_xc()
-        dh = self.hedin_shift()
-        eqp = np.empty(self.n_core)
+        todo = range(self.n_core) if cores is None else list(cores)
+        dh = np.full(self.n_core, np.nan)
+        for c in todo:
+            n = self.core_idx[c]
+            dh[c] = self.sigma_c_core(c, float(self.eps[n])).real + sx[c] - vxc[c]
+        eqp = np.full(self.n_core, np.nan)
         iters = np.zeros(self.n_core, dtype=np.int64)
-        for c, n in enumerate(self.core_idx):
+        for c in todo:
+            n = self.core_idx[c]
             e_n = float(self.eps[n])
 
             def g(e):

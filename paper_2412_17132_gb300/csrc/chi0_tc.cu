@@ -2,23 +2,27 @@
 //
 //   Pi_PQ(z_f) = sum_k O_Pk D_f(k) O_Qk      (RI polarizability, Sec. "Self-energy evaluation")
 //
-// One CTA computes a 128 x 128 lower-triangle tile (P-tile >= Q-tile) for up to four
-// frequency parts (a complex z has two parts, Re D and Im D; a point on the imaginary axis
-// one). The contraction index k = (i, a) runs over the occupied-virtual pairs in chunks of 64.
+// One CTA computes one 128 x 128 lower-triangle tile (P-tile >= Q-tile) for two frequency
+// parts: the real and imaginary parts of D at one complex z, or two points of the imaginary
+// axis. The contraction index k = (i, a) runs over the occupied-virtual pairs in 64-wide chunks.
 //
-//   * B operand  O[Q-tile][k-chunk] (BF16 hi, and lo in split mode) arrives by TMA
-//     (SWIZZLE_128B, K-major) into a 2-stage ring; it is shared by every frequency part.
-//   * A operand  O[P-tile][k] * D_f(k) is formed on the fly by 8 transform warps: each
-//     thread reads its row's 32 FP32 values once per chunk, scales them by D of each part,
-//     splits them into BF16 hi (+ lo = bf16(v - hi)) and writes them in the swizzled K-major
-//     layout the MMA reads; the D scaling is thereby fused into the operand load.
+//   * TMA brings, per chunk, the B operand O[Q-tile][chunk] (BF16 hi, and lo in split mode,
+//     SWIZZLE_128B, K-major), the FP32 rows O[P-tile][chunk] and the two 64-value slices of
+//     the D(z) table into two-stage rings.
+//   * 4 transform warps form the A operand O[P][k] D_p(k) (the D scaling is fused into the
+//     operand load): each thread owns one row, scales its 64 values, splits them into BF16 hi
+//     and lo = bf16(v - hi), and writes them in the swizzled K-major layout the MMA reads.
 //   * One thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM): per part and
-//     16-wide k step, hi*hi (+ hi*lo + lo*hi in split mode, Henry, Tang & Heinecke 2019).
-//   * Epilogue: the transform warps read the accumulators with tcgen05.ld and write
-//     alpha * Pi + beta * I (eps = 1 - Pi with alpha = -1, beta = 1) in FP32.
+//     16-wide k step hi*hi (+ hi*lo + lo*hi in split mode; Henry, Tang & Heinecke 2019).
+//   * Segmented accumulation: the FP32 accumulator of the tensor core rounds toward zero, a
+//     bias that grows with the number of accumulations into one accumulator. Each part
+//     therefore accumulates only kSeg chunks into a "fresh" TMEM accumulator; 4 fold warps
+//     then add it (round-to-nearest FP32) into a running sum kept in TMEM and release the
+//     accumulator. The last fold writes alpha * Pi + beta * I (eps = 1 - Pi for alpha = -1,
+//     beta = 1) to global memory.
 //
-// Every wait on an mbarrier is bounded (about one second); on expiry the CTA records
-// kStatTimeout, stops issuing work, waits (bounded) for its issued MMAs and frees TMEM.
+// Every wait on an mbarrier is bounded (one second); on expiry the CTA records kStatTimeout,
+// stops issuing work, drains the copies and MMAs it issued and frees TMEM.
 #include <cuda.h>
 
 #include <cstdio>
@@ -31,24 +35,27 @@ namespace gwc {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
-constexpr int NB_ST = 2;               // B ring stages
-constexpr int NA_ST = 4;               // A ring slots (one frequency part each)
-constexpr int TILE = BM * BK * 2;      // 16 KB: one BF16 128 x 64 operand tile
-constexpr int NTHREADS = 384;          // warps 0-3 control, 4-11 transform + epilogue
-constexpr int NXF = 256;               // transform threads
-constexpr int SMEM_BYTES = 1024 + NB_ST * 2 * TILE + NA_ST * 2 * TILE + 256;
+constexpr int kParts = 2;                  // frequency parts per CTA
+constexpr int kSeg = 4;                    // chunks accumulated per fresh accumulator
+constexpr int NB_ST = 2;                   // B ring / raw-A ring stages
+constexpr int NA_ST = 3;                   // scaled-A slots (one part each)
+constexpr int TILE = BM * BK * 2;          // 16 KB: one BF16 128 x 64 operand tile
+constexpr int RAW = BM * BK * 4;           // 32 KB: FP32 128 x 64 rows (two 128-B swizzled halves)
+constexpr int DSL = kParts * BK * 4;       // 512 B: D slices of one chunk
+constexpr int NTHREADS = 384;              // warp 0 TMA, 1 MMA, 2 TMEM, 4-7 transform, 8-11 fold
+constexpr int NXF = 128;                   // transform threads
+constexpr int NFOLD = 128;                 // fold threads
+constexpr int SMEM_BYTES = 1024 + NB_ST * 2 * TILE + NB_ST * RAW + NA_ST * 2 * TILE + NB_ST * DSL + 256;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s bound per wait
 
 struct TcParams {
-  const float* o32;
-  int ld;                 // leading dim of o32 (= n_ov_pad)
   const float* dtab;
   int ld_dtab;
   int n_aux;
   int n_kc;               // number of 64-wide chunks
   int F;
   int ppf;                // parts per frequency (1 real, 2 complex)
-  int fpc;                // frequencies per CTA
+  int fpc;                // frequencies per CTA (kParts / ppf)
   int split3;
   float alpha, beta;
   void* out;
@@ -91,8 +98,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: returns false (and raises the CTA abort flag) if the phase does not
-// complete within kWaitNs or if another role already aborted.
+// Bounded wait: false (and the CTA abort flag raised) if the phase does not complete within
+// kWaitNs, or if another role aborted already.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try(bar, parity)) return true;
   unsigned long long t0 = gtime();
@@ -108,7 +115,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   }
 }
 
-// Bounded drain wait that ignores the abort flag (for copies already in flight).
+// Bounded drain wait that ignores the abort flag (for copies or MMAs already in flight).
 __device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
   unsigned long long t0 = gtime();
   for (uint32_t it = 0;; ++it) {
@@ -122,6 +129,12 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(bar)
       : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major, SWIZZLE_128B, 8-row groups 1024 B apart.
@@ -165,6 +178,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tile_pair(int t, int& ip, int& iq) {
   int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
   while ((a + 1) * (a + 2) / 2 <= t) ++a;
@@ -180,18 +205,25 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 
 template <bool CPLX>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    chi0_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, TcParams p) {
+    chi0_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+                   const __grid_constant__ CUtensorMap tm_raw, TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* b_ring = base;                          // NB_ST x [hi | lo]
-  uint8_t* a_ring = base + NB_ST * 2 * TILE;       // NA_ST x [hi | lo]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(a_ring + NA_ST * 2 * TILE);
+  uint8_t* b_ring = base;                            // NB_ST x [hi | lo]
+  uint8_t* r_ring = b_ring + NB_ST * 2 * TILE;       // NB_ST x [k 0..31 | k 32..63] FP32, swizzled
+  uint8_t* a_ring = r_ring + NB_ST * RAW;            // NA_ST x [hi | lo]
+  float* d_ring = reinterpret_cast<float*>(a_ring + NA_ST * 2 * TILE);  // NB_ST x [part][64]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(d_ring + NB_ST * kParts * BK);
   uint64_t* b_full = bars;
-  uint64_t* b_empty = bars + NB_ST;
-  uint64_t* a_full = bars + 2 * NB_ST;
-  uint64_t* a_empty = bars + 2 * NB_ST + NA_ST;
-  uint64_t* acc_done = bars + 2 * NB_ST + 2 * NA_ST;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_done + 1);
+  uint64_t* b_empty = b_full + NB_ST;
+  uint64_t* r_full = b_empty + NB_ST;
+  uint64_t* r_empty = r_full + NB_ST;
+  uint64_t* a_full = r_empty + NB_ST;
+  uint64_t* a_empty = a_full + NA_ST;
+  uint64_t* seg_full = a_empty + NA_ST;
+  uint64_t* fold_done = seg_full + 1;
+  uint64_t* mma_done = fold_done + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,18 +237,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int u = 0; u < nf; ++u) any |= p.active[f0 + u];
     if (!any) return;  // uniform across the CTA, before any barrier or TMEM use
   }
-  const int n_parts = nf * p.ppf;
+  const int n_parts = nf * p.ppf;  // 1 or 2
+  const int n_seg = (p.n_kc + kSeg - 1) / kSeg;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NB_ST; ++i) {
       mbar_init(smem_u32(&b_full[i]), 1);
       mbar_init(smem_u32(&b_empty[i]), 1);
+      mbar_init(smem_u32(&r_full[i]), 1);
+      mbar_init(smem_u32(&r_empty[i]), NXF);
     }
     for (int i = 0; i < NA_ST; ++i) {
       mbar_init(smem_u32(&a_full[i]), NXF);
       mbar_init(smem_u32(&a_empty[i]), 1);
     }
-    mbar_init(smem_u32(acc_done), 1);
+    mbar_init(smem_u32(seg_full), 1);
+    mbar_init(smem_u32(fold_done), NFOLD);
+    mbar_init(smem_u32(mma_done), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -231,22 +268,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t b_bytes = p.split3 ? 2 * TILE : TILE;
 
   if (warp == 0) {
+    // ---------------- TMA producer --------------------------------------------------------
     if (lane == 0) {
       int issued = 0;
       for (int kc = 0; kc < p.n_kc; ++kc) {
         const int s = kc % NB_ST, u = kc / NB_ST;
         if (!mbar_wait(smem_u32(&b_empty[s]), (u & 1) ^ 1, abort_flag)) break;
         mbar_expect_tx(smem_u32(&b_full[s]), b_bytes);
-        uint8_t* dst = b_ring + s * 2 * TILE;
-        tma_load_2d(smem_u32(dst), &tm_hi, kc * BK, Q0, smem_u32(&b_full[s]));
-        if (p.split3) tma_load_2d(smem_u32(dst + TILE), &tm_lo, kc * BK, Q0, smem_u32(&b_full[s]));
+        uint8_t* bd = b_ring + s * 2 * TILE;
+        tma_load_2d(smem_u32(bd), &tm_hi, kc * BK, Q0, smem_u32(&b_full[s]));
+        if (p.split3) tma_load_2d(smem_u32(bd + TILE), &tm_lo, kc * BK, Q0, smem_u32(&b_full[s]));
+        if (!mbar_wait(smem_u32(&r_empty[s]), (u & 1) ^ 1, abort_flag)) {
+          issued = kc + 1;  // the B copy of this chunk is in flight
+          break;
+        }
+        mbar_expect_tx(smem_u32(&r_full[s]), RAW + n_parts * BK * 4);
+        uint8_t* rd = r_ring + s * RAW;
+        tma_load_2d(smem_u32(rd), &tm_raw, kc * BK, P0, smem_u32(&r_full[s]));
+        tma_load_2d(smem_u32(rd + RAW / 2), &tm_raw, kc * BK + 32, P0, smem_u32(&r_full[s]));
+        for (int part = 0; part < n_parts; ++part) {
+          const int f = f0 + part / p.ppf, comp = part % p.ppf;
+          bulk_load(smem_u32(d_ring + (s * kParts + part) * BK), p.dtab + ((size_t)f * 2 + comp) * p.ld_dtab + kc * BK,
+                    BK * 4, smem_u32(&r_full[s]));
+        }
         issued = kc + 1;
       }
       // no copy may still be writing shared memory when the CTA exits
-      for (int kc = issued > NB_ST ? issued - NB_ST : 0; kc < issued; ++kc)
+      for (int kc = issued > NB_ST ? issued - NB_ST : 0; kc < issued; ++kc) {
         mbar_drain(smem_u32(&b_full[kc % NB_ST]), (kc / NB_ST) & 1);
+        mbar_drain(smem_u32(&r_full[kc % NB_ST]), (kc / NB_ST) & 1);
+      }
     }
   } else if (warp == 1) {
+    // ---------------- MMA issuer ------------------------------------------------------------
     if (lane == 0) {
       int a = 0;
       bool ok = true;
@@ -258,6 +312,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         tc_fence_after();
         const uint32_t bh = smem_u32(b_ring + s * 2 * TILE), bl = bh + TILE;
+        const bool seg_start = (kc % kSeg) == 0;
         for (int part = 0; part < n_parts; ++part, ++a) {
           const int t = a % NA_ST, ua = a / NA_ST;
           if (!mbar_wait(smem_u32(&a_full[t]), ua & 1, abort_flag)) {
@@ -266,11 +321,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t ah = smem_u32(a_ring + t * 2 * TILE), al = ah + TILE;
-          const uint32_t d = tmem_base + (uint32_t)(part * BN);
+          const uint32_t d = tmem_base + (uint32_t)(part * BN);  // fresh accumulator of this part
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
             const uint32_t off = k * 32;  // 16 BF16 = 32 bytes along K inside the 128-B row
-            const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
+            const uint32_t acc = (seg_start && k == 0) ? 0u : 1u;
             mma_bf16(d, sdesc(ah + off), sdesc(bh + off), acc);
             if (p.split3) {
               mma_bf16(d, sdesc(ah + off), sdesc(bl + off), 1u);
@@ -281,42 +336,54 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (!ok) break;
         mma_commit(smem_u32(&b_empty[s]));
+        const bool seg_end = (kc % kSeg) == kSeg - 1 || kc == p.n_kc - 1;
+        if (seg_end) {
+          const int seg = kc / kSeg;
+          mma_commit(smem_u32(seg_full));
+          // the next segment overwrites the fresh accumulators: wait until they are folded
+          if (seg < n_seg - 1 && !mbar_wait(smem_u32(fold_done), seg & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
       }
-      // acc_done fires when every MMA issued so far has completed (also after an abort)
-      mma_commit(smem_u32(acc_done));
+      mma_commit(smem_u32(mma_done));  // fires when every MMA issued above has completed
     }
-  } else if (warp >= 4) {
-    const int tt = threadIdx.x - 128;
-    const int r = tt & 127, h = tt >> 7;
-    const float* orow = p.o32 + (size_t)(P0 + r) * p.ld + 32 * h;
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- transform: A = O[P][k] D_p(k), split into BF16 hi / lo -------------------
+    const int r = threadIdx.x - 128;  // row of the P tile
     int a = 0;
-    bool ok = true;
-    for (int kc = 0; kc < p.n_kc && ok; ++kc) {
-      float raw[32];
-      const float4* src = reinterpret_cast<const float4*>(orow + kc * BK);
+    for (int kc = 0; kc < p.n_kc; ++kc) {
+      const int s = kc % NB_ST, u = kc / NB_ST;
+      if (!mbar_wait(smem_u32(&r_full[s]), u & 1, abort_flag)) break;
+      float raw[64];
+      const uint8_t* rrow = r_ring + s * RAW + r * 128;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        float4 v = __ldg(src + u);
-        raw[4 * u] = v.x;
-        raw[4 * u + 1] = v.y;
-        raw[4 * u + 2] = v.z;
-        raw[4 * u + 3] = v.w;
-      }
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {  // 16-byte chunk c (4 floats) of half h, swizzled by row%8
+          float4 v = *reinterpret_cast<const float4*>(rrow + h * (RAW / 2) + ((c ^ (r & 7)) << 4));
+          raw[32 * h + 4 * c] = v.x;
+          raw[32 * h + 4 * c + 1] = v.y;
+          raw[32 * h + 4 * c + 2] = v.z;
+          raw[32 * h + 4 * c + 3] = v.w;
+        }
+      bool ok = true;
       for (int part = 0; part < n_parts; ++part, ++a) {
         const int t = a % NA_ST, ua = a / NA_ST;
         if (!mbar_wait(smem_u32(&a_empty[t]), (ua & 1) ^ 1, abort_flag)) {
           ok = false;
           break;
         }
-        const int f = f0 + part / p.ppf, comp = part % p.ppf;
-        const float4* dsrc = reinterpret_cast<const float4*>(p.dtab + ((size_t)f * 2 + comp) * p.ld_dtab + kc * BK + 32 * h);
+        const float4* ds = reinterpret_cast<const float4*>(d_ring + (s * kParts + part) * BK);  // broadcast reads
         uint8_t* ah = a_ring + t * 2 * TILE + r * 128;
         uint8_t* al = ah + TILE;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {  // 16-byte chunk c (8 values) of this thread's 32
-          float4 d0 = __ldg(dsrc + 2 * c), d1 = __ldg(dsrc + 2 * c + 1);
-          float v[8] = {raw[8 * c] * d0.x, raw[8 * c + 1] * d0.y, raw[8 * c + 2] * d0.z, raw[8 * c + 3] * d0.w,
-                        raw[8 * c + 4] * d1.x, raw[8 * c + 5] * d1.y, raw[8 * c + 6] * d1.z, raw[8 * c + 7] * d1.w};
+        for (int c = 0; c < 8; ++c) {  // 16-byte chunk c = 8 BF16 values k = 8c .. 8c+7
+          const float4 d0 = ds[2 * c], d1 = ds[2 * c + 1];
+          const float v[8] = {raw[8 * c] * d0.x,     raw[8 * c + 1] * d0.y, raw[8 * c + 2] * d0.z, raw[8 * c + 3] * d0.w,
+                              raw[8 * c + 4] * d1.x, raw[8 * c + 5] * d1.y, raw[8 * c + 6] * d1.z, raw[8 * c + 7] * d1.w};
           uint32_t hw[4], lw[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -325,49 +392,73 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             float2 hf = __bfloat1622float2(hb);
             lw[e] = pack_bf16x2(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
           }
-          const int chunk = (4 * h + c) ^ (r & 7);  // SWIZZLE_128B: 16-B chunk index XOR row%8
+          const int chunk = c ^ (r & 7);  // SWIZZLE_128B: 16-B chunk index XOR row%8
           *reinterpret_cast<uint4*>(ah + chunk * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           if (p.split3) *reinterpret_cast<uint4*>(al + chunk * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(smem_u32(&a_full[t]));
       }
+      if (ok) mbar_arrive(smem_u32(&r_empty[s]));  // raw rows and D slices of this stage are consumed
+      if (!ok) break;
     }
-    // ---- epilogue -----------------------------------------------------------------------
-    bool done = mbar_wait(smem_u32(acc_done), 0, abort_flag) && ok;
-    if (!done) mbar_drain(smem_u32(acc_done), 0);  // issued MMAs must finish before TMEM is freed
-    done = __all_sync(0xffffffffu, done && !*abort_flag);
-    tc_fence_after();
-    if (done) {
-      const int q = warp & 3, chalf = (warp - 4) >> 2;
-      const int row = 32 * q + lane;
-      const int P = P0 + row;
-      const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
-      for (int fl = 0; fl < nf; ++fl) {
+  } else if (warp >= 8) {
+    // ---------------- fold + epilogue: running += fresh (FP32, round to nearest) -------------
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    const int P = P0 + row;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+    bool ok = true;
+    for (int seg = 0; seg < n_seg; ++seg) {
+      ok = mbar_wait(smem_u32(seg_full), seg & 1, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      const bool last = seg == n_seg - 1;
+      for (int part = 0; part < n_parts; ++part) {
+        const int fl = part / p.ppf;
         const int f = f0 + fl;
-        if (p.active && !p.active[f]) continue;
-        for (int cc = 0; cc < 4; ++cc) {
-          const int col = chalf * 64 + cc * 16;
-          float re[16], im[16];
-          tmem_ld16(lane_base + (uint32_t)((fl * p.ppf) * BN + col), re);
-          if (CPLX) tmem_ld16(lane_base + (uint32_t)((fl * p.ppf + 1) * BN + col), im);
-          if (P >= p.n_aux) continue;
+        const bool write = last && (!p.active || p.active[f]);
+        for (int cc = 0; cc < BN / 16; ++cc) {
+          float fr[16], run[16];
+          tmem_ld16(lane_base + (uint32_t)(part * BN + cc * 16), fr);
+          if (seg > 0) {
+            tmem_ld16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), run);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int Q = Q0 + col + i;
-            if (Q >= p.n_aux || Q > P) continue;
-            const float dg = (P == Q) ? p.beta : 0.0f;
-            if (CPLX) {
-              float2* o = reinterpret_cast<float2*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + Q;
-              *o = make_float2(p.alpha * re[i] + dg, p.alpha * im[i]);
-            } else {
-              float* o = reinterpret_cast<float*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + Q;
-              *o = p.alpha * re[i] + dg;
+            for (int i = 0; i < 16; ++i) fr[i] += run[i];
+          }
+          if (!last) {
+            tmem_st16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), fr);
+          } else if (write && P < p.n_aux) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int Q = Q0 + cc * 16 + i;
+              if (Q >= p.n_aux || Q > P) continue;
+              const float dg = (P == Q) ? p.beta : 0.0f;
+              if (CPLX) {
+                // parts 0 and 1 are Re and Im of one frequency; each writes its own component
+                float* o = reinterpret_cast<float*>(reinterpret_cast<float2*>(p.out) + f * p.mat_stride +
+                                                    (long long)P * p.ldm + Q) + (part % 2);
+                *o = p.alpha * fr[i] + ((part % 2) == 0 ? dg : 0.0f);
+              } else {
+                float* o = reinterpret_cast<float*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + Q;
+                *o = p.alpha * fr[i] + dg;
+              }
             }
           }
         }
       }
+      if (!last) {
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(smem_u32(fold_done));
+      }
     }
+  }
+  // drain: every issued MMA completes before TMEM is freed (immediate on the normal path)
+  if (warp == 2) {
+    if (lane == 0) mbar_drain(smem_u32(mma_done), 0);
+    __syncwarp();
   }
   tc_fence_before();
   __syncthreads();
@@ -395,14 +486,15 @@ EncodeTiledFn encoder() {
   return fn;
 }
 
-bool make_map(CUtensorMap* tm, const __nv_bfloat16* ptr, int rows, int cols) {
+// 2-D tensor map over a row-major [rows][cols] array, box = box_cols x 128 rows, SWIZZLE_128B.
+bool make_map(CUtensorMap* tm, const void* ptr, CUtensorMapDataType dt, int elem, int rows, int cols, int box_cols) {
   EncodeTiledFn enc = encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {BK, BN};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * elem};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)BM};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  CUresult r = enc(tm, dt, 2, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -427,21 +519,24 @@ int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* 
                    double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
                    unsigned* status, cudaStream_t s) {
   if (!tc_supported()) return -2;
-  if (n_aux_pad % BM || n_ov_pad % BK || ld_pad != n_ov_pad) return -2;
-  // TMA: base 16-B aligned and row stride a multiple of 16 B (n_ov_pad is a multiple of 64)
-  if ((reinterpret_cast<uintptr_t>(o_hi) & 15) || (reinterpret_cast<uintptr_t>(o_lo) & 15)) return -2;
-  CUtensorMap tm_hi, tm_lo;
-  if (!make_map(&tm_hi, o_hi, n_aux_pad, n_ov_pad) || !make_map(&tm_lo, o_lo, n_aux_pad, n_ov_pad)) return -2;
+  if (n_aux_pad % BM || n_ov_pad % BK || ld_pad != n_ov_pad || ld_dtab % BK) return -2;
+  // TMA: 16-B aligned bases, row strides multiples of 16 B, x coordinates multiples of 64 / 32
+  if ((reinterpret_cast<uintptr_t>(o_hi) & 15) || (reinterpret_cast<uintptr_t>(o_lo) & 15) ||
+      (reinterpret_cast<uintptr_t>(o_f32) & 15) || (reinterpret_cast<uintptr_t>(dtab) & 15))
+    return -2;
+  CUtensorMap tm_hi, tm_lo, tm_raw;
+  if (!make_map(&tm_hi, o_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, n_aux_pad, n_ov_pad, BK) ||
+      !make_map(&tm_lo, o_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, n_aux_pad, n_ov_pad, BK) ||
+      !make_map(&tm_raw, o_f32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, n_aux_pad, n_ov_pad, 32))
+    return -2;
   TcParams p;
-  p.o32 = o_f32;
-  p.ld = ld_pad;
   p.dtab = dtab;
   p.ld_dtab = ld_dtab;
   p.n_aux = n_aux;
   p.n_kc = n_ov_pad / BK;
   p.F = F;
   p.ppf = complex_out ? 2 : 1;
-  p.fpc = complex_out ? 2 : 4;
+  p.fpc = kParts / p.ppf;
   p.split3 = split3 ? 1 : 0;
   p.alpha = (float)alpha;
   p.beta = (float)beta;
@@ -459,14 +554,14 @@ int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* 
         return -1;
       attr_c = true;
     }
-    chi0_tc_kernel<true><<<grid, NTHREADS, SMEM_BYTES, s>>>(tm_hi, tm_lo, p);
+    chi0_tc_kernel<true><<<grid, NTHREADS, SMEM_BYTES, s>>>(tm_hi, tm_lo, tm_raw, p);
   } else {
     if (!attr_r) {
       if (cudaFuncSetAttribute(chi0_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess)
         return -1;
       attr_r = true;
     }
-    chi0_tc_kernel<false><<<grid, NTHREADS, SMEM_BYTES, s>>>(tm_hi, tm_lo, p);
+    chi0_tc_kernel<false><<<grid, NTHREADS, SMEM_BYTES, s>>>(tm_hi, tm_lo, tm_raw, p);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -280,3 +280,18 @@ def test_singular_pivot_is_reported_not_faulted(gwc):
     ctx.screen(zt, rhs)
     assert ctx.sync_status() == 4
     ctx.sync()  # status cleared
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_benzene_qp_gate_vs_oracle(gwc, prec):
+    """QP gate (|dE| <= 1e-3 eV) at the benzene size, mixed precision vs the FP64 oracle (core 0
+    and core 3; the oracle solves those cores only to keep the CPU time bounded)."""
+    mol = synth.benzene()
+    ctx = gwc.Context.from_molecule(mol, prec=prec)
+    e, dh, _ = ctx.qp_solve()
+    ctx.sync()
+    s = G.System.from_molecule(mol)
+    e_ref, dh_ref, _ = s.qp_solve(cores=[0, 3])
+    for c in (0, 3):
+        assert abs(float(e[c]) - e_ref[c]) * EV <= 1e-3, (c, (float(e[c]) - e_ref[c]) * EV)
+        assert abs(float(dh[c]) - dh_ref[c]) * EV <= 1e-3
