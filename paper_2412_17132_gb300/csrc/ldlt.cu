@@ -7,19 +7,238 @@
 // possible in exact arithmetic only; it is detected (|d| below a floor) and reported
 // through the status word, and the pivot is replaced by 1 so the batch stays finite.
 //
-// One CTA factors one matrix, right-looking and blocked (panel width NB = 32):
-//   1. the NB x NB diagonal block is factored in shared memory,
-//   2. every row below solves against it (one thread per row),
-//   3. the trailing lower triangle is updated tile by tile (64 x 64 tiles, 4 x 4 per thread)
-//      with the rank-NB product (L D)_panel L_panel^T staged through shared memory.
+// Storage after the factorisation (matrix [n][ldm], row-major):
+//   strictly lower part  W = L D   (W_ij = L_ij d_j, j < i)
+//   diagonal             d
+//   strictly upper part  L^T       (A[j][i] = L_ij; scratch used by the trailing updates)
+//
+// One CTA factors one matrix, right-looking and blocked:
+//   * 64-wide panels, each factored as two 32-wide sub-panels: the 32 x 32 diagonal block in
+//     shared memory, then every row below solves against it (one thread per row) and stores
+//     W (lower) and L (upper); a narrow update applies the first sub-panel to the second.
+//   * the trailing lower triangle is updated with the rank-64 product W_panel L_panel^T, in
+//     64 x 64 tiles (4 x 4 per thread); both operands are staged through shared memory by
+//     cp.async in 32-deep chunks, double-buffered across chunks and tiles.
 #include "gwc_internal.h"
 
 namespace gwc {
 
 namespace {
 
-constexpr int NB = 32;
-constexpr int TT = 64;
+constexpr int NB = 32;   // sub-panel width (diagonal block)
+constexpr int PW = 64;   // panel width
+constexpr int TT = 64;   // trailing tile
+constexpr int KC = 32;   // staged K chunk
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared-memory layout of the factor kernel (element type S):
+//   lkk [NB][NB+1], dinv [NB], then 2 stages of { X [TT][KC + PADX], Y [KC][TT] }
+template <typename S>
+struct FactorSmem {
+  static constexpr int PADX = 16 / (int)sizeof(S);
+  static constexpr int XS = TT * (KC + PADX);
+  static constexpr int YS = KC * TT;
+  static constexpr int STAGE = XS + YS;
+  static constexpr size_t LKK_BYTES = ((sizeof(S) * (NB * (NB + 1) + NB)) + 15) / 16 * 16;
+  static constexpr size_t bytes() { return LKK_BYTES + 2 * sizeof(S) * STAGE; }
+};
+
+// A[i][j] -= sum_{l in [k0, k0+klen)} W[i][l] L[j][l] for rows [r0, n), columns [c0, c1), j <= i.
+// W is read from the lower part (row i), L from the upper part (row l, column j).
+template <typename S>
+__device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, int c0, int c1, int k0, int klen,
+                              S* __restrict__ stages) {
+  using SM = FactorSmem<S>;
+  constexpr int PER = 16 / (int)sizeof(S);  // elements per 16-byte copy
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int n_ti = (n - r0 + TT - 1) / TT;
+  const int nk = (klen + KC - 1) / KC;
+  // tiles (tI, tJ): row tile i0 = r0 + TT*tI, column tile j0 = c0 + TT*tJ with j0 <= i0 + TT - 1;
+  // every row tile has at least one column tile because c0 == r0 or c1 - c0 <= TT.
+  auto cnt_of = [&](int tI) {
+    const int jmax = min(c1, r0 + TT * tI + TT);
+    return jmax > c0 ? (jmax - c0 + TT - 1) / TT : 0;
+  };
+  int n_tiles = 0;
+  for (int tI = 0; tI < n_ti; ++tI) n_tiles += cnt_of(tI);
+  const int total = n_tiles * nk;
+  if (total == 0) return;
+
+  struct It {
+    int tI, tJ, cnt, chunk;
+  };
+  auto advance = [&](It& it) {
+    if (++it.chunk == nk) {
+      it.chunk = 0;
+      if (++it.tJ == it.cnt) {
+        it.tJ = 0;
+        ++it.tI;
+        it.cnt = it.tI < n_ti ? cnt_of(it.tI) : 0;
+      }
+    }
+  };
+
+  auto issue = [&](const It& it, S* buf) {
+    const int i0 = r0 + TT * it.tI, j0 = c0 + TT * it.tJ;
+    const int kc = k0 + it.chunk * KC;
+    S* X = buf;
+    S* Y = buf + SM::XS;
+    // X[ii][l] = A[i0+ii][kc+l]   (TT rows x KC, 16-byte pieces along l)
+    constexpr int XPR = KC / PER;  // pieces per row
+    for (int e = tid; e < TT * XPR; e += blockDim.x) {
+      const int ii = e / XPR, l = (e % XPR) * PER;
+      const int gi = i0 + ii;
+      const bool ok = gi < n && (kc + l) < k0 + klen;
+      const S* src = ok ? A + (long long)gi * ldm + kc + l : A;
+      cp_async16(X + ii * (KC + SM::PADX) + l, src, ok);
+    }
+    // Y[l][jj] = A[kc+l][j0+jj]  (upper part: L^T rows), 16-byte pieces along jj
+    constexpr int YPR = TT / PER;
+    for (int e = tid; e < KC * YPR; e += blockDim.x) {
+      const int l = e / YPR, jj = (e % YPR) * PER;
+      const int gj = j0 + jj;
+      const bool ok = (kc + l) < k0 + klen && gj < n;
+      const S* src = ok ? A + (long long)(kc + l) * ldm + gj : A;
+      cp_async16(Y + l * TT + jj, src, ok);
+    }
+  };
+
+  S acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = szero<S>();
+
+  It it_issue{0, 0, cnt_of(0), 0};
+  It it_comp = it_issue;
+  issue(it_issue, stages);
+  cp_commit();
+  advance(it_issue);
+  for (int s = 0; s < total; ++s) {
+    S* buf = stages + (s & 1) * SM::STAGE;
+    if (s + 1 < total) {
+      issue(it_issue, stages + ((s + 1) & 1) * SM::STAGE);
+      cp_commit();
+      advance(it_issue);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();
+    const int kc = k0 + it_comp.chunk * KC;
+    const int lmax = min(KC, k0 + klen - kc);
+    const S* X = buf;
+    const S* Y = buf + SM::XS;
+#pragma unroll 4
+    for (int l = 0; l < lmax; ++l) {
+      S xa[4], yb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xa[a] = X[(ty + 16 * a) * (KC + SM::PADX) + l];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) yb[b] = Y[l * TT + tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = sfnms(xa[a], yb[b], acc[a][b]);
+    }
+    if (it_comp.chunk == nk - 1) {
+      const int i0 = r0 + TT * it_comp.tI, j0 = c0 + TT * it_comp.tJ;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
+          if (gi < n && gj < c1 && gj <= gi) {
+            S* p = A + (long long)gi * ldm + gj;
+            *p = sadd(*p, acc[a][b]);
+          }
+          acc[a][b] = szero<S>();
+        }
+    }
+    advance(it_comp);
+    __syncthreads();
+  }
+}
+
+// Factor the NB-wide sub-panel starting at column c0 (its columns already hold the Schur
+// complement): diagonal block, then W (lower) and L^T (upper) for the rows below.
+template <typename S>
+__device__ void factor_subpanel(S* __restrict__ A, int n, long long ldm, int c0, S (*lkk)[NB + 1], S* dinv, int& sing) {
+  const int tid = threadIdx.x;
+  const int kb = min(NB, n - c0);
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, j = e % NB;
+    lkk[i][j] = (i < kb && j <= i) ? A[(long long)(c0 + i) * ldm + (c0 + j)] : szero<S>();
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    S d = lkk[j][j];
+    if (sabs2(d) < 1e-60) {
+      if (tid == 0) sing = 1;
+      d = sfrom<S>(1.0, 0.0);
+    }
+    const S inv = sinv(d);
+    const int m = kb - 1 - j;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, l = j + 1 + e % m;
+      if (l <= i) lkk[i][l] = sfnms(smul(lkk[i][j], inv), lkk[l][j], lkk[i][l]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      lkk[j][j] = d;
+      dinv[j] = inv;
+    }
+    for (int i = j + 1 + tid; i < kb; i += blockDim.x) lkk[i][j] = smul(lkk[i][j], inv);
+    __syncthreads();
+  }
+  // diagonal block: W = L d below the diagonal, d on it, L^T above it
+  for (int e = tid; e < kb * kb; e += blockDim.x) {
+    const int i = e / kb, j = e % kb;
+    if (j < i) {
+      A[(long long)(c0 + i) * ldm + (c0 + j)] = smul(lkk[i][j], lkk[j][j]);
+      A[(long long)(c0 + j) * ldm + (c0 + i)] = lkk[i][j];
+    } else if (j == i) {
+      A[(long long)(c0 + i) * ldm + (c0 + i)] = lkk[i][i];
+    }
+  }
+  // rows below: w = a L_kk^-T (= W row), L row = w D^-1
+  for (int i = c0 + kb + tid; i < n; i += blockDim.x) {
+    S w[NB];
+    S* row = A + (long long)i * ldm + c0;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) w[j] = j < kb ? row[j] : szero<S>();
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j < kb) {
+        S acc = w[j];
+#pragma unroll
+        for (int l = 0; l < j; ++l) acc = sfnms(w[l], lkk[j][l], acc);
+        w[j] = acc;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      if (j < kb) {
+        row[j] = w[j];
+        A[(long long)(c0 + j) * ldm + i] = smul(w[j], dinv[j]);
+      }
+  }
+  __syncthreads();
+}
 
 template <typename S>
 __global__ void __launch_bounds__(256) ldlt_kernel(S* __restrict__ mats, int n, long long ldm, long long stride,
@@ -27,125 +246,33 @@ __global__ void __launch_bounds__(256) ldlt_kernel(S* __restrict__ mats, int n, 
   const int f = blockIdx.x;
   if (active && !active[f]) return;
   S* A = mats + f * stride;
-  const int tid = threadIdx.x;
-
+  using SM = FactorSmem<S>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S(*lkk)[NB + 1] = reinterpret_cast<S(*)[NB + 1]>(smem_raw);
   S* dinv = reinterpret_cast<S*>(smem_raw + sizeof(S) * NB * (NB + 1));
-  S(*ws)[TT + 1] = reinterpret_cast<S(*)[TT + 1]>(smem_raw + sizeof(S) * (NB * (NB + 1) + NB));  // (L D) of tile I
-  S(*ls)[TT + 1] = ws + NB;  // L rows of tile J, transposed: ls[l][jj]
+  S* stages = reinterpret_cast<S*>(smem_raw + SM::LKK_BYTES);
   __shared__ int sing;
-  if (tid == 0) sing = 0;
+  if (threadIdx.x == 0) sing = 0;
 
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = min(NB, n - k0);
-    // ---- 1. diagonal block -------------------------------------------------------------
-    __syncthreads();
-    for (int e = tid; e < NB * NB; e += 256) {
-      int i = e / NB, j = e % NB;
-      lkk[i][j] = (i < kb && j <= i) ? A[(long long)(k0 + i) * ldm + (k0 + j)] : szero<S>();
+  for (int k0 = 0; k0 < n; k0 += PW) {
+    const int kb = min(PW, n - k0);
+    factor_subpanel(A, n, ldm, k0, lkk, dinv, sing);
+    if (kb > NB) {
+      // first sub-panel applied to the second: rows >= k0+NB, columns [k0+NB, k0+kb)
+      update_region(A, n, ldm, k0 + NB, k0 + NB, k0 + kb, k0, NB, stages);
+      factor_subpanel(A, n, ldm, k0 + NB, lkk, dinv, sing);
     }
-    __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-      S d = lkk[j][j];
-      if (sabs2(d) < 1e-60) {
-        if (tid == 0) sing = 1;
-        d = sfrom<S>(1.0, 0.0);
-      }
-      S inv = sinv(d);
-      // trailing update inside the block with the unscaled column j
-      int m = kb - 1 - j;
-      for (int e = tid; e < m * m; e += 256) {
-        int i = j + 1 + e / m, l = j + 1 + e % m;
-        if (l <= i) lkk[i][l] = sfnms(smul(lkk[i][j], inv), lkk[l][j], lkk[i][l]);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        lkk[j][j] = d;
-        dinv[j] = inv;
-      }
-      for (int i = j + 1 + tid; i < kb; i += 256) lkk[i][j] = smul(lkk[i][j], inv);
-      __syncthreads();
-    }
-    for (int e = tid; e < kb * kb; e += 256) {
-      int i = e / kb, j = e % kb;
-      if (j <= i) A[(long long)(k0 + i) * ldm + (k0 + j)] = lkk[i][j];
-    }
-    // ---- 2. panel rows: L_i = A_i L_kk^-T D^-1 ------------------------------------------
-    for (int i = k0 + kb + tid; i < n; i += 256) {
-      S w[NB];
-      S* row = A + (long long)i * ldm + k0;
-#pragma unroll
-      for (int j = 0; j < NB; ++j) w[j] = j < kb ? row[j] : szero<S>();
-#pragma unroll
-      for (int j = 0; j < NB; ++j) {
-        if (j < kb) {
-          S acc = w[j];
-#pragma unroll
-          for (int l = 0; l < j; ++l) acc = sfnms(w[l], lkk[j][l], acc);
-          w[j] = acc;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NB; ++j)
-        if (j < kb) row[j] = smul(w[j], dinv[j]);
-    }
-    __syncthreads();
-    // ---- 3. trailing update: A_ij -= sum_l L_il d_l L_jl, i >= j >= k0 + kb ----------------
-    const int r0 = k0 + kb;
-    const int mrows = n - r0;
-    if (mrows <= 0) break;
-    const int nt = (mrows + TT - 1) / TT;
-    const int tx = tid & 15, ty = tid >> 4;
-    for (int tI = 0; tI < nt; ++tI) {
-      for (int tJ = 0; tJ <= tI; ++tJ) {
-        const int i0 = r0 + tI * TT, j0 = r0 + tJ * TT;
-        for (int e = tid; e < TT * NB; e += 256) {
-          int rr = e / NB, l = e % NB;
-          int gi = i0 + rr, gj = j0 + rr;
-          S li = (gi < n && l < kb) ? A[(long long)gi * ldm + k0 + l] : szero<S>();
-          S lj = (gj < n && l < kb) ? A[(long long)gj * ldm + k0 + l] : szero<S>();
-          ws[l][rr] = (l < kb) ? smul(li, lkk[l][l]) : szero<S>();
-          ls[l][rr] = lj;
-        }
-        __syncthreads();
-        S acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = szero<S>();
-#pragma unroll 4
-        for (int l = 0; l < kb; ++l) {
-          S wa[4], lb[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) wa[a] = ws[l][ty + 16 * a];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) lb[b] = ls[l][tx + 16 * b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = sfnms(wa[a], lb[b], acc[a][b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
-            if (gi < n && gj < n && gj <= gi) {
-              S* p = A + (long long)gi * ldm + gj;
-              *p = sadd(*p, acc[a][b]);
-            }
-          }
-        __syncthreads();
-      }
-    }
+    // rank-kb trailing update of the lower triangle beyond the panel
+    if (k0 + kb < n) update_region(A, n, ldm, k0 + kb, k0 + kb, n, k0, kb, stages);
   }
   __syncthreads();
-  if (tid == 0 && sing) atomicOr(status, kStatSingular);
+  if (threadIdx.x == 0 && sing) atomicOr(status, kStatSingular);
 }
 
-// Forward substitution y = L^-1 b for a block of RB right-hand sides (in place), then
-// w_q = sum_i y_i^2 / d_i - |b_q|^2.  Grid: (matrix f, RHS block).
+// Forward substitution with the W storage, for a block of RB right-hand sides (in place):
+//   y_i = b_i - sum_{l<i} W_il u_l,  u_l = y_l / d_l   (since L_il = W_il / d_l)
+//   w_q = sum_i y_i^2 / d_i - |b_q|^2 = sum_i u_i^2 d_i - |b_q|^2.
+// The right-hand-side buffer ends up holding u. Grid: (matrix f, RHS block).
 constexpr int RB = 32;
 
 template <typename S>
@@ -162,9 +289,10 @@ __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ m
   const int tid = threadIdx.x;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S(*ls)[NB + 1] = reinterpret_cast<S(*)[NB + 1]>(smem_raw);                             // L[k0+i][l0+l]
-  S(*ys)[RB + 1] = reinterpret_cast<S(*)[RB + 1]>(smem_raw + sizeof(S) * NB * (NB + 1));  // y[l0+l][q]
+  S(*ls)[NB + 1] = reinterpret_cast<S(*)[NB + 1]>(smem_raw);                             // W[k0+i][l0+l]
+  S(*ys)[RB + 1] = reinterpret_cast<S(*)[RB + 1]>(smem_raw + sizeof(S) * NB * (NB + 1));  // u[l0+l][q]
   S(*accs)[RB + 1] = ys + NB;                                                              // panel partial sums
+  S* dv = reinterpret_cast<S*>(accs + NB);                                                 // d of the panel
 
   const int ii = tid & 31, qg = tid >> 5;  // row in panel, group of 4 rhs
   for (int k0 = 0; k0 < n; k0 += NB) {
@@ -174,17 +302,17 @@ __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ m
     for (int u = 0; u < 4; ++u) acc[u] = szero<S>();
     for (int l0 = 0; l0 < k0; l0 += NB) {
       for (int e = tid; e < NB * NB; e += 256) {
-        int i = e / NB, l = e % NB;
+        const int i = e / NB, l = e % NB;
         ls[i][l] = (i < kb) ? L[(long long)(k0 + i) * ldm + l0 + l] : szero<S>();
       }
       for (int e = tid; e < NB * RB; e += 256) {
-        int q = e / NB, l = e % NB;
+        const int q = e / NB, l = e % NB;
         ys[l][q] = (q < nq) ? Y[(long long)q * ldr + l0 + l] : szero<S>();
       }
       __syncthreads();
 #pragma unroll 8
       for (int l = 0; l < NB; ++l) {
-        S a = ls[ii][l];
+        const S a = ls[ii][l];
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[u] = sfnms(a, ys[l][qg * 4 + u], acc[u]);
       }
@@ -192,11 +320,11 @@ __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ m
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) accs[ii][qg * 4 + u] = acc[u];
-    // diagonal block of the panel
     for (int e = tid; e < NB * NB; e += 256) {
-      int i = e / NB, l = e % NB;
+      const int i = e / NB, l = e % NB;
       ls[i][l] = (i < kb && l < i) ? L[(long long)(k0 + i) * ldm + k0 + l] : szero<S>();
     }
+    if (tid < NB) dv[tid] = tid < kb ? L[(long long)(k0 + tid) * ldm + k0 + tid] : sfrom<S>(1.0, 0.0);
     __syncthreads();
     if (tid < nq) {
       const int q = tid;
@@ -204,19 +332,21 @@ __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ m
       for (int i = 0; i < kb; ++i) {
         S v = sadd(y[i], accs[i][q]);
         for (int l = 0; l < i; ++l) v = sfnms(ls[i][l], ys[l][q], v);
-        ys[i][q] = v;
-        y[i] = v;
+        const S u = smul(v, sinv(dv[i]));
+        ys[i][q] = u;
+        y[i] = u;
       }
     }
     __syncthreads();
   }
-  // w_q = sum_i y_i^2 / d_i - |b|^2  (FP64 accumulation)
+  // w_q = sum_i u_i^2 d_i - |b|^2  (FP64 accumulation)
+  __shared__ double red[2][8];
   for (int q = 0; q < nq; ++q) {
     double sr = 0.0, si = 0.0;
-    const S* y = Y + (long long)q * ldr;
+    const S* u = Y + (long long)q * ldr;
     for (int i = tid; i < n; i += 256) {
-      S yi = y[i];
-      S t = smul(smul(yi, yi), sinv(L[(long long)i * ldm + i]));
+      const S ui = u[i];
+      const S t = smul(smul(ui, ui), L[(long long)i * ldm + i]);
       sr += sre(t);
       si += sim(t);
     }
@@ -224,7 +354,6 @@ __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ m
       sr += __shfl_down_sync(0xffffffffu, sr, o);
       si += __shfl_down_sync(0xffffffffu, si, o);
     }
-    __shared__ double red[2][8];
     if ((tid & 31) == 0) {
       red[0][tid >> 5] = sr;
       red[1][tid >> 5] = si;
@@ -232,9 +361,9 @@ __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ m
     __syncthreads();
     if (tid == 0) {
       double a = 0.0, b = 0.0;
-      for (int u = 0; u < 8; ++u) {
-        a += red[0][u];
-        b += red[1][u];
+      for (int v = 0; v < 8; ++v) {
+        a += red[0][v];
+        b += red[1][v];
       }
       double* o = w + f * w_stride + (long long)(q0 + q) * 2;
       o[0] = a - bnorm2[(long long)f * r + q0 + q];
@@ -245,18 +374,14 @@ __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ m
 }
 
 template <typename S>
-size_t ldlt_smem() {
-  return sizeof(S) * (NB * (NB + 1) + NB + 2 * NB * (TT + 1));
-}
-template <typename S>
 size_t solve_smem() {
-  return sizeof(S) * (NB * (NB + 1) + 2 * NB * (RB + 1));
+  return sizeof(S) * (NB * (NB + 1) + 2 * NB * (RB + 1) + NB);
 }
 
 template <typename S>
 int run_ldlt(S* mats, int n, long long ldm, long long stride, int F, const int* active, unsigned* status, cudaStream_t s) {
   static bool attr = false;
-  size_t sm = ldlt_smem<S>();
+  const size_t sm = FactorSmem<S>::bytes();
   if (!attr) {
     if (cudaFuncSetAttribute(ldlt_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
     attr = true;
@@ -269,7 +394,7 @@ template <typename S>
 int run_solve(const S* mats, int n, long long ldm, long long stride, S* rhs, int r, long long ldr, long long rhs_stride,
               const double* bnorm2, int F, double* w, long long w_stride, const int* active, cudaStream_t s) {
   static bool attr = false;
-  size_t sm = solve_smem<S>();
+  const size_t sm = solve_smem<S>();
   if (!attr) {
     if (cudaFuncSetAttribute(ldlt_solve_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
       return -1;
@@ -284,6 +409,8 @@ int run_solve(const S* mats, int n, long long ldm, long long stride, S* rhs, int
 
 int launch_ldlt(MatKind kind, void* mats, int n, long long ldm, long long stride, int F, const int* active,
                 unsigned* status, cudaStream_t s) {
+  // 16-byte staging needs even leading dimensions and 16-byte aligned matrices
+  if ((ldm % 4) || (stride % 4) || (reinterpret_cast<uintptr_t>(mats) & 15)) return -1;
   switch (kind) {
     case MatKind::RealF32: return run_ldlt((float*)mats, n, ldm, stride, F, active, status, s);
     case MatKind::CplxF32: return run_ldlt((float2*)mats, n, ldm, stride, F, active, status, s);
