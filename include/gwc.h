@@ -95,7 +95,14 @@ typedef struct {
   int batch;             /* frequencies per internal batch (0: chosen from free memory)       */
   int profile;           /* nonzero: time the chi0, factorisation and solve kernels with CUDA
                             events on the launching stream (accumulated in gwc_stats)          */
+  int qp_mode;           /* gwc_qp_mode: how gwc_qp_solve and the request step get eps^QP     */
 } gwc_options;
+
+/* GWC_QP_SECANT: iterate the G_dH W0 QP equation (eq quasiparticle_equation with the shifted
+ *   self-energy of eq hedin_sigma_spectral) by the secant method from eps_n;
+ * GWC_QP_HEDIN: the GW+C QP energy of eq QPGWC, eps_n + dH_n, which is the exact fixed point of
+ *   that equation (one self-energy evaluation per core instead of one per iterate). */
+typedef enum { GWC_QP_SECANT = 0, GWC_QP_HEDIN = 1 } gwc_qp_mode;
 
 typedef struct {
   long long chi0_builds;     /* polarizability builds launched (one per frequency)            */
@@ -114,7 +121,7 @@ typedef struct {
 typedef struct gwc_ctx gwc_ctx;
 
 /* Fills o with the defaults: eta 1e-3, n_im 32, xi0 1, BF16X3, DIAG, n_t 2^16, t_max 2000,
- * max_qp_iter 50, qp_tol 1e-7, batch 0, profile 0. */
+ * max_qp_iter 50, qp_tol 1e-7, batch 0, profile 0, qp_mode SECANT. */
 gwc_status gwc_default_options(gwc_options* o);
 
 /* Device bytes a context of this shape allocates (resident copies + workspace + the
@@ -206,6 +213,56 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
 gwc_status gwc_cumulant_spectrum_noalloc(const double* omega_rel, int n_omega, const double* im_sigma, int n_core,
                                          int n_t, double t_max, double eta, double* a_out, double* nu_out,
                                          void* stream);
+
+/* ---- Request mode: one molecule's spectra + QP as one capturable step --------------------------
+ * A "request" is the work a user of the serving and batched forms asks for: the decoupled Im Sigma
+ * of every core on a relative grid omega_rel (eq cd_sigma_imaginary_decoupled; all cores share the
+ * residue frequencies |omega_rel| + i eta, so one dielectric build serves every core), the QP energies
+ * (Hedin shift and, with GWC_QP_SECANT, the secant iteration) and one cumulant spectrum per core.
+ *
+ * gwc_request_plan: HOST omega_rel [n_omega] (relative to each core's eps_n, ascending); builds the
+ *   residue plan on the device and sizes the result buffers. Synchronises `stream`. Needs the DIAG
+ *   decoupling mode.
+ * gwc_request_step: enqueues the whole request (imaginary-axis W table, QP, residues, decoupled
+ *   Im Sigma, spectra) on `stream` with no host synchronisation and no allocation; after one call
+ *   outside stream capture it may be captured into a CUDA graph (gwc_batch_create does so).
+ * gwc_request_results: device pointers to the context-owned results of the last step:
+ *   eps_qp, dh [n_core], iters [n_core] (int), im_sigma [n_core][n_omega], a [n_core][n_t], nu [n_t]. */
+typedef struct {
+  const double* eps_qp;
+  const double* dh;
+  const int* iters;
+  const double* im_sigma;
+  const double* a;
+  const double* nu;
+  int n_core, n_omega, n_t;
+} gwc_request_results;
+
+gwc_status gwc_request_plan(gwc_ctx* ctx, const double* omega_rel, int n_omega, void* stream);
+gwc_status gwc_request_step(gwc_ctx* ctx, void* stream);
+gwc_status gwc_request_results_get(const gwc_ctx* ctx, gwc_request_results* out);
+/* Copies the results of the last step into caller buffers (host or device; any may be NULL),
+ * enqueued on `stream`: eps_qp, dh [n_core], iters [n_core] int, im_sigma [n_core][n_omega],
+ * a [n_core][n_t], nu [n_t]. */
+gwc_status gwc_request_copy_results(const gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, double* im_sigma,
+                                    double* a, double* nu, void* stream);
+
+/* Frequencies per internal batch chosen by timing the request step for 16, 32, ..., up to the
+ * capacity the context was created with (cached per shape bucket and precision for the process).
+ * Needs a request plan; synchronises `stream`; *chosen receives the batch used from now on. */
+gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen);
+
+/* ---- Batched form: many molecules of uneven size in one CUDA-graph launch ----------------------
+ * gwc_batch_create captures the request step of every context (each with a request plan) on its
+ * own forked stream into one CUDA graph; it first runs each step once outside capture, and
+ * synchronises `stream` before capturing on a private stream. The contexts
+ * must outlive the batch and must not be used concurrently with a launch of it.
+ * gwc_batch_launch replays the whole graph on `stream` (results in each context, see
+ * gwc_request_results_get). */
+typedef struct gwc_batch gwc_batch;
+gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* stream);
+gwc_status gwc_batch_launch(gwc_batch* batch, void* stream);
+void gwc_batch_destroy(gwc_batch* batch);
 
 /* Synchronises `stream` and reports the first device-side status raised since the
  * previous gwc_sync (then clears it). */

@@ -6,6 +6,9 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -193,6 +196,7 @@ gwc_status validate_options(const gwc_options* o, int n_core) {
   if (o->max_qp_iter < 2 || o->max_qp_iter > 200) return fail(nullptr, GWC_ERR_INVALID_ARG, "max_qp_iter must be in 2..200");
   if (!(o->qp_tol > 0.0)) return fail(nullptr, GWC_ERR_INVALID_ARG, "qp_tol must be > 0");
   if (o->batch < 0 || o->batch > 4096) return fail(nullptr, GWC_ERR_INVALID_ARG, "batch must be in 0..4096");
+  if (o->qp_mode < 0 || o->qp_mode > 1) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad qp_mode");
   (void)n_core;
   return GWC_OK;
 }
@@ -245,28 +249,6 @@ int choose_batch(const gwc_system* s, const gwc_options* o, const Sizes& z) {
 
 gwc_status upload(gwc_ctx* ctx, void* dst, const void* src, size_t bytes, int memory, cudaStream_t st) {
   CU(cudaMemcpyAsync(dst, src, bytes, memory == GWC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
-  return GWC_OK;
-}
-
-gwc_status ensure_pinned_i(gwc_ctx* ctx, size_t n) {
-  if (n <= ctx->h_pin_i_cap) return GWC_OK;
-  for (auto& r : ctx->ev_pending) {
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
-  }
-  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-  if (ctx->h_pin_i) cudaFreeHost(ctx->h_pin_i);
-  ctx->h_pin_i = nullptr;
-  CU(cudaMallocHost((void**)&ctx->h_pin_i, n * sizeof(int)));
-  ctx->h_pin_i_cap = n;
-  return GWC_OK;
-}
-gwc_status ensure_pinned_d(gwc_ctx* ctx, size_t n) {
-  if (n <= ctx->h_pin_d_cap) return GWC_OK;
-  if (ctx->h_pin_d) cudaFreeHost(ctx->h_pin_d);
-  ctx->h_pin_d = nullptr;
-  CU(cudaMallocHost((void**)&ctx->h_pin_d, n * sizeof(double)));
-  ctx->h_pin_d_cap = n;
   return GWC_OK;
 }
 
@@ -340,70 +322,47 @@ double factor_flop(int n, bool cplx, int F) {
 }
 
 // ---- imaginary-axis W table --------------------------------------------------------------------
-gwc_status compute_wim(gwc_ctx* ctx, cudaStream_t st) {
-  if (ctx->wim_valid) return GWC_OK;
+// Enqueues W^c_mn(i xi_k) for all states m and cores n, k = 0..n_im (node n_im is xi = 0), without
+// host synchronisation or allocation (the frequencies were uploaded at creation).
+gwc_status enqueue_wim(gwc_ctx* ctx, cudaStream_t st) {
   const int nodes = ctx->opt.n_im + 1;
   MatKind rk = real_kind(ctx);
   const size_t per_real = (size_t)ctx->n_aux * ctx->ldm * mat_elem_bytes(rk);
   int fb = (int)std::max<size_t>(1, std::min<size_t>(ctx->mats_bytes / per_real, (size_t)ctx->batch));
   fb = std::min(fb, nodes);
   const int r = ctx->n_states * ctx->n_core;
-  std::vector<double> xi(ctx->opt.n_im);
-  CU(cudaMemcpyAsync(xi.data(), ctx->d_xi, sizeof(double) * ctx->opt.n_im, cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
-  TRY(ensure_pinned_d(ctx, 2 * (size_t)nodes));
-  for (int k = 0; k < nodes; ++k) {
-    ctx->h_pin_d[2 * k] = 0.0;
-    ctx->h_pin_d[2 * k + 1] = k < ctx->opt.n_im ? xi[k] : 0.0;
-  }
   const size_t plane = (size_t)ctx->n_states * ctx->n_core;
   const long long stride = (long long)ctx->n_aux * ctx->ldm;
-  double* d_zall = nullptr;
-  TRY(dalloc(ctx, &d_zall, 2 * (size_t)nodes));
-  cudaError_t ce = cudaMemcpyAsync(d_zall, ctx->h_pin_d, sizeof(double) * 2 * nodes, cudaMemcpyHostToDevice, st);
-  if (ce != cudaSuccess) {
-    cudaFree(d_zall);
-    return fail(ctx, GWC_ERR_CUDA, cudaGetErrorString(ce));
-  }
-  gwc_status res = GWC_OK;
-  for (int k0 = 0; k0 < nodes && res == GWC_OK; k0 += fb) {
+  for (int k0 = 0; k0 < nodes; k0 += fb) {
     const int nb = std::min(fb, nodes - k0);
-    res = run_chi0(ctx, false, nb, d_zall + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st);
-    if (res != GWC_OK) break;
+    TRY(run_chi0(ctx, false, nb, ctx->d_zim + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st));
     cudaEvent_t ev = ev_begin(ctx, st);
-    int n = launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st);
+    LAUNCH(launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st));
     ev_end(ctx, kClsFactor, ev, st);
     ctx->stats.factor_flop += factor_flop(ctx->n_aux, false, nb);
-    if (n < 0) {
-      res = fail(ctx, GWC_ERR_CUDA, "ldlt launch failed");
-      break;
-    }
-    ctx->stats.kernel_launches += n;
     ctx->stats.factorizations += nb;
-    for (int u = 0; u < nb && res == GWC_OK; ++u) {
+    for (int u = 0; u < nb; ++u) {
       const int k = k0 + u;
-      int n1 = launch_rhs_gather(rk, ctx->d_o_core, ctx->n_aux, ctx->d_rowmap, 1, r, ctx->n_aux, ctx->d_rhs_im, ctx->ldm,
-                                 0, ctx->d_bnorm, st);
+      LAUNCH(launch_rhs_gather(rk, ctx->d_o_core, ctx->n_aux, ctx->d_rowmap, 1, r, ctx->n_aux, ctx->d_rhs_im, ctx->ldm, 0,
+                               ctx->d_bnorm, st));
       char* mat = (char*)ctx->d_mats + (size_t)u * stride * mat_elem_bytes(rk);
       cudaEvent_t evs = ev_begin(ctx, st);
-      int n2 = launch_ldlt_solve_w(rk, mat, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs_im, r, ctx->ldm, 0, ctx->d_bnorm, 1,
-                                   ctx->d_wtmp, 0, nullptr, st);
+      LAUNCH(launch_ldlt_solve_w(rk, mat, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs_im, r, ctx->ldm, 0, ctx->d_bnorm, 1,
+                                 ctx->d_wtmp, 0, nullptr, st));
       ev_end(ctx, kClsSolve, evs, st);
-      if (n1 < 0 || n2 < 0) {
-        res = fail(ctx, GWC_ERR_CUDA, "imaginary-axis solve launch failed");
-        break;
-      }
-      ctx->stats.kernel_launches += n1 + n2;
       // real part of w -> W table plane k
-      ce = cudaMemcpy2DAsync(ctx->d_wim + (size_t)k * plane, sizeof(double), ctx->d_wtmp, 2 * sizeof(double),
-                             sizeof(double), plane, cudaMemcpyDeviceToDevice, st);
-      if (ce != cudaSuccess) res = fail(ctx, GWC_ERR_CUDA, cudaGetErrorString(ce));
+      CU(cudaMemcpy2DAsync(ctx->d_wim + (size_t)k * plane, sizeof(double), ctx->d_wtmp, 2 * sizeof(double), sizeof(double),
+                           plane, cudaMemcpyDeviceToDevice, st));
     }
   }
-  cudaStreamSynchronize(st);
-  cudaFree(d_zall);
-  if (res == GWC_OK) ctx->wim_valid = true;
-  return res;
+  return GWC_OK;
+}
+
+gwc_status compute_wim(gwc_ctx* ctx, cudaStream_t st) {
+  if (ctx->wim_valid) return GWC_OK;
+  TRY(enqueue_wim(ctx, st));
+  ctx->wim_valid = true;
+  return GWC_OK;
 }
 
 // ---- residue W for a list of (frequency, state m) pairs ---------------------------------------------
@@ -429,6 +388,37 @@ gwc_status residue_batches(gwc_ctx* ctx, int n_pairs, const double* z_dev, const
                                ctx->d_bnorm, nb, w_out + (size_t)p0 * r * 2, (long long)r * 2, act, st));
     ev_end(ctx, kClsSolve, evs, st);
   }
+  return GWC_OK;
+}
+
+// QP rounds on the device (eqs hedin_shift, quasiparticle_equation, hedin_sigma_spectral, QPGWC).
+// With poll, the host reads the 4-byte "all converged" flag every 4 rounds and stops early;
+// without, all rounds are enqueued and finished cores cost only empty launches (capturable).
+gwc_status enqueue_qp(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, bool poll, cudaStream_t st) {
+  const int nc = ctx->n_core, no = ctx->n_occ;
+  const int np = nc * no;
+  const bool hedin = ctx->opt.qp_mode == GWC_QP_HEDIN;
+  LAUNCH(launch_qp_init(ctx->d_eps, ctx->d_core_idx, nc, ctx->d_qp, st));
+  const int rounds = hedin ? 1 : ctx->opt.max_qp_iter + 2;
+  for (int r = 0; r < rounds; ++r) {
+    LAUNCH(launch_qp_pairs(ctx->d_eps, ctx->d_core_idx, nc, no, ctx->eps_f, ctx->opt.eta, ctx->d_qp, ctx->d_qp_z,
+                           ctx->d_qp_active, ctx->d_qp_fac, ctx->d_all_done, st));
+    TRY(residue_batches(ctx, np, ctx->d_qp_z, ctx->d_qp_rowmap, 1, ctx->d_qp_w, ctx->d_qp_active, st));
+    LAUNCH(launch_qp_assemble_update(ctx->d_eps, ctx->n_states, no, nc, ctx->d_core_idx, ctx->eps_f, ctx->d_xi,
+                                     ctx->d_wxi, ctx->opt.n_im, ctx->d_wim, ctx->d_qp_w, ctx->d_qp_fac, ctx->d_sx,
+                                     ctx->d_vxc_eff, ctx->opt.qp_tol, ctx->opt.max_qp_iter, ctx->d_qp, ctx->d_all_done,
+                                     st));
+    if (poll && (r & 3) == 3) {
+      int done = 0;
+      CU(cudaMemcpyAsync(&done, ctx->d_all_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      if (done) break;
+    }
+  }
+  if (hedin)
+    LAUNCH(launch_qp_finish_hedin(ctx->d_qp, ctx->d_eps, ctx->d_core_idx, nc, eps_qp, dh, iters, st));
+  else
+    LAUNCH(launch_qp_finish(ctx->d_qp, nc, eps_qp, dh, iters, ctx->d_status, st));
   return GWC_OK;
 }
 
@@ -479,6 +469,7 @@ gwc_status gwc_default_options(gwc_options* o) {
   o->qp_tol = 1e-7;
   o->batch = 0;
   o->profile = 0;
+  o->qp_mode = GWC_QP_SECANT;
   return GWC_OK;
 }
 
@@ -561,6 +552,11 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
     }
     CTRY(dalloc(ctx, &ctx->d_xi, o->n_im));
     CTRY(dalloc(ctx, &ctx->d_wxi, o->n_im));
+    std::vector<double> zim(2 * (o->n_im + 1), 0.0);
+    for (int k = 0; k < o->n_im; ++k) zim[2 * k + 1] = xi[k];
+    CTRY(dalloc(ctx, &ctx->d_zim, zim.size()));
+    if (cudaMemcpy(ctx->d_zim, zim.data(), sizeof(double) * zim.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(ctx, GWC_ERR_CUDA, "grid upload failed"));
     if (cudaMemcpy(ctx->d_xi, xi.data(), sizeof(double) * o->n_im, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(ctx->d_wxi, wx.data(), sizeof(double) * o->n_im, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(ctx, GWC_ERR_CUDA, "grid upload failed"));
@@ -569,6 +565,7 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   CTRY(dalloc(ctx, &ctx->d_wim, (size_t)(o->n_im + 1) * plane));
   // workspace
   ctx->batch = choose_batch(s, o, z);
+  ctx->batch_cap = ctx->batch;
   ctx->mats_bytes = (size_t)ctx->batch * s->n_aux * z.ldm * z.elem_c;
   {
     char* p = nullptr;
@@ -633,7 +630,9 @@ void gwc_destroy(gwc_ctx* ctx) {
                   ctx->d_wtmp, ctx->d_rhs_im, ctx->d_status, ctx->d_pidx, ctx->d_wres, ctx->d_pair_m, ctx->d_pair_w,
                   ctx->d_grid_w, ctx->d_qp, ctx->d_qp_z, ctx->d_qp_active, ctx->d_qp_fac, ctx->d_qp_w,
                   ctx->d_qp_rowmap, ctx->d_all_done, ctx->d_cw_a, ctx->d_cw_b, ctx->d_coef, ctx->d_tw,
-                  ctx->d_pair_z, ctx->d_pair_rows};
+                  ctx->d_pair_z, ctx->d_pair_rows, ctx->d_zim, ctx->d_req_wrel, ctx->d_req_z, ctx->d_req_rows,
+                  ctx->d_req_pair_of, ctx->d_req_w, ctx->d_req_im, ctx->d_req_a, ctx->d_req_nu, ctx->d_req_eqp,
+                  ctx->d_req_dh, ctx->d_req_it};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& r : ctx->ev_pending) {
@@ -781,27 +780,7 @@ gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, vo
   if (!eps_qp || !dh || !iters) return fail(ctx, GWC_ERR_INVALID_ARG, "need eps_qp, dh, iters");
   cudaStream_t st = (cudaStream_t)stream;
   TRY(compute_wim(ctx, st));
-  const int nc = ctx->n_core, no = ctx->n_occ;
-  const int np = nc * no;
-  LAUNCH(launch_qp_init(ctx->d_eps, ctx->d_core_idx, nc, ctx->d_qp, st));
-  const int rounds = ctx->opt.max_qp_iter + 2;
-  for (int r = 0; r < rounds; ++r) {
-    LAUNCH(launch_qp_pairs(ctx->d_eps, ctx->d_core_idx, nc, no, ctx->eps_f, ctx->opt.eta, ctx->d_qp, ctx->d_qp_z,
-                           ctx->d_qp_active, ctx->d_qp_fac, ctx->d_all_done, st));
-    TRY(residue_batches(ctx, np, ctx->d_qp_z, ctx->d_qp_rowmap, 1, ctx->d_qp_w, ctx->d_qp_active, st));
-    LAUNCH(launch_qp_assemble_update(ctx->d_eps, ctx->n_states, no, nc, ctx->d_core_idx, ctx->eps_f, ctx->d_xi,
-                                     ctx->d_wxi, ctx->opt.n_im, ctx->d_wim, ctx->d_qp_w, ctx->d_qp_fac, ctx->d_sx,
-                                     ctx->d_vxc_eff, ctx->opt.qp_tol, ctx->opt.max_qp_iter, ctx->d_qp, ctx->d_all_done,
-                                     st));
-    // every 4 rounds, stop early if all cores are done (one 4-byte read)
-    if ((r & 3) == 3) {
-      int done = 0;
-      CU(cudaMemcpyAsync(&done, ctx->d_all_done, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CU(cudaStreamSynchronize(st));
-      if (done) break;
-    }
-  }
-  LAUNCH(launch_qp_finish(ctx->d_qp, nc, eps_qp, dh, iters, ctx->d_status, st));
+  TRY(enqueue_qp(ctx, eps_qp, dh, iters, true, st));
   return check_stream_error(ctx);
 }
 
@@ -825,6 +804,274 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
   LAUNCH(launch_cumulant_spectrum(omega_rel, n_omega, im_sigma, (int)nc, (int)nt, ctx->opt.t_max, ctx->opt.eta,
                                   ctx->d_cw_a, ctx->d_cw_b, ctx->d_coef, ctx->d_tw, a_out, nu_out, st));
   return check_stream_error(ctx);
+}
+
+// ---- request mode ----------------------------------------------------------------------------------
+gwc_status gwc_request_plan(gwc_ctx* ctx, const double* omega_rel, int n_omega, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!omega_rel || n_omega < 1 || n_omega > 8192)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "need omega_rel and 1 <= n_omega <= 8192");
+  if (ctx->opt.dec != GWC_DECOUPLE_DIAG)
+    return fail(ctx, GWC_ERR_UNSUPPORTED, "request mode computes the DIAG decoupled Im Sigma only");
+  for (int j = 0; j < n_omega; ++j) {
+    if (!std::isfinite(omega_rel[j])) return fail(ctx, GWC_ERR_INVALID_ARG, "omega_rel must be finite");
+    if (j > 0 && !(omega_rel[j] > omega_rel[j - 1])) return fail(ctx, GWC_ERR_INVALID_ARG, "omega_rel must ascend");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nc = ctx->n_core;
+  // one residue pair per grid point with f != 0 for the (occupied) cores: w_rel <= 0 (eq cd_prefactors)
+  auto th = [](double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); };
+  std::vector<int> pair_of(n_omega, -1), rows;
+  std::vector<double> z;
+  for (int j = 0; j < n_omega; ++j) {
+    bool any = false;
+    for (int c = 0; c < nc; ++c) {
+      const double ec = ctx->h_eps[ctx->h_core[c]], w = ec + omega_rel[j];
+      const double f = -th(ctx->eps_f - ec) * th(ec - w) + th(ec - ctx->eps_f) * th(w - ec);
+      any = any || f != 0.0;
+    }
+    if (!any) continue;
+    pair_of[j] = (int)(z.size() / 2);
+    z.push_back(std::fabs(omega_rel[j]));
+    z.push_back(ctx->opt.eta);
+    for (int c = 0; c < nc; ++c) rows.push_back(ctx->h_core[c] * nc + c);  // o_core[core c][c]: O^P_cc
+  }
+  const int np = (int)(z.size() / 2);
+  std::vector<double> wrel((size_t)nc * n_omega);
+  for (int c = 0; c < nc; ++c)
+    for (int j = 0; j < n_omega; ++j) wrel[(size_t)c * n_omega + j] = omega_rel[j];
+  const size_t nt = ctx->opt.n_t;
+  TRY(dalloc(ctx, &ctx->d_req_wrel, wrel.size()));
+  TRY(dalloc(ctx, &ctx->d_req_z, std::max<size_t>(2, z.size())));
+  TRY(dalloc(ctx, &ctx->d_req_rows, std::max<size_t>(1, rows.size())));
+  TRY(dalloc(ctx, &ctx->d_req_pair_of, n_omega));
+  TRY(dalloc(ctx, &ctx->d_req_w, std::max<size_t>(1, (size_t)np) * nc * 2));
+  TRY(dalloc(ctx, &ctx->d_req_im, (size_t)nc * n_omega));
+  TRY(dalloc(ctx, &ctx->d_req_a, (size_t)nc * nt));
+  TRY(dalloc(ctx, &ctx->d_req_nu, nt));
+  TRY(dalloc(ctx, &ctx->d_req_eqp, nc));
+  TRY(dalloc(ctx, &ctx->d_req_dh, nc));
+  TRY(dalloc(ctx, &ctx->d_req_it, nc));
+  if (nc * nt * 2 > ctx->cw_cap) {
+    TRY(dalloc(ctx, &ctx->d_cw_a, nc * nt * 2));
+    TRY(dalloc(ctx, &ctx->d_cw_b, nc * nt * 2));
+    TRY(dalloc(ctx, &ctx->d_tw, nt));
+    ctx->cw_cap = nc * nt * 2;
+  }
+  if ((size_t)nc * n_omega > ctx->coef_cap) {
+    TRY(dalloc(ctx, &ctx->d_coef, (size_t)nc * n_omega));
+    ctx->coef_cap = (size_t)nc * n_omega;
+  }
+  CU(cudaMemcpyAsync(ctx->d_req_wrel, wrel.data(), sizeof(double) * wrel.size(), cudaMemcpyHostToDevice, st));
+  if (np > 0) {
+    CU(cudaMemcpyAsync(ctx->d_req_z, z.data(), sizeof(double) * z.size(), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(ctx->d_req_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, st));
+  }
+  CU(cudaMemcpyAsync(ctx->d_req_pair_of, pair_of.data(), sizeof(int) * n_omega, cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  ctx->req_n_omega = n_omega;
+  ctx->req_n_pairs = np;
+  return check_stream_error(ctx);
+}
+
+gwc_status gwc_request_step(gwc_ctx* ctx, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->req_n_omega <= 0) return fail(ctx, GWC_ERR_INVALID_ARG, "no request plan (call gwc_request_plan first)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nc = ctx->n_core;
+  TRY(enqueue_wim(ctx, st));
+  ctx->wim_valid = true;
+  TRY(enqueue_qp(ctx, ctx->d_req_eqp, ctx->d_req_dh, ctx->d_req_it, false, st));
+  if (ctx->req_n_pairs > 0)
+    TRY(residue_batches(ctx, ctx->req_n_pairs, ctx->d_req_z, ctx->d_req_rows, nc, ctx->d_req_w, nullptr, st));
+  LAUNCH(launch_request_dec(ctx->d_eps, ctx->d_core_idx, nc, ctx->eps_f, ctx->d_req_wrel, ctx->req_n_omega,
+                            ctx->d_req_pair_of, ctx->d_req_w, ctx->d_req_im, st));
+  LAUNCH(launch_cumulant_spectrum(ctx->d_req_wrel, ctx->req_n_omega, ctx->d_req_im, nc, ctx->opt.n_t, ctx->opt.t_max,
+                                  ctx->opt.eta, ctx->d_cw_a, ctx->d_cw_b, ctx->d_coef, ctx->d_tw, ctx->d_req_a,
+                                  ctx->d_req_nu, st));
+  return check_stream_error(ctx);
+}
+
+gwc_status gwc_request_results_get(const gwc_ctx* ctx, gwc_request_results* out) {
+  if (!ctx || !out) return GWC_ERR_INVALID_ARG;
+  if (ctx->req_n_omega <= 0) return GWC_ERR_INVALID_ARG;
+  out->eps_qp = ctx->d_req_eqp;
+  out->dh = ctx->d_req_dh;
+  out->iters = ctx->d_req_it;
+  out->im_sigma = ctx->d_req_im;
+  out->a = ctx->d_req_a;
+  out->nu = ctx->d_req_nu;
+  out->n_core = ctx->n_core;
+  out->n_omega = ctx->req_n_omega;
+  out->n_t = ctx->opt.n_t;
+  return GWC_OK;
+}
+
+gwc_status gwc_request_copy_results(const gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, double* im_sigma,
+                                    double* a, double* nu, void* stream) {
+  if (!ctx || ctx->req_n_omega <= 0) return GWC_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nc = ctx->n_core, nw = ctx->req_n_omega, nt = ctx->opt.n_t;
+  struct Cp {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  } cps[] = {{eps_qp, ctx->d_req_eqp, nc * 8}, {dh, ctx->d_req_dh, nc * 8}, {iters, ctx->d_req_it, nc * 4},
+             {im_sigma, ctx->d_req_im, nc * nw * 8}, {a, ctx->d_req_a, nc * nt * 8}, {nu, ctx->d_req_nu, nt * 8}};
+  for (auto& c : cps)
+    if (c.dst && cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyDefault, st) != cudaSuccess) return GWC_ERR_CUDA;
+  return GWC_OK;
+}
+
+// ---- autotuner: frequencies per batch, timed on the request step, cached per shape bucket ------------
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;  // (n_aux/128, n_ov/4096, n_core, prec) -> batch
+}  // namespace
+
+gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->req_n_omega <= 0) return fail(ctx, GWC_ERR_INVALID_ARG, "no request plan (call gwc_request_plan first)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto key = std::make_tuple((ctx->n_aux + 127) / 128, (ctx->n_ov + 4095) / 4096, ctx->n_core, ctx->opt.prec);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      ctx->batch = std::min(it->second, ctx->batch_cap);
+      if (chosen) *chosen = ctx->batch;
+      return GWC_OK;
+    }
+  }
+  const int saved_profile = ctx->opt.profile;
+  ctx->opt.profile = 0;
+  int best = ctx->batch_cap;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  gwc_status res = GWC_OK;
+  for (int f = 16; f <= ctx->batch_cap && res == GWC_OK; f *= 2) {
+    ctx->batch = f;
+    res = gwc_request_step(ctx, stream);  // warm-up for this shape
+    if (res != GWC_OK) break;
+    cudaEventRecord(e0, st);
+    res = gwc_request_step(ctx, stream);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) res = fail(ctx, GWC_ERR_CUDA, "autotune sync failed");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (res == GWC_OK && ms < best_ms) {
+      best_ms = ms;
+      best = f;
+    }
+    if (f * 2 > ctx->batch_cap && f != ctx->batch_cap) f = ctx->batch_cap / 2;  // try the capacity last
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->opt.profile = saved_profile;
+  ctx->batch = best;
+  if (res != GWC_OK) return res;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best;
+  }
+  if (chosen) *chosen = best;
+  return GWC_OK;
+}
+
+// ---- batched form: one CUDA graph over many contexts ----------------------------------------------------
+struct gwc_batch {
+  cudaStream_t cap = nullptr;  // internal capture origin (the caller's stream may be the legacy one)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  std::vector<gwc_ctx*> ctxs;
+};
+
+void gwc_batch_destroy(gwc_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto e : b->events) cudaEventDestroy(e);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* stream) {
+  // errors of this function go to gwc_last_error(NULL)
+  if (!out || !ctxs || n < 1) return fail(nullptr, GWC_ERR_INVALID_ARG, "need out, ctxs and n >= 1");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i] || ctxs[i]->req_n_omega <= 0)
+      return fail(nullptr, GWC_ERR_INVALID_ARG, "every context needs a request plan");
+  gwc_batch* b = new gwc_batch();
+  b->ctxs.assign(ctxs, ctxs + n);
+  auto bail = [&](gwc_status s, const std::string& m) {
+    gwc_batch_destroy(b);
+    return fail(nullptr, s, m);
+  };
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(GWC_ERR_CUDA, "capture stream creation failed");
+  cudaStream_t st = b->cap;
+  b->streams.resize(n);
+  b->events.resize(n + 1);
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess)
+      return bail(GWC_ERR_CUDA, "stream creation failed");
+  for (int i = 0; i <= n; ++i)
+    if (cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming) != cudaSuccess)
+      return bail(GWC_ERR_CUDA, "event creation failed");
+  // one uncaptured run per context sets function attributes and first-use state
+  std::vector<int> saved(n);
+  for (int i = 0; i < n; ++i) {
+    saved[i] = ctxs[i]->opt.profile;
+    ctxs[i]->opt.profile = 0;
+    if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK) {
+      for (int k = 0; k <= i; ++k) ctxs[k]->opt.profile = saved[k];
+      return bail(GWC_ERR_CUDA, std::string("warm-up step failed: ") + ctxs[i]->last_error);
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamSynchronize(b->streams[i]) != cudaSuccess) return bail(GWC_ERR_CUDA, "warm-up sync failed");
+  gwc_status res = GWC_OK;
+  std::string msg;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    res = GWC_ERR_CUDA;
+    msg = "cudaStreamBeginCapture failed";
+  } else {
+    cudaEventRecord(b->events[n], st);
+    for (int i = 0; i < n && res == GWC_OK; ++i) {
+      cudaStreamWaitEvent(b->streams[i], b->events[n], 0);
+      if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK) {
+        res = GWC_ERR_CUDA;
+        msg = std::string("capture of a step failed: ") + ctxs[i]->last_error;
+      }
+      cudaEventRecord(b->events[i], b->streams[i]);
+      cudaStreamWaitEvent(st, b->events[i], 0);
+    }
+    cudaError_t e = cudaStreamEndCapture(st, &b->graph);
+    if (res == GWC_OK && e != cudaSuccess) {
+      res = GWC_ERR_CUDA;
+      msg = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+    }
+  }
+  for (int i = 0; i < n; ++i) ctxs[i]->opt.profile = saved[i];
+  if (res != GWC_OK) return bail(res, msg);
+  cudaError_t e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) return bail(GWC_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  *out = b;
+  return GWC_OK;
+}
+
+gwc_status gwc_batch_launch(gwc_batch* b, void* stream) {
+  if (!b || !b->exec) return fail(nullptr, GWC_ERR_INVALID_ARG, "batch is NULL");
+  cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, GWC_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+  return GWC_OK;
 }
 
 gwc_status gwc_sync(gwc_ctx* ctx, void* stream) {

@@ -162,6 +162,13 @@ int launch_qp_assemble_update(const double* eps, int n_states, int n_occ, int n_
                               cudaStream_t s);
 int launch_qp_finish(const QpState* st, int n_core, double* eps_qp, double* dh, int* iters, unsigned* status,
                      cudaStream_t s);
+// eps_qp = eps_n + dH_n after the phase-0 round (closed form of the G_dH W0 QP equation)
+int launch_qp_finish_hedin(const QpState* st, const double* eps, const int* core_idx, int n_core, double* eps_qp,
+                           double* dh, int* iters, cudaStream_t s);
+
+// Request mode: im[c][j] = f_c(eps_c + w_j) Im W[pair_of[j]][c] (0 when pair_of[j] < 0).
+int launch_request_dec(const double* eps, const int* core_idx, int n_core, double eps_f, const double* omega_rel, int n_w,
+                       const int* pair_of, const double* wpair, double* im, cudaStream_t s);
 
 // Cumulant + FFT; see cumulant.cu
 int launch_cumulant_spectrum(const double* omega_rel, int n_w, const double* im_sigma, int n_core, int n_t,
@@ -250,6 +257,22 @@ struct gwc_ctx {
   // cumulant
   double *d_cw_a = nullptr, *d_cw_b = nullptr, *d_coef = nullptr, *d_tw = nullptr;
   size_t cw_cap = 0, coef_cap = 0;
+
+  // imaginary-axis frequencies (0, xi_k) and (0, 0), uploaded at creation
+  double* d_zim = nullptr;  // [n_im + 1][2]
+  int batch_cap = 0;        // batch the workspace was sized for (gwc_autotune may lower batch)
+
+  // request mode
+  int req_n_omega = 0, req_n_pairs = 0;
+  double* d_req_wrel = nullptr;    // [n_core][n_omega] relative grid (same row for every core)
+  double* d_req_z = nullptr;       // [n_pairs][2]
+  int* d_req_rows = nullptr;       // [n_pairs][n_core]
+  int* d_req_pair_of = nullptr;    // [n_omega] -> pair or -1
+  double* d_req_w = nullptr;       // [n_pairs][n_core][2]
+  double* d_req_im = nullptr;      // [n_core][n_omega]
+  double *d_req_a = nullptr, *d_req_nu = nullptr;
+  double *d_req_eqp = nullptr, *d_req_dh = nullptr;
+  int* d_req_it = nullptr;
 
   // host staging
   int* h_pin_i = nullptr;

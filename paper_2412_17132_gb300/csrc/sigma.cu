@@ -203,7 +203,48 @@ __global__ void qp_finish_kernel(const QpState* __restrict__ st, int n_core, dou
   if (s.done != 1) atomicOr(status, kStatNotConverged);
 }
 
+// Closed form of the G_dH W0 QP equation (eq QPGWC): eps^QP_n = eps_n + dH_n, after the phase-0
+// round computed dH_n.
+__global__ void qp_finish_hedin_kernel(const QpState* __restrict__ st, const double* __restrict__ eps,
+                                       const int* __restrict__ core_idx, int n_core, double* __restrict__ eps_qp,
+                                       double* __restrict__ dh, int* __restrict__ iters) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_core) return;
+  const QpState s = st[c];
+  eps_qp[c] = eps[core_idx[c]] + s.dh;
+  dh[c] = s.dh;
+  iters[c] = 1;
+}
+
+// Decoupled Im Sigma on a relative grid shared by all cores (eq cd_sigma_imaginary_decoupled):
+// Im Sigma_c(eps_c + w_j) = f_c(eps_c + w_j) Im W^c_cc(|w_j| + i eta).
+__global__ void request_dec_kernel(const double* __restrict__ eps, const int* __restrict__ core_idx, int n_core,
+                                   double eps_f, const double* __restrict__ omega_rel, int n_w,
+                                   const int* __restrict__ pair_of, const double* __restrict__ wpair,
+                                   double* __restrict__ im) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_core * n_w) return;
+  const int c = t / n_w, j = t % n_w;
+  const int p = pair_of[j];
+  const double ec = eps[core_idx[c]];
+  const double f = prefactor(ec, ec + omega_rel[j], eps_f);
+  im[t] = (p < 0 || f == 0.0) ? 0.0 : f * wpair[((size_t)p * n_core + c) * 2 + 1];
+}
+
 }  // namespace
+
+int launch_qp_finish_hedin(const QpState* st, const double* eps, const int* core_idx, int n_core, double* eps_qp,
+                           double* dh, int* iters, cudaStream_t s) {
+  qp_finish_hedin_kernel<<<(n_core + 63) / 64, 64, 0, s>>>(st, eps, core_idx, n_core, eps_qp, dh, iters);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_request_dec(const double* eps, const int* core_idx, int n_core, double eps_f, const double* omega_rel, int n_w,
+                       const int* pair_of, const double* wpair, double* im, cudaStream_t s) {
+  int n = n_core * n_w;
+  request_dec_kernel<<<(n + 255) / 256, 256, 0, s>>>(eps, core_idx, n_core, eps_f, omega_rel, n_w, pair_of, wpair, im);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_sigma_grid(const double* eps, int n_states, int n_core, const int* core_idx, const double* omega, int n_w,
                       double eps_f, const double* xi, const double* wxi, int n_im, const double* wim, const int* pidx,

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libgwc.so")
 
 PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "fp32": 3}
 DEC = {"none": 0, "diag": 1, "group": 2}
+QP = {"secant": 0, "hedin": 1}
 STATUS = {
     0: "ok",
     1: "invalid argument",
@@ -68,6 +69,7 @@ class Options(ctypes.Structure):
         ("qp_tol", ctypes.c_double),
         ("batch", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("qp_mode", ctypes.c_int),
     ]
 
 
@@ -106,6 +108,14 @@ _SIGS = {
     "gwc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "gwc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "gwc_destroy": (None, [ctypes.c_void_p]),
+    "gwc_request_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "gwc_request_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_request_copy_results": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_void_p]),
+    "gwc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "gwc_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                        ctypes.c_void_p]),
+    "gwc_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_batch_destroy": (None, [ctypes.c_void_p]),
     "gwc_cumulant_spectrum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                       ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                                       ctypes.c_void_p]),
@@ -166,6 +176,30 @@ def cumulant_spectrum_noalloc(omega_rel, im_sigma, n_t, t_max, eta, a_out, nu_ou
     return a_out, nu_out
 
 
+class Batch:
+    """Many contexts' request steps captured into one CUDA graph (gwc_batch_*)."""
+
+    def __init__(self, contexts, stream=None):
+        self._contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self._contexts))(*[c._ctx.value for c in self._contexts])
+        self._b = ctypes.c_void_p()
+        _check(lib().gwc_batch_create(ctypes.byref(self._b), arr, len(self._contexts), _stream(stream)), None)
+
+    def launch(self, stream=None):
+        _check(lib().gwc_batch_launch(self._b, _stream(stream)), None)
+
+    def close(self):
+        if self._b:
+            lib().gwc_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """One molecule resident on the current CUDA device (wraps ``gwc_ctx``).
 
@@ -175,7 +209,7 @@ class Context:
 
     def __init__(self, eps, n_occ, core_idx, o_ov, o_core, *, vxc=None, eps_f=math.nan, eta=1e-3, n_im=32, xi0=1.0,
                  prec="bf16x3", dec="diag", groups=None, n_t=1 << 16, t_max=2000.0, max_qp_iter=50, qp_tol=1e-7,
-                 batch=0, profile=False, stream=None):
+                 batch=0, profile=False, qp_mode="secant", stream=None):
         self._ctx = ctypes.c_void_p()
         host = isinstance(eps, np.ndarray)
         self._keep = []
@@ -196,6 +230,7 @@ class Context:
         opt.n_t, opt.t_max = int(n_t), float(t_max)
         opt.max_qp_iter, opt.qp_tol, opt.batch = int(max_qp_iter), float(qp_tol), int(batch)
         opt.profile = 1 if profile else 0
+        opt.qp_mode = QP[qp_mode]
         self.opt = opt
         self.prec = prec
         _check(lib().gwc_create(ctypes.byref(self._ctx), ctypes.byref(sysd), ctypes.byref(opt), _stream(stream)), None)
@@ -274,6 +309,32 @@ class Context:
         _check(lib().gwc_cumulant_spectrum(self._ctx, _ptr(omega_rel), n_w, _ptr(im_sigma), _ptr(a), _ptr(nu), _stream(stream)),
                self._ctx)
         return a, nu
+
+    # -- request mode (decoupled spectra + QP as one capturable step) -------------------------
+    def request_plan(self, omega_rel, stream=None):
+        om = np.ascontiguousarray(np.asarray(omega_rel, dtype=np.float64))
+        self.req_n_omega = int(om.shape[0])
+        _check(lib().gwc_request_plan(self._ctx, om.ctypes.data, self.req_n_omega, _stream(stream)), self._ctx)
+
+    def request_step(self, stream=None):
+        _check(lib().gwc_request_step(self._ctx, _stream(stream)), self._ctx)
+
+    def request_results(self, stream=None, out=None):
+        """Copies the last step's results into CUDA tensors (eps_qp, dh, iters, im_sigma, a, nu)."""
+        import torch
+
+        nc, nw, nt = self.n_core, self.req_n_omega, self.opt.n_t
+        if out is None:
+            out = (torch.empty(nc, dtype=torch.float64, device="cuda"), torch.empty(nc, dtype=torch.float64, device="cuda"),
+                   torch.empty(nc, dtype=torch.int32, device="cuda"), torch.empty((nc, nw), dtype=torch.float64, device="cuda"),
+                   torch.empty((nc, nt), dtype=torch.float64, device="cuda"), torch.empty(nt, dtype=torch.float64, device="cuda"))
+        _check(lib().gwc_request_copy_results(self._ctx, *[_ptr(t) for t in out], _stream(stream)), self._ctx)
+        return out
+
+    def autotune(self, stream=None) -> int:
+        c = ctypes.c_int()
+        _check(lib().gwc_autotune(self._ctx, _stream(stream), ctypes.byref(c)), self._ctx)
+        return c.value
 
     def sync(self, stream=None):
         _check(lib().gwc_sync(self._ctx, _stream(stream)), self._ctx)

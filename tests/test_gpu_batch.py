@@ -1,0 +1,111 @@
+"""Request mode (decoupled spectra + QP as one capturable step), the batched CUDA-graph form and
+the autotuner, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import gwc_oracle as G
+from paper_2412_17132_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+EV = synth.HARTREE_EV
+
+
+@pytest.fixture(scope="module")
+def gwc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_17132_gb300 import gwc as g
+
+    g.lib()
+    return g
+
+
+def _rel_grid(n=201, lo_ev=-25.0, hi_ev=5.0):
+    return np.linspace(lo_ev / EV, hi_ev / EV, n)
+
+
+def _request(gwc, mol, prec="bf16x3", qp_mode="hedin", n=201):
+    ctx = gwc.Context.from_molecule(mol, prec=prec, qp_mode=qp_mode)
+    ctx.request_plan(_rel_grid(n))
+    ctx.request_step()
+    res = [t.clone() for t in ctx.request_results()]
+    ctx.sync()
+    return ctx, res
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_request_step_matches_oracle(gwc, prec):
+    mol = synth.small(n_states=40, n_occ=6, n_core=2, n_aux=90, seed=41)
+    ctx, (eqp, dh, it, im, a, nu) = _request(gwc, mol, prec=prec)
+    s = G.System.from_molecule(mol)
+    w_rel = _rel_grid()
+    tol = {"fp64": (0.0, 1e-9), "bf16x3": (2e-2, 2e-3)}[prec]
+    for c in range(2):
+        ec = float(mol.eps[c])
+        ref = np.array([s.sigma_c(ec + w)[1][c] for w in w_rel])
+        got = im[c].cpu().numpy()
+        assert np.all(np.abs(got - ref) <= tol[0] * np.abs(ref) + tol[1]), np.max(np.abs(got - ref))
+        # QP in closed form (eq QPGWC): eps_n + dH_n with dH_n = Re Sigma^c_n(eps_n) (v^xc = Sigma^x)
+        dh_ref = s.sigma_c_core(c, ec).real
+        assert abs(float(dh[c]) - dh_ref) * EV < (1e-9 if prec == "fp64" else 1e-3)
+        assert abs(float(eqp[c]) - (ec + float(dh[c]))) < 1e-12
+        # spectrum of the request equals the cumulant oracle applied to the same Im Sigma
+        nu_ref, a_ref = G.gwc_spectrum(w_rel, got, mol.eta, mol.n_t, mol.t_max)
+        assert np.max(np.abs(a[c].cpu().numpy() - a_ref)) < 1e-9 * np.max(a_ref)
+
+
+def test_request_secant_agrees_with_closed_form(gwc):
+    mol = synth.small(n_states=40, n_occ=6, n_core=2, n_aux=90, seed=43)
+    _, (e_h, dh_h, _, _, _, _) = _request(gwc, mol, prec="fp64", qp_mode="hedin")
+    _, (e_s, dh_s, it_s, _, _, _) = _request(gwc, mol, prec="fp64", qp_mode="secant")
+    assert torch.allclose(dh_h, dh_s, rtol=0, atol=1e-12)
+    assert float((e_h - e_s).abs().max()) * EV < 1e-3
+    assert int(it_s.min()) >= 2
+
+
+def test_batch_graph_equals_individual_steps(gwc):
+    """Each molecule's result is the same alone and inside the batched graph (uneven sizes)."""
+    mols = [synth.small(n_states=n, n_occ=max(2, n // 8), n_core=1 + (n % 2), n_aux=int(2.5 * n), seed=100 + n)
+            for n in (24, 41, 57, 33)]
+    alone = []
+    for m in mols:
+        ctx, res = _request(gwc, m)
+        alone.append(res)
+        ctx.close()
+    ctxs = []
+    for m in mols:
+        c = gwc.Context.from_molecule(m, prec="bf16x3", qp_mode="hedin")
+        c.request_plan(_rel_grid())
+        ctxs.append(c)
+    batch = gwc.Batch(ctxs)
+    for rep in range(2):  # two launches of the same graph
+        batch.launch()
+        torch.cuda.synchronize()
+        for c, ref in zip(ctxs, alone):
+            got = c.request_results()
+            torch.cuda.synchronize()
+            for g, r in zip(got, ref):
+                if g.dtype == torch.int32:
+                    assert torch.equal(g, r)
+                else:
+                    assert float((g - r).abs().max()) <= 1e-12 * max(1.0, float(r.abs().max()))
+    batch.close()
+    for c in ctxs:
+        c.sync()
+
+
+def test_autotune_picks_a_valid_batch(gwc):
+    mol = synth.small(n_states=40, n_occ=6, n_core=2, n_aux=90, seed=47)
+    ctx = gwc.Context.from_molecule(mol, prec="bf16x3", qp_mode="hedin", batch=128)
+    ctx.request_plan(_rel_grid())
+    chosen = ctx.autotune()
+    assert chosen in (16, 32, 64, 128)
+    ctx.request_step()
+    ctx.sync()
+    # the second context of the same shape bucket reuses the cached choice
+    ctx2 = gwc.Context.from_molecule(mol, prec="bf16x3", qp_mode="hedin", batch=128)
+    ctx2.request_plan(_rel_grid())
+    assert ctx2.autotune() == chosen
