@@ -243,3 +243,120 @@ def serving_request(request_id: int) -> Molecule:
 def small(n_states=24, n_occ=4, n_core=1, n_aux=20, seed=3, n_omega=40, n_high=None) -> Molecule:
     """Arbitrary small system for ragged-shape and brute-force tests."""
     return molecule("small", n_states, n_occ, n_core, n_aux, seed=seed, n_omega=n_omega, n_high=n_high)
+
+
+# ----------------------------------------------------------------------------------------
+# Device-side generation (batched and serving workloads)
+# ----------------------------------------------------------------------------------------
+def _i64(c: int) -> int:
+    """Two's-complement int64 value of a uint64 constant."""
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def _srl(x, k: int):
+    """Logical right shift of int64 torch values (bit pattern of the uint64 shift)."""
+    return (x >> k) & ((1 << (64 - k)) - 1)
+
+
+def _splitmix64_t(x):
+    z = x + _i64(0x9E3779B97F4A7C15)
+    z = (z ^ _srl(z, 30)) * _i64(0xBF58476D1CE4E5B9)
+    z = (z ^ _srl(z, 27)) * _i64(0x94D049BB133111EB)
+    return z ^ _srl(z, 31)
+
+
+def _counter_normal_t(seed, p, lo, hi):
+    """Torch (int64 bit patterns) version of _counter_normal: same draws, torch transcendental functions."""
+    import torch
+
+    key = _splitmix64_t(torch.tensor(_i64((seed * 0xD1B54A32D192ED03 + 0x632BE59BD9B4E019) % (1 << 64)), dtype=torch.int64,
+                                     device=p.device))
+    c = (p << 42) ^ (lo << 21) ^ hi
+    c = c * 2
+    u1 = _splitmix64_t(key ^ c)
+    u2 = _splitmix64_t(key ^ (c + 1))
+    f1 = (_srl(u1, 11).to(torch.float64) + 1.0) * (1.0 / 9007199254740992.0)
+    f2 = _srl(u2, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+    return torch.sqrt(-2.0 * torch.log(f1)) * torch.cos(2.0 * math.pi * f2)
+
+
+def molecule_device(name, n_states, n_occ, n_core, n_aux, *, seed=0, core_lo=-10.41, core_hi=-10.39, n_high=None,
+                    n_omega=800, n_im=32, xi0=1.0, eta=1e-3, n_t=1 << 16, t_max=2000.0, power_steps=20,
+                    device="cuda", sigma=0.02, amp=5.0, frac=0.1):
+    """The recipe of `molecule` with O generated on the GPU (torch), for workloads too large to
+    generate on the host per request. Energies and amplified subsets are the host generator's; the
+    O^P_mn draws are the same counter-based values up to the last bits of log/cos; the global scale
+    comes from `power_steps` steps of power iteration on the device (no host synchronisation), so
+    ||Pi(i0)||_2 = 2 holds to the accuracy of that iteration rather than to 1e-12.
+    Returns a Molecule whose eps/core_idx/omega are numpy and whose o_ov/o_core are CUDA tensors."""
+    import torch
+
+    n_virt = n_states - n_occ
+    if n_high is None:
+        n_high = int(round(n_virt * 5 / 52))
+    rng = np.random.default_rng(seed)
+    eps = _energies(rng, n_core, core_lo, core_hi, n_occ - n_core, n_virt, n_high)
+    amp_p = np.ones((n_core, n_aux))
+    for c in range(n_core):
+        sub = np.random.default_rng([seed, 7, c]).choice(n_aux, size=int(round(frac * n_aux)), replace=False)
+        amp_p[c, sub] = amp
+    dev = torch.device(device)
+    amp_t = torch.as_tensor(amp_p, device=dev)
+    ii = torch.arange(n_occ, device=dev, dtype=torch.int64).repeat_interleave(n_virt)
+    aa = torch.arange(n_occ, n_states, device=dev, dtype=torch.int64).repeat(n_occ)
+    o_ov = torch.empty((n_aux, ii.numel()), dtype=torch.float64, device=dev)
+    chunk = max(1, (1 << 24) // max(1, ii.numel()))
+    for p0 in range(0, n_aux, chunk):
+        p1 = min(n_aux, p0 + chunk)
+        p = torch.arange(p0, p1, device=dev, dtype=torch.int64)[:, None]
+        g = _counter_normal_t(seed, p.expand(-1, ii.numel()), ii[None, :].expand(p1 - p0, -1),
+                              aa[None, :].expand(p1 - p0, -1))
+        f = torch.ones_like(g)
+        for c in range(n_core):
+            f = torch.where(ii[None, :] == c, f * amp_t[c, p0:p1][:, None], f)
+        o_ov[p0:p1] = sigma * g * f
+    m_idx = torch.arange(n_states, device=dev, dtype=torch.int64)
+    o_core = torch.empty((n_states, n_core, n_aux), dtype=torch.float64, device=dev)
+    pp = torch.arange(n_aux, device=dev, dtype=torch.int64)
+    for c in range(n_core):
+        lo = torch.minimum(m_idx, torch.tensor(c, device=dev))
+        hi = torch.maximum(m_idx, torch.tensor(c, device=dev))
+        g = _counter_normal_t(seed, pp[None, :].expand(n_states, -1), lo[:, None].expand(-1, n_aux),
+                              hi[:, None].expand(-1, n_aux))
+        f = amp_t[c][None, :].expand(n_states, -1).clone()
+        if n_core > 0:
+            core_rows = m_idx < n_core
+            f[core_rows] = f[core_rows] * amp_t[m_idx[core_rows]]
+        o_core[:, c, :] = sigma * g * f
+    # global scale: largest eigenvalue of sum_ia (4/Delta_ia) O_ia O_ia^T by power iteration
+    eps_t = torch.as_tensor(eps, device=dev)
+    w = 4.0 / (eps_t[n_occ:][None, :] - eps_t[:n_occ][:, None]).reshape(-1)
+    v = torch.ones(n_aux, dtype=torch.float64, device=dev)
+    lam = torch.tensor(1.0, dtype=torch.float64, device=dev)
+    for _ in range(power_steps):
+        u = o_ov @ (w * (o_ov.t() @ v))
+        lam = torch.linalg.vector_norm(u) / torch.linalg.vector_norm(v)
+        v = u / torch.linalg.vector_norm(u)
+    s = torch.sqrt(2.0 / lam)
+    o_ov.mul_(s)
+    o_core.mul_(s)
+    return Molecule(name=name, eps=eps, n_occ=n_occ, core_idx=np.arange(n_core, dtype=np.int32), o_ov=o_ov, o_core=o_core,
+                    eta=eta, n_im=n_im, xi0=xi0, omega=omega_window(eps[:n_core], n_omega), n_t=n_t, t_max=t_max)
+
+
+def batch_member_device(j: int, **kw) -> Molecule:
+    """Molecule j of the uneven batch (seed 1000 + j) generated on the GPU."""
+    rng = np.random.default_rng(1000 + j)
+    n = int(rng.integers(100, 1301))
+    n_occ = max(2, int(round(n / 18)))
+    n_core = max(1, int(round(0.3 * n_occ)))
+    return molecule_device(f"batch{j}", n, n_occ, n_core, int(round(3.5 * n)), seed=1000 + j, **kw)
+
+
+def serving_request_device(request_id: int, **kw) -> Molecule:
+    """Request of the serving stream (seed = request id) generated on the GPU."""
+    rng = np.random.default_rng(request_id)
+    n = int(round(math.exp(rng.uniform(math.log(100), math.log(1500)))))
+    n_occ = max(2, int(round(n / 18)))
+    n_core = max(1, int(round(0.3 * n_occ)))
+    return molecule_device(f"req{request_id}", n, n_occ, n_core, int(round(3.5 * n)), seed=request_id, **kw)
