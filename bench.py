@@ -40,7 +40,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gwc", choices=["gwc", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp32", "fp64"])
-    ap.add_argument("--workload", default="benzene", choices=["benzene", "tiny"])
+    ap.add_argument("--workload", default="benzene", choices=["benzene", "tiny", "pentacene", "batch", "serve"])
+    ap.add_argument("--molecules", type=int, default=48, help="batched form: molecules in the graph")
+    ap.add_argument("--omega-points", type=int, default=800, help="batched/serving/pentacene: grid points")
+    ap.add_argument("--requests", type=int, default=2000, help="serving form: requests in the stream")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving form: mean arrival rate (1/s)")
+    ap.add_argument("--slots", type=int, default=8, help="serving form: requests in flight at most")
+    ap.add_argument("--time-limit", type=float, default=900.0, help="serving form: stop after this many seconds")
+    ap.add_argument("--fp64-points", type=int, default=1, help="pentacene form: grid points for the FP64 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -418,10 +425,167 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# Precision form at the pentacene size, batched form, serving form
+# ------------------------------------------------------------------------------------------
+def _events():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_pentacene(args):
+    """Pentacene-sized molecule (1300 states, 73 occupied, 22 cores, 4500 aux): Hedin shifts of all
+    cores and Sigma^c of all cores at a subset of grid points, mixed path vs the plain FP64 GPU path,
+    errors per core against the FP64 oracle values of tests/golden/pentacene_oracle.json."""
+    import numpy as np
+    import torch
+
+    from paper_2412_17132_gb300 import gwc, synth
+
+    mol = synth.pentacene_device()
+    pts_idx = [100, 700][: max(1, min(2, args.omega_points))]
+    out = {"metric": "pentacene-sized: Sigma_c points/s, mixed vs FP64 GPU path", "unit": UNIT, "n_gpus": 1,
+           "data": "synthetic", "config": {"workload": describe(mol), "grid_points": pts_idx}}
+    res = {}
+    for prec in (args.prec, "fp64"):
+        ctx = gwc.Context(torch.as_tensor(mol.eps, device="cuda"), mol.n_occ, mol.core_idx, mol.o_ov, mol.o_core,
+                          prec=prec, qp_mode="hedin", batch=args.batch or 64, eta=mol.eta, n_im=mol.n_im, profile=True)
+        torch.cuda.synchronize()
+        t_qp, dh = None, None
+        if prec != "fp64":  # FP64 Hedin shifts of all 22 cores would take ~1.5 h at 1.2 TFLOP/s FP64
+            e0, e1 = _events()
+            e0.record()
+            e, dh, it = ctx.qp_solve()
+            e1.record()
+            e1.synchronize()
+            t_qp = e0.elapsed_time(e1) / 1e3
+            dh = dh.cpu().numpy()
+        pts = mol.omega[pts_idx[: (args.fp64_points if prec == "fp64" else len(pts_idx))]]
+        e0, e1 = _events()
+        e0.record()
+        sig, dec, sx = ctx.sigma_core(pts)
+        e1.record()
+        e1.synchronize()
+        t_sig = e0.elapsed_time(e1) / 1e3
+        ctx.sync()
+        res[prec] = {"dh": dh, "sig": sig.cpu().numpy(), "t_qp": t_qp, "t_sig": t_sig,
+                     "points": mol.n_core * len(pts), "stats": ctx.stats()}
+        ctx.close()
+    m, f = res[args.prec], res["fp64"]
+    out["value"] = m["points"] / m["t_sig"]
+    out["fp64_path"] = {"value": f["points"] / f["t_sig"], "points": f["points"], "seconds": f["t_sig"]}
+    out["mixed_over_fp64"] = out["value"] / out["fp64_path"]["value"]
+    out["hedin_shift_seconds_all_cores"] = m["t_qp"]
+    out["sigma_mixed_minus_fp64_Ha_max"] = float(np.max(np.abs(m["sig"][:, : f["sig"].shape[1]] - f["sig"])))
+    gold_p = os.path.join(ROOT, "tests", "golden", "pentacene_oracle.json")
+    if os.path.exists(gold_p):
+        with open(gold_p) as fh:
+            gold = json.load(fh)
+        out["vs_oracle"] = {
+            "cores": gold["cores"],
+            "dH_err_eV": {p: [float((res[p]["dh"][c] - gold["dH"][k]) * HARTREE_EV) for k, c in enumerate(gold["cores"])]
+                          for p in res if res[p]["dh"] is not None},
+            "sigma_err_Ha_max": {p: float(max(np.max(np.abs(res[p]["sig"][:, j, 0] + 1j * res[p]["sig"][:, j, 1]
+                                                         - np.array([complex(*v) for v in gold["points"][j]["sigma_c"]])))
+                                             for j in range(res[p]["sig"].shape[1]))) for p in res},
+        }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_batch(args):
+    """Batched form: molecules j = 0..M-1 (N_states ~ U{100..1300}, seed 1000 + j) generated on the GPU,
+    each a request (decoupled spectra of all cores on the relative grid + Hedin QP), all captured into
+    one CUDA graph after autotuning the frequency batch per shape bucket."""
+    import numpy as np
+    import torch
+
+    from paper_2412_17132_gb300 import gwc, synth
+
+    grid = np.linspace(-25.0 / HARTREE_EV, 5.0 / HARTREE_EV, args.omega_points)
+    ctxs, sizes, tuned = [], [], []
+    t_setup = time.perf_counter()
+    for j in range(args.molecules):
+        mol = synth.batch_member_device(j)
+        c = gwc.Context(torch.as_tensor(mol.eps, device="cuda"), mol.n_occ, mol.core_idx, mol.o_ov, mol.o_core,
+                        prec=args.prec, qp_mode="hedin", batch=args.batch or 64, eta=mol.eta, n_im=mol.n_im)
+        del mol
+        c.request_plan(grid)
+        tuned.append(c.autotune())
+        ctxs.append(c)
+        sizes.append((c.n_states, c.n_aux, c.n_core))
+        torch.cuda.empty_cache()
+    t_setup = time.perf_counter() - t_setup
+    t_cap = time.perf_counter()
+    batch = gwc.Batch(ctxs)
+    t_cap = time.perf_counter() - t_cap
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = _events()
+        e0.record()
+        batch.launch()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    points = sum(nc for _, _, nc in sizes) * args.omega_points
+    out = {"metric": "batched form: decoupled Sigma points/s (+ Hedin QP + spectra) in one graph launch", "unit": UNIT,
+           "value": points / statistics.mean(times), "n_gpus": 1, "steps": args.steps, "data": "synthetic",
+           "ms_per_step": 1e3 * statistics.mean(times), "dtype": args.prec,
+           "config": {"workload": f"{args.molecules} molecules, N_states ~ U{{100..1300}} (seed 1000+j), N_aux = 3.5 N, "
+                                  f"{args.omega_points}-point relative grid, cores = round(0.3 N_occ), QP = eps_n + dH_n",
+                      "sizes_states_aux_cores": sizes, "autotuned_batch": tuned},
+           "spectra_per_s": sum(nc for _, _, nc in sizes) / statistics.mean(times),
+           "setup_s": t_setup, "capture_s": t_cap}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Serving form: Poisson arrivals of spectrum requests (N_states log-uniform on [100, 1500], inputs
+    generated on the GPU from seed = request id), admitted by HBM footprint, continuous batching."""
+    import numpy as np
+    import torch
+
+    from paper_2412_17132_gb300 import serve, synth
+
+    grid = np.linspace(-25.0 / HARTREE_EV, 5.0 / HARTREE_EV, args.omega_points)
+    arr = serve.poisson_arrivals(args.requests, args.rate, seed=0)
+    reqs = [serve.Request(rid=i, arrival=float(arr[i]), make=(lambda i=i: synth.serving_request_device(i)),
+                          n_states=serve.serving_size(i)) for i in range(args.requests)]
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.SpectrumServer(grid, budget_bytes=int(0.5 * free), slots=args.slots, prec=args.prec, qp_mode="hedin",
+                               batch=args.batch or 64)
+    t0 = time.perf_counter()
+    done = srv.run(reqs, time_limit=args.time_limit)
+    makespan = time.perf_counter() - t0
+    summ = serve.summarize(done, makespan)
+    out = {"metric": "serving form: spectra/s and p50/p99 latency (arrival to results in host memory)", "unit": "requests/s",
+           "value": summ["requests_per_s"], "n_gpus": 1, "data": "synthetic", "dtype": args.prec,
+           "config": {"workload": f"{args.requests} requests offered at {args.rate}/s (Poisson, seed 0), N_states log-uniform "
+                                  f"[100, 1500] from seed = request id, {args.omega_points}-point grid, QP = eps_n + dH_n",
+                      "slots": args.slots, "budget_GB": 0.5 * free / 1e9, "time_limit_s": args.time_limit},
+           "serving": summ, "makespan_s": makespan,
+           "offered_requests": args.requests, "arrived_by_end": int(sum(1 for a in arr if a <= makespan)),
+           "max_sustainable_requests_per_s": summ["requests_per_s"],
+           "note": "completed/makespan under saturation is the sustainable rate; p50/p99 include queueing"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "pentacene":
+        return run_pentacene(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

@@ -247,9 +247,10 @@ gwc_status gwc_request_results_get(const gwc_ctx* ctx, gwc_request_results* out)
 gwc_status gwc_request_copy_results(const gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, double* im_sigma,
                                     double* a, double* nu, void* stream);
 
-/* Frequencies per internal batch chosen by timing the request step for 16, 32, ..., up to the
- * capacity the context was created with (cached per shape bucket and precision for the process).
- * Needs a request plan; synchronises `stream`; *chosen receives the batch used from now on. */
+/* Frequencies per internal batch chosen by timing one residue batch (chi0 build, factorisation and
+ * contraction of that many frequencies) for 16, 32, ... and the capacity the context was created
+ * with, keeping the lowest time per frequency (cached per shape bucket and precision for the
+ * process). Needs a request plan; synchronises `stream`; *chosen receives the batch now used. */
 gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen);
 
 /* ---- Batched form: many molecules of uneven size in one CUDA-graph launch ----------------------

@@ -946,26 +946,35 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
   const int saved_profile = ctx->opt.profile;
   ctx->opt.profile = 0;
   int best = ctx->batch_cap;
-  float best_ms = 1e30f;
+  double best_per = 1e300;
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   gwc_status res = GWC_OK;
-  for (int f = 16; f <= ctx->batch_cap && res == GWC_OK; f *= 2) {
-    ctx->batch = f;
-    res = gwc_request_step(ctx, stream);  // warm-up for this shape
+  // candidates 16, 32, ... and the capacity; each timed on ONE residue batch of that size (its
+  // per-build time), after one warm-up launch, so tuning costs a few batches, not whole steps
+  std::vector<int> cands;
+  for (int f = 16; f < ctx->batch_cap; f *= 2) cands.push_back(f);
+  cands.push_back(ctx->batch_cap);
+  const int np = ctx->req_n_pairs;
+  for (int f : cands) {
+    if (res != GWC_OK || np <= 0) break;
+    const int nb = std::min(f, np);
+    ctx->batch = nb;
+    res = residue_batches(ctx, nb, ctx->d_req_z, ctx->d_req_rows, ctx->n_core, ctx->d_req_w, nullptr, st);
     if (res != GWC_OK) break;
     cudaEventRecord(e0, st);
-    res = gwc_request_step(ctx, stream);
+    res = residue_batches(ctx, nb, ctx->d_req_z, ctx->d_req_rows, ctx->n_core, ctx->d_req_w, nullptr, st);
     cudaEventRecord(e1, st);
     if (cudaEventSynchronize(e1) != cudaSuccess) res = fail(ctx, GWC_ERR_CUDA, "autotune sync failed");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (res == GWC_OK && ms < best_ms) {
-      best_ms = ms;
+    const double per = ms / nb;
+    if (res == GWC_OK && per < best_per) {
+      best_per = per;
       best = f;
     }
-    if (f * 2 > ctx->batch_cap && f != ctx->batch_cap) f = ctx->batch_cap / 2;  // try the capacity last
+    if (nb < f) break;  // fewer pairs than the candidate: larger batches change nothing
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -282,12 +282,14 @@ def _counter_normal_t(seed, p, lo, hi):
 
 def molecule_device(name, n_states, n_occ, n_core, n_aux, *, seed=0, core_lo=-10.41, core_hi=-10.39, n_high=None,
                     n_omega=800, n_im=32, xi0=1.0, eta=1e-3, n_t=1 << 16, t_max=2000.0, power_steps=20,
-                    device="cuda", sigma=0.02, amp=5.0, frac=0.1):
+                    device="cuda", sigma=0.02, amp=5.0, frac=0.1, exact_scale=False):
     """The recipe of `molecule` with O generated on the GPU (torch), for workloads too large to
     generate on the host per request. Energies and amplified subsets are the host generator's; the
     O^P_mn draws are the same counter-based values up to the last bits of log/cos; the global scale
     comes from `power_steps` steps of power iteration on the device (no host synchronisation), so
-    ||Pi(i0)||_2 = 2 holds to the accuracy of that iteration rather than to 1e-12.
+    ||Pi(i0)||_2 = 2 holds to the accuracy of that iteration rather than to 1e-12; with
+    exact_scale=True it is the Lanczos value of the host generator (matrix-vector products on the
+    device), and the molecule equals `molecule(...)` to rounding.
     Returns a Molecule whose eps/core_idx/omega are numpy and whose o_ov/o_core are CUDA tensors."""
     import torch
 
@@ -331,17 +333,36 @@ def molecule_device(name, n_states, n_occ, n_core, n_aux, *, seed=0, core_lo=-10
     # global scale: largest eigenvalue of sum_ia (4/Delta_ia) O_ia O_ia^T by power iteration
     eps_t = torch.as_tensor(eps, device=dev)
     w = 4.0 / (eps_t[n_occ:][None, :] - eps_t[:n_occ][:, None]).reshape(-1)
-    v = torch.ones(n_aux, dtype=torch.float64, device=dev)
-    lam = torch.tensor(1.0, dtype=torch.float64, device=dev)
-    for _ in range(power_steps):
-        u = o_ov @ (w * (o_ov.t() @ v))
-        lam = torch.linalg.vector_norm(u) / torch.linalg.vector_norm(v)
-        v = u / torch.linalg.vector_norm(u)
-    s = torch.sqrt(2.0 / lam)
+    if exact_scale:
+        if n_aux <= 2048:
+            lam = float(torch.linalg.eigvalsh((o_ov * w[None, :]) @ o_ov.t())[-1])
+        else:
+            from scipy.sparse.linalg import LinearOperator, eigsh
+
+            def mv(v):
+                vt = torch.as_tensor(np.asarray(v).reshape(-1), device=dev)
+                return (o_ov @ (w * (o_ov.t() @ vt))).cpu().numpy()
+
+            op = LinearOperator((n_aux, n_aux), matvec=mv, dtype=np.float64)
+            lam = float(eigsh(op, k=1, which="LA", tol=1e-13, v0=np.ones(n_aux))[0][0])
+        s = math.sqrt(2.0 / lam)
+    else:
+        v = torch.ones(n_aux, dtype=torch.float64, device=dev)
+        lam = torch.tensor(1.0, dtype=torch.float64, device=dev)
+        for _ in range(power_steps):
+            u = o_ov @ (w * (o_ov.t() @ v))
+            lam = torch.linalg.vector_norm(u) / torch.linalg.vector_norm(v)
+            v = u / torch.linalg.vector_norm(u)
+        s = torch.sqrt(2.0 / lam)
     o_ov.mul_(s)
     o_core.mul_(s)
     return Molecule(name=name, eps=eps, n_occ=n_occ, core_idx=np.arange(n_core, dtype=np.int32), o_ov=o_ov, o_core=o_core,
                     eta=eta, n_im=n_im, xi0=xi0, omega=omega_window(eps[:n_core], n_omega), n_t=n_t, t_max=t_max)
+
+
+def pentacene_device(seed=0, **kw) -> Molecule:
+    """The pentacene-sized molecule with O generated on the GPU and the exact normalisation."""
+    return molecule_device("pentacene", 1300, 73, 22, 4500, seed=seed, n_omega=800, exact_scale=True, **kw)
 
 
 def batch_member_device(j: int, **kw) -> Molecule:
