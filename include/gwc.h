@@ -177,6 +177,17 @@ gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double
  * GWC_ERR_NOT_CONVERGED (reported by gwc_sync). */
 gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, void* stream);
 
+/* G_dH W0 spectral function beside GW+C (Sec. "G0W0 approximation": eqs gw_full_propagator,
+ * A_definition, A_explicit_real_imaginary, with the shifted self-energy of eq hedin_sigma_spectral):
+ * from Sigma^c_n(w') on a common grid w' (as gwc_sigma_core returns it) and the Hedin shifts,
+ *   A_n(w) = (1/pi) |Im S| / ([w - eps_n + v^xc_n - Sigma^x_n - Re S]^2 + [Im S]^2),
+ *   S = Sigma^c_n(w'), on the shifted grid w = w' + dH_n.
+ *   omega  : DEVICE [n_omega] the common grid w'
+ *   sigma_c: DEVICE [n_core][n_omega][2]; dh: DEVICE [n_core] (from gwc_qp_solve)
+ *   a_out  : DEVICE [n_core][n_omega]; omega_out: DEVICE [n_core][n_omega] (w' + dH_n) or NULL */
+gwc_status gwc_gdh_spectrum(gwc_ctx* ctx, const double* omega, int n_omega, const double* sigma_c, const double* dh,
+                            double* a_out, double* omega_out, void* stream);
+
 /* Retarded-cumulant spectral function (Sec. "Numerical GW+C scheme": Eqs.
  * landau_cumulant_truncated, cumulant_propagator_numerical_time,
  * cumulant_propagator_fourier, cumulant_propagator_convolution, eq:AGWC):

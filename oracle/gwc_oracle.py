@@ -283,6 +283,25 @@ class System:
 
 
 # ----------------------------------------------------------------------------------------
+# G_dH W0 spectral function (Sec. "G0W0 approximation": Eqs. g_dyson, gw_full_propagator,
+# A_definition, A_explicit_real_imaginary, with the shifted self-energy of Eq. hedin_sigma_spectral)
+# ----------------------------------------------------------------------------------------
+
+
+def gdh_spectrum(omega_common, sigma_c, eps_n, dh, sigma_x, vxc):
+    """A^{G_dH W0}_n on the shifted grid w = w' + dH_n, from Sigma^c_n(w') on a common grid w'.
+
+    G_n(w) = [w - eps_n + v^xc_n - Sigma^x_n - Sigma^c_n(w - dH_n)]^-1 and
+    A_n(w) = (1/pi) |Im Sigma| / ([w - eps_n + v^xc_n - Re Sigma]^2 + [Im Sigma]^2).
+    Returns (w [n_w], A [n_w]).
+    """
+    w = omega_common + dh
+    re = w - eps_n + vxc - sigma_x - sigma_c.real
+    im = sigma_c.imag
+    return w, np.abs(im) / (re * re + im * im) / math.pi
+
+
+# ----------------------------------------------------------------------------------------
 # Cumulant and spectral function (Sec. "Numerical GW+C scheme": Eqs. landau_cumulant_truncated,
 # cumulant_propagator_numerical_time, cumulant_propagator_convolution,
 # cumulant_propagator_fourier, eq:AGWC)

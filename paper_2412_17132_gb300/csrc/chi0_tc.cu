@@ -9,9 +9,9 @@
 //   * TMA brings, per chunk, the B operand O[Q-tile][chunk] (BF16 hi, and lo in split mode,
 //     SWIZZLE_128B, K-major), the FP32 rows O[P-tile][chunk] and the two 64-value slices of
 //     the D(z) table into two-stage rings.
-//   * 4 transform warps form the A operand O[P][k] D_p(k) (the D scaling is fused into the
-//     operand load): each thread owns one row, scales its 64 values, splits them into BF16 hi
-//     and lo = bf16(v - hi), and writes them in the swizzled K-major layout the MMA reads.
+//   * 8 transform warps form the A operand O[P][k] D_p(k) (the D scaling is fused into the
+//     operand load): two threads per row, each scaling 32 of its 64 values, split them into
+//     BF16 hi and lo = bf16(v - hi) and write them in the swizzled K-major layout the MMA reads.
 //   * One thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM): per part and
 //     16-wide k step hi*hi (+ hi*lo + lo*hi in split mode; Henry, Tang & Heinecke 2019).
 //   * Segmented accumulation: the FP32 accumulator of the tensor core rounds toward zero, a
@@ -36,14 +36,14 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int kParts = 2;                  // frequency parts per CTA
-constexpr int kSeg = 4;                    // chunks accumulated per fresh accumulator
+constexpr int kSeg = 8;                    // chunks accumulated per fresh accumulator
 constexpr int NB_ST = 2;                   // B ring / raw-A ring stages
 constexpr int NA_ST = 3;                   // scaled-A slots (one part each)
 constexpr int TILE = BM * BK * 2;          // 16 KB: one BF16 128 x 64 operand tile
 constexpr int RAW = BM * BK * 4;           // 32 KB: FP32 128 x 64 rows (two 128-B swizzled halves)
 constexpr int DSL = kParts * BK * 4;       // 512 B: D slices of one chunk
-constexpr int NTHREADS = 384;              // warp 0 TMA, 1 MMA, 2 TMEM, 4-7 transform, 8-11 fold
-constexpr int NXF = 128;                   // transform threads
+constexpr int NTHREADS = 512;              // warp 0 TMA, 1 MMA, 2 TMEM, 4-11 transform, 12-15 fold
+constexpr int NXF = 256;                   // transform threads (two per row of the P tile)
 constexpr int NFOLD = 128;                 // fold threads
 constexpr int SMEM_BYTES = 1024 + NB_ST * 2 * TILE + NB_ST * RAW + NA_ST * 2 * TILE + NB_ST * DSL + 256;
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s bound per wait
@@ -350,25 +350,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       mma_commit(smem_u32(mma_done));  // fires when every MMA issued above has completed
     }
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= 4 && warp < 12) {
     // ---------------- transform: A = O[P][k] D_p(k), split into BF16 hi / lo -------------------
-    const int r = threadIdx.x - 128;  // row of the P tile
+    const int tt = threadIdx.x - 128;
+    const int r = tt & 127, h = tt >> 7;  // row of the P tile, half of the 64-wide chunk
     int a = 0;
     for (int kc = 0; kc < p.n_kc; ++kc) {
       const int s = kc % NB_ST, u = kc / NB_ST;
       if (!mbar_wait(smem_u32(&r_full[s]), u & 1, abort_flag)) break;
-      float raw[64];
-      const uint8_t* rrow = r_ring + s * RAW + r * 128;
+      float raw[32];
+      const uint8_t* rrow = r_ring + s * RAW + h * (RAW / 2) + r * 128;
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {  // 16-byte chunk c (4 floats) of half h, swizzled by row%8
-          float4 v = *reinterpret_cast<const float4*>(rrow + h * (RAW / 2) + ((c ^ (r & 7)) << 4));
-          raw[32 * h + 4 * c] = v.x;
-          raw[32 * h + 4 * c + 1] = v.y;
-          raw[32 * h + 4 * c + 2] = v.z;
-          raw[32 * h + 4 * c + 3] = v.w;
-        }
+      for (int c = 0; c < 8; ++c) {  // 16-byte chunk c (4 floats) of this half, swizzled by row%8
+        float4 v = *reinterpret_cast<const float4*>(rrow + ((c ^ (r & 7)) << 4));
+        raw[4 * c] = v.x;
+        raw[4 * c + 1] = v.y;
+        raw[4 * c + 2] = v.z;
+        raw[4 * c + 3] = v.w;
+      }
       bool ok = true;
       for (int part = 0; part < n_parts; ++part, ++a) {
         const int t = a % NA_ST, ua = a / NA_ST;
@@ -376,11 +375,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ok = false;
           break;
         }
-        const float4* ds = reinterpret_cast<const float4*>(d_ring + (s * kParts + part) * BK);  // broadcast reads
+        const float4* ds = reinterpret_cast<const float4*>(d_ring + (s * kParts + part) * BK + 32 * h);  // broadcast
         uint8_t* ah = a_ring + t * 2 * TILE + r * 128;
         uint8_t* al = ah + TILE;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {  // 16-byte chunk c = 8 BF16 values k = 8c .. 8c+7
+        for (int c = 0; c < 4; ++c) {  // 16-byte chunk 4h + c = 8 BF16 values k = 32h + 8c .. +7
           const float4 d0 = ds[2 * c], d1 = ds[2 * c + 1];
           const float v[8] = {raw[8 * c] * d0.x,     raw[8 * c + 1] * d0.y, raw[8 * c + 2] * d0.z, raw[8 * c + 3] * d0.w,
                               raw[8 * c + 4] * d1.x, raw[8 * c + 5] * d1.y, raw[8 * c + 6] * d1.z, raw[8 * c + 7] * d1.w};
@@ -392,7 +391,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             float2 hf = __bfloat1622float2(hb);
             lw[e] = pack_bf16x2(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
           }
-          const int chunk = c ^ (r & 7);  // SWIZZLE_128B: 16-B chunk index XOR row%8
+          const int chunk = (4 * h + c) ^ (r & 7);  // SWIZZLE_128B: 16-B chunk index XOR row%8
           *reinterpret_cast<uint4*>(ah + chunk * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           if (p.split3) *reinterpret_cast<uint4*>(al + chunk * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
@@ -402,7 +401,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (ok) mbar_arrive(smem_u32(&r_empty[s]));  // raw rows and D slices of this stage are consumed
       if (!ok) break;
     }
-  } else if (warp >= 8) {
+  } else if (warp >= 12) {
     // ---------------- fold + epilogue: running += fresh (FP32, round to nearest) -------------
     const int q = warp & 3;
     const int row = 32 * q + lane;

@@ -806,6 +806,16 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
   return check_stream_error(ctx);
 }
 
+gwc_status gwc_gdh_spectrum(gwc_ctx* ctx, const double* omega, int n_omega, const double* sigma_c, const double* dh,
+                            double* a_out, double* omega_out, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!omega || !sigma_c || !dh || !a_out || n_omega < 1)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "need omega, sigma_c, dh, a_out and n_omega >= 1");
+  LAUNCH(launch_gdh_spectrum(ctx->d_eps, ctx->d_core_idx, ctx->n_core, omega, n_omega, sigma_c, dh, ctx->d_sx,
+                             ctx->d_vxc_eff, a_out, omega_out, (cudaStream_t)stream));
+  return check_stream_error(ctx);
+}
+
 // ---- request mode ----------------------------------------------------------------------------------
 gwc_status gwc_request_plan(gwc_ctx* ctx, const double* omega_rel, int n_omega, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");

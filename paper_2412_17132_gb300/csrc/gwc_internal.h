@@ -166,6 +166,10 @@ int launch_qp_finish(const QpState* st, int n_core, double* eps_qp, double* dh, 
 int launch_qp_finish_hedin(const QpState* st, const double* eps, const int* core_idx, int n_core, double* eps_qp,
                            double* dh, int* iters, cudaStream_t s);
 
+int launch_gdh_spectrum(const double* eps, const int* core_idx, int n_core, const double* omega, int n_w,
+                        const double* sigma, const double* dh, const double* sx, const double* vxc, double* a,
+                        double* w_out, cudaStream_t s);
+
 // Request mode: im[c][j] = f_c(eps_c + w_j) Im W[pair_of[j]][c] (0 when pair_of[j] < 0).
 int launch_request_dec(const double* eps, const int* core_idx, int n_core, double eps_f, const double* omega_rel, int n_w,
                        const int* pair_of, const double* wpair, double* im, cudaStream_t s);

@@ -231,7 +231,32 @@ __global__ void request_dec_kernel(const double* __restrict__ eps, const int* __
   im[t] = (p < 0 || f == 0.0) ? 0.0 : f * wpair[((size_t)p * n_core + c) * 2 + 1];
 }
 
+// G_dH W0 spectral function (eqs gw_full_propagator, A_explicit_real_imaginary with the shifted
+// self-energy of eq hedin_sigma_spectral): on w = w' + dH_n,
+//   A_n(w) = (1/pi) |Im S| / ([w - eps_n + v^xc_n - Sigma^x_n - Re S]^2 + [Im S]^2),  S = Sigma^c_n(w').
+__global__ void gdh_spectrum_kernel(const double* __restrict__ eps, const int* __restrict__ core_idx, int n_core,
+                                    const double* __restrict__ omega, int n_w, const double* __restrict__ sigma,
+                                    const double* __restrict__ dh, const double* __restrict__ sx,
+                                    const double* __restrict__ vxc, double* __restrict__ a, double* __restrict__ w_out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_core * n_w) return;
+  const int c = t / n_w, j = t % n_w;
+  const double w = omega[j] + dh[c];
+  const double re = w - eps[core_idx[c]] + vxc[c] - sx[c] - sigma[2 * (size_t)t];
+  const double im = sigma[2 * (size_t)t + 1];
+  a[t] = fabs(im) / (re * re + im * im) * (1.0 / 3.14159265358979323846);
+  if (w_out) w_out[t] = w;
+}
+
 }  // namespace
+
+int launch_gdh_spectrum(const double* eps, const int* core_idx, int n_core, const double* omega, int n_w,
+                        const double* sigma, const double* dh, const double* sx, const double* vxc, double* a,
+                        double* w_out, cudaStream_t s) {
+  int n = n_core * n_w;
+  gdh_spectrum_kernel<<<(n + 255) / 256, 256, 0, s>>>(eps, core_idx, n_core, omega, n_w, sigma, dh, sx, vxc, a, w_out);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_qp_finish_hedin(const QpState* st, const double* eps, const int* core_idx, int n_core, double* eps_qp,
                            double* dh, int* iters, cudaStream_t s) {

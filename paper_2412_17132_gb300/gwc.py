@@ -108,6 +108,8 @@ _SIGS = {
     "gwc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "gwc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "gwc_destroy": (None, [ctypes.c_void_p]),
+    "gwc_gdh_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_request_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "gwc_request_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_request_copy_results": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_void_p]),
@@ -309,6 +311,17 @@ class Context:
         _check(lib().gwc_cumulant_spectrum(self._ctx, _ptr(omega_rel), n_w, _ptr(im_sigma), _ptr(a), _ptr(nu), _stream(stream)),
                self._ctx)
         return a, nu
+
+    def gdh_spectrum(self, omega, sigma_c, dh, stream=None):
+        """G_dH W0 spectral function on w' + dH_n from Sigma^c on the common grid omega (CUDA tensors)."""
+        import torch
+
+        nw = int(omega.shape[0])
+        a = torch.empty((self.n_core, nw), dtype=torch.float64, device="cuda")
+        w = torch.empty((self.n_core, nw), dtype=torch.float64, device="cuda")
+        _check(lib().gwc_gdh_spectrum(self._ctx, _ptr(omega), nw, _ptr(sigma_c), _ptr(dh), _ptr(a), _ptr(w),
+                                      _stream(stream)), self._ctx)
+        return a, w
 
     # -- request mode (decoupled spectra + QP as one capturable step) -------------------------
     def request_plan(self, omega_rel, stream=None):

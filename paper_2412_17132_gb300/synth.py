@@ -143,18 +143,18 @@ def _coefficients(seed, eps, n_occ, n_core, n_aux, sigma=0.02, amp=5.0, frac=0.1
 
 
 def gram_norm_scale(eps, n_occ, o_ov, target=2.0):
-    """Factor s such that s^2 * ||sum_ia w_ia O_ia O_ia^T||_2 = target, w_ia = 4/(eps_a-eps_i)."""
-    n_virt = eps.shape[0] - n_occ
-    w = 4.0 / (eps[None, n_occ:] - eps[:n_occ, None]).reshape(-1)
-    if o_ov.shape[0] <= 2048:
-        g = (o_ov * w[None, :]) @ o_ov.T
-        lam = float(np.linalg.eigvalsh(g)[-1])
-    else:
-        from scipy.sparse.linalg import LinearOperator, eigsh
+    """Factor s such that s^2 * ||sum_ia w_ia O_ia O_ia^T||_2 = target, w_ia = 4/(eps_a-eps_i).
 
-        op = LinearOperator((o_ov.shape[0],) * 2, matvec=lambda v: o_ov @ (w * (o_ov.T @ v)), dtype=np.float64)
-        lam = float(eigsh(op, k=1, which="LA", tol=1e-13, v0=np.ones(o_ov.shape[0]))[0][0])
-    del n_virt
+    The weighted Gram matrix is formed explicitly (one BLAS product, chunked over the columns) and its
+    largest eigenvalue taken from a dense symmetric eigensolver."""
+    w = 4.0 / (eps[None, n_occ:] - eps[:n_occ, None]).reshape(-1)
+    n_aux = o_ov.shape[0]
+    g = np.zeros((n_aux, n_aux))
+    step = 8192
+    for k0 in range(0, o_ov.shape[1], step):
+        blk = o_ov[:, k0 : k0 + step]
+        g += (blk * w[None, k0 : k0 + step]) @ blk.T
+    lam = float(np.linalg.eigvalsh(g)[-1])
     return math.sqrt(target / lam)
 
 
@@ -334,17 +334,12 @@ def molecule_device(name, n_states, n_occ, n_core, n_aux, *, seed=0, core_lo=-10
     eps_t = torch.as_tensor(eps, device=dev)
     w = 4.0 / (eps_t[n_occ:][None, :] - eps_t[:n_occ][:, None]).reshape(-1)
     if exact_scale:
-        if n_aux <= 2048:
-            lam = float(torch.linalg.eigvalsh((o_ov * w[None, :]) @ o_ov.t())[-1])
-        else:
-            from scipy.sparse.linalg import LinearOperator, eigsh
-
-            def mv(v):
-                vt = torch.as_tensor(np.asarray(v).reshape(-1), device=dev)
-                return (o_ov @ (w * (o_ov.t() @ vt))).cpu().numpy()
-
-            op = LinearOperator((n_aux, n_aux), matvec=mv, dtype=np.float64)
-            lam = float(eigsh(op, k=1, which="LA", tol=1e-13, v0=np.ones(n_aux))[0][0])
+        g = torch.zeros((n_aux, n_aux), dtype=torch.float64, device=dev)
+        step = 8192
+        for k0 in range(0, o_ov.shape[1], step):
+            blk = o_ov[:, k0 : k0 + step]
+            g += (blk * w[None, k0 : k0 + step]) @ blk.t()
+        lam = float(np.linalg.eigvalsh(g.cpu().numpy())[-1])
         s = math.sqrt(2.0 / lam)
     else:
         v = torch.ones(n_aux, dtype=torch.float64, device=dev)

@@ -27,8 +27,10 @@ def main(out_path):
     mol = synth.pentacene()
     s = G.System.from_molecule(mol)
     t_gen = time.time() - t0
+    print(f"generated ({t_gen:.0f} s)", flush=True)
     s.w_imag_table()
     t_tab = time.time() - t0
+    print(f"imaginary-axis table ({t_tab:.0f} s)", flush=True)
     sx = s.sigma_x()
     res = {"workload": "pentacene-sized synthetic molecule (synth.pentacene(), seed 0)", "cores": CORES,
            "omega_idx": OMEGA_IDX, "sigma_x": [float(v) for v in sx], "eps": [float(mol.eps[c]) for c in CORES]}

@@ -295,3 +295,19 @@ def test_benzene_qp_gate_vs_oracle(gwc, prec):
     for c in (0, 3):
         assert abs(float(e[c]) - e_ref[c]) * EV <= 1e-3, (c, (float(e[c]) - e_ref[c]) * EV)
         assert abs(float(dh[c]) - dh_ref[c]) * EV <= 1e-3
+
+
+def test_gdh_spectral_function_matches_oracle(gwc, tiny, tiny_oracle):
+    """G_dH W0 spectral function from the GPU Sigma and Hedin shift vs the oracle's (FP64 path)."""
+    ctx = gwc.Context.from_molecule(tiny, prec="fp64")
+    sig, _, sx = ctx.sigma_core(tiny.omega)
+    e, dh, _ = ctx.qp_solve()
+    om = torch.as_tensor(tiny.omega, device="cuda")
+    a, w = ctx.gdh_spectrum(om, sig, dh)
+    ctx.sync()
+    ref_sig, _ = tiny_oracle.sigma_c_grid(tiny.omega)
+    dh_ref = tiny_oracle.hedin_shift()[0]
+    w_ref, a_ref = G.gdh_spectrum(tiny.omega, ref_sig[0], tiny.eps[0], dh_ref, tiny_oracle.sigma_x()[0],
+                                  tiny_oracle.v_xc()[0])
+    assert np.max(np.abs(w[0].cpu().numpy() - w_ref)) < 1e-9
+    assert np.max(np.abs(a[0].cpu().numpy() - a_ref)) <= 1e-6 * np.max(a_ref)

@@ -408,3 +408,38 @@ def test_peak_finder_on_parabola():
     a = 1.0 - (nu - 0.0123) ** 2
     (p, h), = G.find_peaks(nu, a)
     assert abs(p - 0.0123) < 1e-12 and abs(h - 1.0) < 1e-12
+
+
+# ----------------------------------------------------------------------------------------
+# G_dH W0 spectral function (eqs gw_full_propagator, A_explicit_real_imaginary, hedin_sigma_spectral)
+# ----------------------------------------------------------------------------------------
+
+
+def test_gw_spectral_function_of_the_three_level_model():
+    # With Sigma^c(w) = rho^2/(w - eps_c + Omega - i eta) (eq sigma_spectral for the model) and
+    # v^xc = Sigma^x, G has the two poles x = (-Omega +- sqrt(Omega^2 + 4 rho^2))/2 (x = w - eps_c):
+    # one QP peak and one satellite below it, with weights (x_+ + Omega)/(x_+ - x_-) and the rest.
+    om, rho, eta, ec = 0.5, 0.2, 1e-4, -10.0
+    w = np.linspace(ec - 1.5, ec + 0.5, 200001)
+    sig = rho**2 / (w - ec + om - 1j * eta)
+    ww, a = G.gdh_spectrum(w, sig, ec, 0.0, -3.0, -3.0)
+    disc = math.sqrt(om * om + 4 * rho * rho)
+    xp, xm = (-om + disc) / 2, (-om - disc) / 2
+    pk = sorted(p for p, h in G.find_peaks(ww - ec, a, 1e-3))
+    assert len(pk) == 2
+    assert abs(pk[1] - xp) < 2e-5 and abs(pk[0] - xm) < 2e-5
+    dw = w[1] - w[0]
+    wp = (xp + om) / (xp - xm)
+    assert abs(np.sum(a[np.abs(ww - ec - xp) < 0.05]) * dw - wp) < 5e-3
+    assert abs(np.sum(a) * dw - 1.0) < 5e-3
+
+
+def test_gdh_qp_peak_sits_at_eps_plus_hedin_shift(tiny_mol):
+    # the real part of the G_dH W0 denominator vanishes at w = eps_n + dH_n (eq QPGWC)
+    s = G.System.from_molecule(tiny_mol)
+    ec = float(tiny_mol.eps[0])
+    dh = s.hedin_shift()[0]
+    sig0 = s.sigma_c_core(0, ec)
+    w, a = G.gdh_spectrum(np.array([ec]), np.array([sig0]), ec, dh, s.sigma_x()[0], s.v_xc()[0])
+    re = w[0] - ec + s.v_xc()[0] - s.sigma_x()[0] - sig0.real
+    assert abs(w[0] - (ec + dh)) < 1e-15 and abs(re) < 1e-12
