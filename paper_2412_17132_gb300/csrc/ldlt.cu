@@ -45,15 +45,17 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 // Shared-memory layout of the factor kernel (element type S):
-//   lkk [NB][NB+1], dinv [NB], then 2 stages of { X [TT][KC + PADX], Y [KC][TT] }
+//   lkk [NB][NB+1], dinv [NB], then 2 stages of { X [TT][KC + PADX], Y [KC][TT] }, then the
+//   prefetched target tile C [TT][TT] of the read-modify-write
 template <typename S>
 struct FactorSmem {
   static constexpr int PADX = 16 / (int)sizeof(S);
   static constexpr int XS = TT * (KC + PADX);
   static constexpr int YS = KC * TT;
   static constexpr int STAGE = XS + YS;
+  static constexpr int CS = TT * TT;
   static constexpr size_t LKK_BYTES = ((sizeof(S) * (NB * (NB + 1) + NB)) + 15) / 16 * 16;
-  static constexpr size_t bytes() { return LKK_BYTES + 2 * sizeof(S) * STAGE; }
+  static constexpr size_t bytes() { return LKK_BYTES + sizeof(S) * (2 * STAGE + CS); }
 };
 
 // A[i][j] -= sum_{l in [k0, k0+klen)} W[i][l] L[j][l] for rows [r0, n), columns [c0, c1), j <= i.
@@ -91,11 +93,24 @@ __device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, i
     }
   };
 
+  S* Cs = stages + 2 * SM::STAGE;  // target tile, prefetched with the tile's last chunk (nk > 1)
   auto issue = [&](const It& it, S* buf) {
     const int i0 = r0 + TT * it.tI, j0 = c0 + TT * it.tJ;
     const int kc = k0 + it.chunk * KC;
     S* X = buf;
     S* Y = buf + SM::XS;
+    if (nk > 1 && it.chunk == nk - 1) {
+      // C[ii][jj] = A[i0+ii][j0+jj]; the previous tile's read-modify-write is complete (it ended
+      // before this tile's first chunk was computed), so the single buffer is free
+      constexpr int CPR = TT / PER;
+      for (int e = tid; e < TT * CPR; e += blockDim.x) {
+        const int ii = e / CPR, jj = (e % CPR) * PER;
+        const int gi = i0 + ii, gj = j0 + jj;
+        const bool ok = gi < n && gj < n;
+        const S* src = ok ? A + (long long)gi * ldm + gj : A;
+        cp_async16(Cs + ii * TT + jj, src, ok);
+      }
+    }
     // X[ii][l] = A[i0+ii][kc+l]   (TT rows x KC, 16-byte pieces along l)
     constexpr int XPR = KC / PER;  // pieces per row
     for (int e = tid; e < TT * XPR; e += blockDim.x) {
@@ -163,7 +178,8 @@ __device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, i
           const int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
           if (gi < n && gj < c1 && gj <= gi) {
             S* p = A + (long long)gi * ldm + gj;
-            *p = sadd(*p, acc[a][b]);
+            const S c = nk > 1 ? Cs[(ty + 16 * a) * TT + tx + 16 * b] : *p;
+            *p = sadd(c, acc[a][b]);
           }
           acc[a][b] = szero<S>();
         }
