@@ -177,6 +177,18 @@ gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double
  * GWC_ERR_NOT_CONVERGED (reported by gwc_sync). */
 gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, void* stream);
 
+/* Sigma^c of every core on an absolute grid by CD-WAC (Sec. "Self-energy evaluation", eq
+ * pade_approximation): the imaginary-axis term as in gwc_sigma_core; W^c_mn for each occupied residue
+ * state m and core n is a continued fraction (Thiele interpolation) through its values at the
+ * imaginary-axis nodes, at i0 and at real reference points x_l + i eta: n_core_ref points uniform on
+ * [0, 40 eV] and n_val_ref points uniform on [0.92 x_lo, 1.01 x_hi], x_lo/x_hi bounding |eps_m - w| over
+ * the non-core occupied states with a residue on the grid (0/0: 100/100). One dielectric build per real
+ * reference point replaces one per (w_j, m). Frequencies must lie below the LUMO (occupied residues).
+ *   omega: HOST [n_omega]; sigma_c: DEVICE [n_core][n_omega][2]; im_sigma_dec: DEVICE [n_core][n_omega]
+ *   (DIAG decoupled Im Sigma from the fitted W^c_nn) or NULL. Allocates scratch; synchronises `stream`. */
+gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
+                              double* sigma_c, double* im_sigma_dec, void* stream);
+
 /* G_dH W0 spectral function beside GW+C (Sec. "G0W0 approximation": eqs gw_full_propagator,
  * A_definition, A_explicit_real_imaginary, with the shifted self-energy of eq hedin_sigma_spectral):
  * from Sigma^c_n(w') on a common grid w' (as gwc_sigma_core returns it) and the Hedin shifts,

@@ -283,6 +283,92 @@ class System:
 
 
 # ----------------------------------------------------------------------------------------
+# CD-WAC: W^c_mn(w) by analytic continuation (Sec. "Self-energy evaluation", Eq. pade_approximation)
+# ----------------------------------------------------------------------------------------
+
+
+def thiele_coefficients(zref: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Coefficients of the continued fraction C(z) = a_0/(1 + a_1(z - z_0)/(1 + a_2(z - z_1)/(1 + ...)))
+    through the points (z_i, u_i) (Eq. pade_approximation; Thiele's interpolation, recursion of
+    Vidberg and Serene, J. Low Temp. Phys. 29, 179 (1977)):
+    g_0(z_i) = u_i,  g_p(z_i) = [g_{p-1}(z_{p-1}) - g_{p-1}(z_i)] / [(z_i - z_{p-1}) g_{p-1}(z_i)],  a_p = g_p(z_p)."""
+    g = np.array(u, dtype=np.complex128)
+    z = np.asarray(zref, dtype=np.complex128)
+    a = np.empty(g.size, dtype=np.complex128)
+    a[0] = g[0]
+    for p in range(1, g.size):
+        g[p:] = (g[p - 1] - g[p:]) / ((z[p:] - z[p - 1]) * g[p:])
+        a[p] = g[p]
+    return a
+
+
+def thiele_eval(a: np.ndarray, zref: np.ndarray, z) -> np.ndarray:
+    """C(z) of thiele_coefficients, evaluated from the innermost level outwards."""
+    z = np.asarray(z, dtype=np.complex128)
+    t = np.ones_like(z)
+    for p in range(a.size - 1, 0, -1):
+        t = 1.0 + a[p] * (z - zref[p - 1]) / t
+    return a[0] / t
+
+
+def wac_reference_points(eps, n_occ, core_idx, omegas, eps_f, n_core_ref=100, n_val_ref=100, wc_max_ev=40.0,
+                         d_lower=0.08, d_upper=0.01):
+    """Real reference frequencies x (W is sampled at x + i eta).
+
+    Reading of the paper's parameters (Sec. "Computational Details": N_C = N_V = 100 points,
+    w_C in [0, 40] eV for the core region, Delta_lower = 8 %, Delta_upper = 1 % for the valence
+    region): N_C points uniform on [0, w_C^max]; N_V points uniform on [x_lo (1 - Delta_lower),
+    x_hi (1 + Delta_upper)], where x_lo, x_hi bound |eps_m - w| over the non-core occupied states m
+    with a nonzero residue prefactor on the requested frequencies.
+    """
+    cores = set(int(c) for c in core_idx)
+    xs = [abs(eps[m] - w) for w in omegas for m in range(n_occ)
+          if m not in cores and residue_prefactor(eps[m], w, eps_f) != 0.0]
+    core_pts = np.linspace(0.0, wc_max_ev / 27.211386245988, n_core_ref)
+    if not xs:
+        return core_pts
+    lo, hi = min(xs) * (1.0 - d_lower), max(xs) * (1.0 + d_upper)
+    return np.concatenate([core_pts, np.linspace(lo, hi, n_val_ref)])
+
+
+def sigma_c_wac(system, omegas, xref):
+    """Sigma^c_n(w) = -I_n(w) + R_n(w) with R from the continued-fraction W^c_mn.
+
+    Reference values: W^c_mn(i xi_k) (the imaginary-axis quadrature nodes and i0, real) and
+    W^c_mn(x_l + i eta) at the real reference points; one fit per (occupied m, core n).
+    Returns complex [n_core][n_w]."""
+    s = system
+    tab, w0 = s.w_imag_table()
+    zim = np.concatenate([1j * s.xi, [0.0]])
+    zre = xref + 1j * s.eta
+    # W at the real references for every occupied m and core n: one build per reference frequency
+    wre = np.empty((xref.size, s.n_occ, s.n_core), dtype=np.complex128)
+    rhs = s.o_core[: s.n_occ].reshape(s.n_occ * s.n_core, -1).T
+    for l, z in enumerate(zre):
+        wre[l] = screened_wc(chi0(s.o_ov, s.delta, z), rhs).reshape(s.n_occ, s.n_core)
+    zref = np.concatenate([zim, zre])
+    coef = {}
+    for m in range(s.n_occ):
+        for c in range(s.n_core):
+            u = np.concatenate([tab[:, m, c], [w0[m, c]], wre[:, m, c]])
+            coef[(m, c)] = thiele_coefficients(zref, u)
+    out = np.empty((s.n_core, len(omegas)), dtype=np.complex128)
+    for j, w in enumerate(omegas):
+        i_term = s.imag_axis_term(float(w))
+        for c in range(s.n_core):
+            r = 0.0 + 0.0j
+            for m in range(s.n_states):
+                f = residue_prefactor(s.eps[m], float(w), s.eps_f)
+                if f == 0.0:
+                    continue
+                if m >= s.n_occ:
+                    raise ValueError("CD-WAC here covers frequencies below the LUMO (occupied residues only)")
+                r += f * thiele_eval(coef[(m, c)], zref, abs(s.eps[m] - w) + 1j * s.eta)
+            out[c, j] = -i_term[c] + r
+    return out
+
+
+# ----------------------------------------------------------------------------------------
 # G_dH W0 spectral function (Sec. "G0W0 approximation": Eqs. g_dyson, gw_full_propagator,
 # A_definition, A_explicit_real_imaginary, with the shifted self-energy of Eq. hedin_sigma_spectral)
 # ----------------------------------------------------------------------------------------

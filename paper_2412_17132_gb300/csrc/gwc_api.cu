@@ -367,13 +367,15 @@ gwc_status compute_wim(gwc_ctx* ctx, cudaStream_t st) {
 
 // ---- residue W for a list of (frequency, state m) pairs ---------------------------------------------
 // z_dev [n_pairs][2], rows_dev [n_pairs * r] (rows of o_core flattened [m][c]), output w [n_pairs][r][2].
-gwc_status residue_batches(gwc_ctx* ctx, int n_pairs, const double* z_dev, const int* rows_dev, int r, double* w_out,
-                           const int* active, cudaStream_t st) {
+// rhs/bnorm: right-hand-side staging for `chunk` frequencies of r vectors each.
+gwc_status residue_batches_buf(gwc_ctx* ctx, int n_pairs, const double* z_dev, const int* rows_dev, int r, double* w_out,
+                               const int* active, void* rhs, double* bnorm, int chunk, cudaStream_t st) {
   MatKind ck = cplx_kind(ctx);
   const long long stride = (long long)ctx->n_aux * ctx->ldm;
   const long long rstride = (long long)r * ctx->ldm;
-  for (int p0 = 0; p0 < n_pairs; p0 += ctx->batch) {
-    const int nb = std::min(ctx->batch, n_pairs - p0);
+  chunk = std::max(1, std::min(chunk, ctx->batch));
+  for (int p0 = 0; p0 < n_pairs; p0 += chunk) {
+    const int nb = std::min(chunk, n_pairs - p0);
     const int* act = active ? active + p0 : nullptr;
     TRY(run_chi0(ctx, true, nb, z_dev + 2 * (size_t)p0, act, ctx->d_mats, -1.0, 1.0, 0, st));
     cudaEvent_t ev = ev_begin(ctx, st);
@@ -381,14 +383,19 @@ gwc_status residue_batches(gwc_ctx* ctx, int n_pairs, const double* z_dev, const
     ev_end(ctx, kClsFactor, ev, st);
     ctx->stats.factorizations += nb;
     ctx->stats.factor_flop += factor_flop(ctx->n_aux, true, nb);
-    LAUNCH(launch_rhs_gather(ck, ctx->d_o_core, ctx->n_aux, rows_dev + (size_t)p0 * r, nb, r, ctx->n_aux, ctx->d_rhs,
-                             ctx->ldm, rstride, ctx->d_bnorm, st));
+    LAUNCH(launch_rhs_gather(ck, ctx->d_o_core, ctx->n_aux, rows_dev + (size_t)p0 * r, nb, r, ctx->n_aux, rhs, ctx->ldm,
+                             rstride, bnorm, st));
     cudaEvent_t evs = ev_begin(ctx, st);
-    LAUNCH(launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs, r, ctx->ldm, rstride,
-                               ctx->d_bnorm, nb, w_out + (size_t)p0 * r * 2, (long long)r * 2, act, st));
+    LAUNCH(launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, rhs, r, ctx->ldm, rstride, bnorm, nb,
+                               w_out + (size_t)p0 * r * 2, (long long)r * 2, act, st));
     ev_end(ctx, kClsSolve, evs, st);
   }
   return GWC_OK;
+}
+
+gwc_status residue_batches(gwc_ctx* ctx, int n_pairs, const double* z_dev, const int* rows_dev, int r, double* w_out,
+                           const int* active, cudaStream_t st) {
+  return residue_batches_buf(ctx, n_pairs, z_dev, rows_dev, r, w_out, active, ctx->d_rhs, ctx->d_bnorm, ctx->batch, st);
 }
 
 // QP rounds on the device (eqs hedin_shift, quasiparticle_equation, hedin_sigma_spectral, QPGWC).
@@ -803,6 +810,98 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
   }
   LAUNCH(launch_cumulant_spectrum(omega_rel, n_omega, im_sigma, (int)nc, (int)nt, ctx->opt.t_max, ctx->opt.eta,
                                   ctx->d_cw_a, ctx->d_cw_b, ctx->d_coef, ctx->d_tw, a_out, nu_out, st));
+  return check_stream_error(ctx);
+}
+
+gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
+                              double* sigma_c, double* im_sigma_dec, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!omega || !sigma_c || n_omega < 1 || n_omega > (1 << 20) || n_core_ref < 0 || n_val_ref < 0 ||
+      n_core_ref + n_val_ref > 4096)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "need omega, sigma_c, 1 <= n_omega <= 2^20, reference counts in 0..4096");
+  if (n_core_ref == 0 && n_val_ref == 0) n_core_ref = n_val_ref = 100;
+  cudaStream_t st = (cudaStream_t)stream;
+  TRY(compute_wim(ctx, st));
+  auto th = [](double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); };
+  // real reference points (reading of the paper's N_C, N_V, w_C^max = 40 eV, Delta_lower/upper = 8 %/1 %)
+  std::vector<double> xref;
+  for (int l = 0; l < n_core_ref; ++l)
+    xref.push_back(n_core_ref > 1 ? (40.0 / 27.211386245988) * l / (n_core_ref - 1) : 0.0);
+  double lo = 1e300, hi = -1e300;
+  for (int j = 0; j < n_omega; ++j)
+    for (int m = 0; m < ctx->n_occ; ++m) {
+      if (std::find(ctx->h_core.begin(), ctx->h_core.end(), m) != ctx->h_core.end()) continue;
+      const double em = ctx->h_eps[m], w = omega[j];
+      const double f = -th(ctx->eps_f - em) * th(em - w) + th(em - ctx->eps_f) * th(w - em);
+      if (f == 0.0) continue;
+      lo = std::min(lo, std::fabs(em - w));
+      hi = std::max(hi, std::fabs(em - w));
+    }
+  if (hi >= lo && n_val_ref > 0) {
+    lo *= 1.0 - 0.08;
+    hi *= 1.0 + 0.01;
+    for (int l = 0; l < n_val_ref; ++l) xref.push_back(n_val_ref > 1 ? lo + (hi - lo) * l / (n_val_ref - 1) : lo);
+  }
+  const int n_ref = (int)xref.size(), n_im = ctx->opt.n_im, n_pts = n_im + 1 + n_ref;
+  const int pairs = ctx->n_occ * ctx->n_core;
+  if (n_ref == 0) return fail(ctx, GWC_ERR_INVALID_ARG, "no real reference points");
+  std::vector<double> zall(2 * (size_t)n_pts), zreal(2 * (size_t)n_ref);
+  std::vector<double> xi(n_im);
+  CU(cudaMemcpyAsync(xi.data(), ctx->d_xi, sizeof(double) * n_im, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  for (int k = 0; k < n_im; ++k) zall[2 * k + 1] = xi[k];
+  for (int l = 0; l < n_ref; ++l) {
+    zall[2 * (n_im + 1 + l)] = zreal[2 * l] = xref[l];
+    zall[2 * (n_im + 1 + l) + 1] = zreal[2 * l + 1] = ctx->opt.eta;
+  }
+  std::vector<int> rows((size_t)n_ref * pairs);
+  for (int l = 0; l < n_ref; ++l)
+    for (int p = 0; p < pairs; ++p) rows[(size_t)l * pairs + p] = p;  // o_core row (m, c) = m n_core + c, m < n_occ
+  const size_t es = mat_elem_bytes(cplx_kind(ctx));
+  int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)ctx->batch, ((size_t)1 << 31) / ((size_t)pairs * ctx->ldm * es)));
+  chunk = std::min(chunk, n_ref);
+  double *d_zall = nullptr, *d_zreal = nullptr, *d_wref = nullptr, *d_coef = nullptr, *d_om = nullptr, *d_bn = nullptr;
+  int* d_rows = nullptr;
+  void* d_rhs = nullptr;
+  auto release = [&]() {
+    cudaFree(d_zall);
+    cudaFree(d_zreal);
+    cudaFree(d_wref);
+    cudaFree(d_coef);
+    cudaFree(d_om);
+    cudaFree(d_bn);
+    cudaFree(d_rows);
+    cudaFree(d_rhs);
+  };
+  if (cudaMalloc(&d_zall, sizeof(double) * zall.size()) != cudaSuccess ||
+      cudaMalloc(&d_zreal, sizeof(double) * zreal.size()) != cudaSuccess ||
+      cudaMalloc(&d_wref, sizeof(double) * 2 * (size_t)n_ref * pairs) != cudaSuccess ||
+      cudaMalloc(&d_coef, sizeof(double) * 2 * (size_t)pairs * n_pts) != cudaSuccess ||
+      cudaMalloc(&d_om, sizeof(double) * n_omega) != cudaSuccess ||
+      cudaMalloc(&d_bn, sizeof(double) * (size_t)chunk * pairs) != cudaSuccess ||
+      cudaMalloc(&d_rows, sizeof(int) * rows.size()) != cudaSuccess ||
+      cudaMalloc(&d_rhs, (size_t)chunk * pairs * ctx->ldm * es) != cudaSuccess) {
+    release();
+    return fail(ctx, GWC_ERR_OOM, "CD-WAC scratch allocation failed");
+  }
+  gwc_status res = GWC_OK;
+  if (cudaMemcpyAsync(d_zall, zall.data(), sizeof(double) * zall.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d_zreal, zreal.data(), sizeof(double) * zreal.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d_om, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    res = fail(ctx, GWC_ERR_CUDA, "CD-WAC upload failed");
+  if (res == GWC_OK) res = residue_batches_buf(ctx, n_ref, d_zreal, d_rows, pairs, d_wref, nullptr, d_rhs, d_bn, chunk, st);
+  if (res == GWC_OK) {
+    int n1 = launch_thiele_fit(ctx->d_wim, ctx->n_states, ctx->n_core, n_im, d_wref, n_ref, pairs, d_zall, d_coef, st);
+    int n2 = launch_sigma_grid_wac(ctx->d_eps, ctx->n_states, ctx->n_occ, ctx->n_core, ctx->d_core_idx, d_om, n_omega,
+                                   ctx->eps_f, ctx->opt.eta, ctx->d_xi, ctx->d_wxi, n_im, ctx->d_wim, d_coef, d_zall, n_pts,
+                                   sigma_c, im_sigma_dec, ctx->d_status, st);
+    if (n1 < 0 || n2 < 0) res = fail(ctx, GWC_ERR_CUDA, "CD-WAC launch failed");
+    ctx->stats.kernel_launches += std::max(0, n1) + std::max(0, n2);
+  }
+  cudaStreamSynchronize(st);
+  release();
+  if (res != GWC_OK) return res;
   return check_stream_error(ctx);
 }
 

@@ -166,6 +166,14 @@ int launch_qp_finish(const QpState* st, int n_core, double* eps_qp, double* dh, 
 int launch_qp_finish_hedin(const QpState* st, const double* eps, const int* core_idx, int n_core, double* eps_qp,
                            double* dh, int* iters, cudaStream_t s);
 
+// CD-WAC: continued-fraction coefficients per (occupied m, core c) and the self-energy from them
+int launch_thiele_fit(const double* wim, int n_states, int n_core, int n_im, const double* wref, int n_ref, int n_pairs,
+                      const double* zref, double* coef, cudaStream_t s);
+int launch_sigma_grid_wac(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx, const double* omega,
+                          int n_w, double eps_f, double eta, const double* xi, const double* wxi, int n_im,
+                          const double* wim, const double* coef, const double* zref, int n_pts, double* sigma,
+                          double* im_dec, unsigned* status, cudaStream_t s);
+
 int launch_gdh_spectrum(const double* eps, const int* core_idx, int n_core, const double* omega, int n_w,
                         const double* sigma, const double* dh, const double* sx, const double* vxc, double* a,
                         double* w_out, cudaStream_t s);

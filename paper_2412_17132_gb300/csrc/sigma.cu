@@ -248,7 +248,114 @@ __global__ void gdh_spectrum_kernel(const double* __restrict__ eps, const int* _
   if (w_out) w_out[t] = w;
 }
 
+// ---- CD-WAC (Eq. pade_approximation) ------------------------------------------------------------
+// Continued-fraction coefficients through (z_i, u_i), one thread per (occupied m, core c) pair:
+// g_0(z_i) = u_i, g_p(z_i) = [g_{p-1}(z_{p-1}) - g_{p-1}(z_i)] / [(z_i - z_{p-1}) g_{p-1}(z_i)], a_p = g_p(z_p).
+// u: W^c(i xi_k) (k < n_im), W^c(i0), then W^c(x_l + i eta) (l < n_ref). In place in a[pair][n_pts].
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+__global__ void thiele_fit_kernel(const double* __restrict__ wim, int n_states, int n_core, int n_im,
+                                  const double* __restrict__ wref /*[n_ref][n_pairs][2]*/, int n_ref, int n_pairs,
+                                  const double2* __restrict__ zref, double2* __restrict__ a) {
+  const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pr >= n_pairs) return;
+  const int m = pr / n_core, c = pr % n_core;
+  const int n_pts = n_im + 1 + n_ref;
+  double2* g = a + (size_t)pr * n_pts;
+  const size_t plane = (size_t)n_states * n_core;
+  for (int k = 0; k <= n_im; ++k) g[k] = make_double2(wim[(size_t)k * plane + (size_t)m * n_core + c], 0.0);
+  for (int l = 0; l < n_ref; ++l) {
+    const double* w = wref + ((size_t)l * n_pairs + pr) * 2;
+    g[n_im + 1 + l] = make_double2(w[0], w[1]);
+  }
+  for (int p = 1; p < n_pts; ++p) {
+    const double2 gp = g[p - 1], zp = zref[p - 1];
+    for (int i = p; i < n_pts; ++i) {
+      const double2 gi = g[i];
+      const double2 dz = make_double2(zref[i].x - zp.x, zref[i].y - zp.y);
+      g[i] = cdiv(make_double2(gp.x - gi.x, gp.y - gi.y), cmul(dz, gi));
+    }
+  }
+}
+
+__device__ __forceinline__ double2 thiele_eval(const double2* __restrict__ a, const double2* __restrict__ zref, int n,
+                                               double2 z) {
+  double2 t = make_double2(1.0, 0.0);
+  for (int p = n - 1; p > 0; --p) {
+    const double2 dz = make_double2(z.x - zref[p - 1].x, z.y - zref[p - 1].y);
+    const double2 q = cdiv(cmul(a[p], dz), t);
+    t = make_double2(1.0 + q.x, q.y);
+  }
+  return cdiv(a[0], t);
+}
+
+// Sigma^c by CD-WAC: the imaginary-axis term as in CD, the residue term from the continued fraction.
+__global__ void sigma_grid_wac_kernel(const double* __restrict__ eps, int n_states, int n_occ, int n_core,
+                                      const int* __restrict__ core_idx, const double* __restrict__ omega, int n_w,
+                                      double eps_f, double eta, const double* __restrict__ xi,
+                                      const double* __restrict__ wxi, int n_im, const double* __restrict__ wim,
+                                      const double2* __restrict__ coef, const double2* __restrict__ zref, int n_pts,
+                                      double* __restrict__ sigma, double* __restrict__ im_dec,
+                                      unsigned* __restrict__ status) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_core * n_w) return;
+  const int c = warp / n_w, j = warp % n_w;
+  const double w = omega[j];
+  const int n = core_idx[c];
+  double si = 0.0, rr = 0.0, ri = 0.0, dec = 0.0;
+  for (int m = lane; m < n_states; m += 32) {
+    const double em = eps[m];
+    si += imag_term(w - em, m, c, n_states, n_core, xi, wxi, n_im, wim);
+    const double f = prefactor(em, w, eps_f);
+    if (f == 0.0) continue;
+    if (m >= n_occ) {  // a virtual residue (w above the LUMO) has no fit: flag it
+      atomicOr(status, kStatBadIndex);
+      continue;
+    }
+    const double2 wv = thiele_eval(coef + (size_t)(m * n_core + c) * n_pts, zref, n_pts, make_double2(fabs(em - w), eta));
+    rr += f * wv.x;
+    ri += f * wv.y;
+    if (m == n) dec += f * wv.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    si += __shfl_down_sync(0xffffffffu, si, o);
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+    ri += __shfl_down_sync(0xffffffffu, ri, o);
+    dec += __shfl_down_sync(0xffffffffu, dec, o);
+  }
+  if (lane == 0) {
+    double* o = sigma + ((size_t)c * n_w + j) * 2;
+    o[0] = -si + rr;
+    o[1] = ri;
+    if (im_dec) im_dec[(size_t)c * n_w + j] = dec;
+  }
+}
+
 }  // namespace
+
+int launch_thiele_fit(const double* wim, int n_states, int n_core, int n_im, const double* wref, int n_ref, int n_pairs,
+                      const double* zref, double* coef, cudaStream_t s) {
+  thiele_fit_kernel<<<(n_pairs + 63) / 64, 64, 0, s>>>(wim, n_states, n_core, n_im, wref, n_ref, n_pairs,
+                                                       (const double2*)zref, (double2*)coef);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_sigma_grid_wac(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx, const double* omega,
+                          int n_w, double eps_f, double eta, const double* xi, const double* wxi, int n_im,
+                          const double* wim, const double* coef, const double* zref, int n_pts, double* sigma,
+                          double* im_dec, unsigned* status, cudaStream_t s) {
+  long long warps = (long long)n_core * n_w;
+  int blocks = (int)((warps * 32 + 255) / 256);
+  sigma_grid_wac_kernel<<<blocks, 256, 0, s>>>(eps, n_states, n_occ, n_core, core_idx, omega, n_w, eps_f, eta, xi, wxi,
+                                               n_im, wim, (const double2*)coef, (const double2*)zref, n_pts, sigma,
+                                               im_dec, status);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_gdh_spectrum(const double* eps, const int* core_idx, int n_core, const double* omega, int n_w,
                         const double* sigma, const double* dh, const double* sx, const double* vxc, double* a,

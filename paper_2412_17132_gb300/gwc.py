@@ -108,6 +108,8 @@ _SIGS = {
     "gwc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "gwc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "gwc_destroy": (None, [ctypes.c_void_p]),
+    "gwc_sigma_core_wac": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_gdh_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_request_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -311,6 +313,17 @@ class Context:
         _check(lib().gwc_cumulant_spectrum(self._ctx, _ptr(omega_rel), n_w, _ptr(im_sigma), _ptr(a), _ptr(nu), _stream(stream)),
                self._ctx)
         return a, nu
+
+    def sigma_core_wac(self, omega, n_core_ref=100, n_val_ref=100, stream=None):
+        """Sigma^c by CD-WAC on the host grid omega: CUDA tensors (sigma [n_core][n_w][2], decoupled Im)."""
+        import torch
+
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        sig = torch.empty((self.n_core, om.shape[0], 2), dtype=torch.float64, device="cuda")
+        dec = torch.empty((self.n_core, om.shape[0]), dtype=torch.float64, device="cuda")
+        _check(lib().gwc_sigma_core_wac(self._ctx, om.ctypes.data, om.shape[0], int(n_core_ref), int(n_val_ref), _ptr(sig),
+                                        _ptr(dec), _stream(stream)), self._ctx)
+        return sig, dec
 
     def gdh_spectrum(self, omega, sigma_c, dh, stream=None):
         """G_dH W0 spectral function on w' + dH_n from Sigma^c on the common grid omega (CUDA tensors)."""

@@ -311,3 +311,29 @@ def test_gdh_spectral_function_matches_oracle(gwc, tiny, tiny_oracle):
                                   tiny_oracle.v_xc()[0])
     assert np.max(np.abs(w[0].cpu().numpy() - w_ref)) < 1e-9
     assert np.max(np.abs(a[0].cpu().numpy() - a_ref)) <= 1e-6 * np.max(a_ref)
+
+
+def test_cdwac_exact_for_few_poles_and_matches_oracle(gwc):
+    """CD-WAC on the GPU: equals CD (GPU) and the oracle's CD-WAC when W has few poles (the fit is exact)."""
+    mol = synth.small(n_states=4, n_occ=2, n_core=1, n_aux=6, seed=13, n_high=1, n_omega=9)
+    ctx = gwc.Context.from_molecule(mol, prec="fp64")
+    wac, dec = ctx.sigma_core_wac(mol.omega, 10, 10)
+    cd, cd_dec, _ = ctx.sigma_core(mol.omega)
+    ctx.sync()
+    assert float((wac - cd).abs().max()) < 1e-7
+    s = G.System.from_molecule(mol)
+    xref = G.wac_reference_points(mol.eps, mol.n_occ, mol.core_idx, mol.omega, s.eps_f, n_core_ref=10, n_val_ref=10)
+    ref = G.sigma_c_wac(s, mol.omega, xref)
+    assert np.max(np.abs(_cplx(wac) - ref)) < 1e-7
+
+
+def test_cdwac_hedin_shift_matches_oracle_tiny(gwc, tiny, tiny_oracle):
+    """At w = eps_n (the Hedin shift) the references reproduce the residues; GPU CD-WAC vs oracle CD-WAC."""
+    ctx = gwc.Context.from_molecule(tiny, prec="fp64")
+    w = np.array([tiny.eps[0], tiny.eps[0] + 0.05])
+    wac, _ = ctx.sigma_core_wac(w)
+    ctx.sync()
+    xref = G.wac_reference_points(tiny.eps, tiny.n_occ, tiny.core_idx, w, tiny_oracle.eps_f)
+    ref = G.sigma_c_wac(tiny_oracle, w, xref)
+    assert np.max(np.abs(_cplx(wac) - ref)) < 1e-6
+    assert abs(_cplx(wac)[0, 0].real - tiny_oracle.sigma_c_core(0, float(tiny.eps[0])).real) * EV < 1e-3

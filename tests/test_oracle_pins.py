@@ -443,3 +443,38 @@ def test_gdh_qp_peak_sits_at_eps_plus_hedin_shift(tiny_mol):
     w, a = G.gdh_spectrum(np.array([ec]), np.array([sig0]), ec, dh, s.sigma_x()[0], s.v_xc()[0])
     re = w[0] - ec + s.v_xc()[0] - s.sigma_x()[0] - sig0.real
     assert abs(w[0] - (ec + dh)) < 1e-15 and abs(re) < 1e-12
+
+
+# ----------------------------------------------------------------------------------------
+# CD-WAC (Eq. pade_approximation): the continued fraction interpolates, reproduces rational
+# functions exactly, and then gives the CD self-energy exactly
+# ----------------------------------------------------------------------------------------
+
+
+def test_thiele_interpolates_and_reproduces_rational_functions():
+    rng = np.random.default_rng(3)
+    z = rng.uniform(-2, 2, 12) + 1j * rng.uniform(0.1, 2, 12)
+    u = rng.normal(size=12) + 1j * rng.normal(size=12)
+    a = G.thiele_coefficients(z, u)
+    assert np.max(np.abs(G.thiele_eval(a, z, z) - u)) < 1e-9 * np.max(np.abs(u))
+    # W^c of three poles is a rational function of degree 6: 13 points determine it everywhere
+    rho, om = np.array([0.3, 0.2, 0.1]), np.array([0.7, 1.9, 3.4])
+
+    def w(zz):
+        return np.sum(rho[:, None] ** 2 * 2 * om[:, None] / (np.asarray(zz)[None, :] ** 2 - om[:, None] ** 2), axis=0)
+
+    zr = np.concatenate([1j * np.linspace(0.1, 5, 7), np.linspace(0.2, 4.0, 7) + 1e-3j])
+    a = G.thiele_coefficients(zr, w(zr))
+    zt = np.array([0.55 + 1e-3j, 2.7 + 1e-3j, 1.1j, 7.0 + 1e-3j])
+    assert np.max(np.abs(G.thiele_eval(a, zr, zt) - w(zt))) < 1e-8 * np.max(np.abs(w(zt)))
+
+
+def test_cdwac_equals_cd_when_w_has_few_poles():
+    # 2 occupied x 2 virtual states -> 4 RPA poles: W^c_mn is rational of degree 8, so the fit through
+    # 33 + 20 reference points is exact and CD-WAC reproduces the CD self-energy
+    m = synth.small(n_states=4, n_occ=2, n_core=1, n_aux=6, seed=13, n_high=1, n_omega=9)
+    s = G.System.from_molecule(m, n_im=32)
+    xref = G.wac_reference_points(m.eps, m.n_occ, m.core_idx, m.omega, s.eps_f, n_core_ref=10, n_val_ref=10)
+    wac = G.sigma_c_wac(s, m.omega, xref)
+    cd = np.array([s.sigma_c(float(w))[0] for w in m.omega]).T
+    assert np.max(np.abs(wac - cd)) < 1e-7 * max(1.0, np.max(np.abs(cd)))
