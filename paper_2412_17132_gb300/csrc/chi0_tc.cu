@@ -414,34 +414,65 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!ok) break;
       tc_fence_after();
       const bool last = seg == n_seg - 1;
-      for (int part = 0; part < n_parts; ++part) {
-        const int fl = part / p.ppf;
-        const int f = f0 + fl;
-        const bool write = last && (!p.active || p.active[f]);
-        for (int cc = 0; cc < BN / 16; ++cc) {
-          float fr[16], run[16];
-          tmem_ld16(lane_base + (uint32_t)(part * BN + cc * 16), fr);
-          if (seg > 0) {
-            tmem_ld16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), run);
+      if (!last) {
+        for (int part = 0; part < n_parts; ++part)
+          for (int cc = 0; cc < BN / 16; ++cc) {
+            float fr[16], run[16];
+            tmem_ld16(lane_base + (uint32_t)(part * BN + cc * 16), fr);
+            if (seg > 0) {
+              tmem_ld16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), run);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) fr[i] += run[i];
-          }
-          if (!last) {
+              for (int i = 0; i < 16; ++i) fr[i] += run[i];
+            }
             tmem_st16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), fr);
-          } else if (write && P < p.n_aux) {
+          }
+      } else {
+        // final fold fused with the store: per frequency, 16 columns at a time, 16-byte stores
+        const int nfl = n_parts / p.ppf;
+        for (int fl = 0; fl < nfl; ++fl) {
+          const int f = f0 + fl;
+          const bool write = (!p.active || p.active[f]) && P < p.n_aux;
+          for (int cc = 0; cc < BN / 16; ++cc) {
+            float v[CPLX ? 2 : 1][16];
+#pragma unroll
+            for (int comp = 0; comp < (CPLX ? 2 : 1); ++comp) {
+              const int part = fl * p.ppf + comp;
+              float run[16];
+              tmem_ld16(lane_base + (uint32_t)(part * BN + cc * 16), v[comp]);
+              if (seg > 0) {
+                tmem_ld16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), run);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[comp][i] += run[i];
+              }
+            }
+            if (!write) continue;
+            const int qb = Q0 + cc * 16;
+            const bool full = qb + 15 < p.n_aux && qb + 15 <= P;  // every column of the chunk is stored
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const int Q = Q0 + cc * 16 + i;
-              if (Q >= p.n_aux || Q > P) continue;
-              const float dg = (P == Q) ? p.beta : 0.0f;
-              if (CPLX) {
-                // parts 0 and 1 are Re and Im of one frequency; each writes its own component
-                float* o = reinterpret_cast<float*>(reinterpret_cast<float2*>(p.out) + f * p.mat_stride +
-                                                    (long long)P * p.ldm + Q) + (part % 2);
-                *o = p.alpha * fr[i] + ((part % 2) == 0 ? dg : 0.0f);
+              const float dg = (P == qb + i) ? p.beta : 0.0f;
+              v[0][i] = p.alpha * v[0][i] + dg;
+              if (CPLX) v[CPLX ? 1 : 0][i] = p.alpha * v[CPLX ? 1 : 0][i];
+            }
+            if (CPLX) {
+              float2* o = reinterpret_cast<float2*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + qb;
+              if (full) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 2)
+                  *reinterpret_cast<float4*>(o + i) = make_float4(v[0][i], v[CPLX ? 1 : 0][i], v[0][i + 1], v[CPLX ? 1 : 0][i + 1]);
               } else {
-                float* o = reinterpret_cast<float*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + Q;
-                *o = p.alpha * fr[i] + dg;
+                for (int i = 0; i < 16; ++i)
+                  if (qb + i < p.n_aux && qb + i <= P) o[i] = make_float2(v[0][i], v[CPLX ? 1 : 0][i]);
+              }
+            } else {
+              float* o = reinterpret_cast<float*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + qb;
+              if (full) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                  *reinterpret_cast<float4*>(o + i) = make_float4(v[0][i], v[0][i + 1], v[0][i + 2], v[0][i + 3]);
+              } else {
+                for (int i = 0; i < 16; ++i)
+                  if (qb + i < p.n_aux && qb + i <= P) o[i] = v[0][i];
               }
             }
           }
