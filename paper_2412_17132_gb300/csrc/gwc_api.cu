@@ -286,13 +286,12 @@ gwc_status load_system(gwc_ctx* ctx, const gwc_system* s, cudaStream_t st) {
 }
 
 // ---- chi0 dispatch ------------------------------------------------------------------------------
-gwc_status run_chi0(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, const int* active, void* out, double alpha,
-                    double beta, int full, cudaStream_t st) {
+gwc_status run_chi0_any(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, const int* active, void* out,
+                        double alpha, double beta, int full, long long stride, cudaStream_t st) {
   const int prec = ctx->opt.prec;
   const bool fp64 = prec == GWC_PREC_FP64;
   LAUNCH(launch_dtable(d_z, F, ctx->d_delta, ctx->n_ov, ctx->ld_dtab, !fp64, ctx->d_dtab, st));
   MatKind kind = complex_z ? cplx_kind(ctx) : real_kind(ctx);
-  const long long stride = (long long)ctx->n_aux * ctx->ldm;
   cudaEvent_t ev = ev_begin(ctx, st);
   if (prec == GWC_PREC_FP64) {
     LAUNCH(launch_chi0_simt(kind, ctx->d_o_ov, ctx->n_ov, ctx->n_aux, ctx->n_ov, ctx->d_dtab, ctx->ld_dtab, F, alpha, beta,
@@ -321,6 +320,17 @@ double factor_flop(int n, bool cplx, int F) {
   return (double)F * (cplx ? 8.0 : 2.0) * (double)n * n * n / 3.0;
 }
 
+gwc_status run_chi0(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, const int* active, void* out, double alpha,
+                    double beta, int full, cudaStream_t st) {
+  return run_chi0_any(ctx, complex_z, F, d_z, active, out, alpha, beta, full, (long long)ctx->n_aux * ctx->ldm, st);
+}
+
+// eps = 1 - Pi into matrices of `stride` elements (room for appended rows)
+gwc_status run_chi0_stride(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, const int* active, void* out,
+                           long long stride, cudaStream_t st) {
+  return run_chi0_any(ctx, complex_z, F, d_z, active, out, -1.0, 1.0, 0, stride, st);
+}
+
 // ---- imaginary-axis W table --------------------------------------------------------------------
 // Enqueues W^c_mn(i xi_k) for all states m and cores n, k = 0..n_im (node n_im is xi = 0), without
 // host synchronisation or allocation (the frequencies were uploaded at creation).
@@ -337,7 +347,7 @@ gwc_status enqueue_wim(gwc_ctx* ctx, cudaStream_t st) {
     const int nb = std::min(fb, nodes - k0);
     TRY(run_chi0(ctx, false, nb, ctx->d_zim + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st));
     cudaEvent_t ev = ev_begin(ctx, st);
-    LAUNCH(launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st));
+    LAUNCH(launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st));
     ev_end(ctx, kClsFactor, ev, st);
     ctx->stats.factor_flop += factor_flop(ctx->n_aux, false, nb);
     ctx->stats.factorizations += nb;
@@ -371,24 +381,38 @@ gwc_status compute_wim(gwc_ctx* ctx, cudaStream_t st) {
 gwc_status residue_batches_buf(gwc_ctx* ctx, int n_pairs, const double* z_dev, const int* rows_dev, int r, double* w_out,
                                const int* active, void* rhs, double* bnorm, int chunk, cudaStream_t st) {
   MatKind ck = cplx_kind(ctx);
-  const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  const bool border = r <= ctx->border_max;  // right-hand sides appended as rows of the factored matrix
+  const long long stride = (long long)(ctx->n_aux + (border ? r : 0)) * ctx->ldm;
   const long long rstride = (long long)r * ctx->ldm;
   chunk = std::max(1, std::min(chunk, ctx->batch));
   for (int p0 = 0; p0 < n_pairs; p0 += chunk) {
     const int nb = std::min(chunk, n_pairs - p0);
     const int* act = active ? active + p0 : nullptr;
-    TRY(run_chi0(ctx, true, nb, z_dev + 2 * (size_t)p0, act, ctx->d_mats, -1.0, 1.0, 0, st));
-    cudaEvent_t ev = ev_begin(ctx, st);
-    LAUNCH(launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, act, ctx->d_status, st));
-    ev_end(ctx, kClsFactor, ev, st);
+    const int* rows = rows_dev + (size_t)p0 * r;
+    double* wout = w_out + (size_t)p0 * r * 2;
+    if (border) {
+      // chi0 writes eps into rows 0..n-1 of each [n+r][ldm] matrix
+      TRY(run_chi0_stride(ctx, true, nb, z_dev + 2 * (size_t)p0, act, ctx->d_mats, stride, st));
+      LAUNCH(launch_border_rows(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, ctx->d_o_core, ctx->n_aux, rows, nb, r,
+                                ctx->d_bnorm, st));
+      cudaEvent_t ev = ev_begin(ctx, st);
+      LAUNCH(launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->n_aux + r, ctx->ldm, stride, nb, act, ctx->d_status, st));
+      ev_end(ctx, kClsFactor, ev, st);
+      LAUNCH(launch_border_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, r, ctx->d_bnorm, wout, (long long)r * 2,
+                             act, st));
+    } else {
+      TRY(run_chi0(ctx, true, nb, z_dev + 2 * (size_t)p0, act, ctx->d_mats, -1.0, 1.0, 0, st));
+      cudaEvent_t ev = ev_begin(ctx, st);
+      LAUNCH(launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->n_aux, ctx->ldm, stride, nb, act, ctx->d_status, st));
+      ev_end(ctx, kClsFactor, ev, st);
+      LAUNCH(launch_rhs_gather(ck, ctx->d_o_core, ctx->n_aux, rows, nb, r, ctx->n_aux, rhs, ctx->ldm, rstride, bnorm, st));
+      cudaEvent_t evs = ev_begin(ctx, st);
+      LAUNCH(launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, rhs, r, ctx->ldm, rstride, bnorm, nb, wout,
+                                 (long long)r * 2, act, st));
+      ev_end(ctx, kClsSolve, evs, st);
+    }
     ctx->stats.factorizations += nb;
     ctx->stats.factor_flop += factor_flop(ctx->n_aux, true, nb);
-    LAUNCH(launch_rhs_gather(ck, ctx->d_o_core, ctx->n_aux, rows_dev + (size_t)p0 * r, nb, r, ctx->n_aux, rhs, ctx->ldm,
-                             rstride, bnorm, st));
-    cudaEvent_t evs = ev_begin(ctx, st);
-    LAUNCH(launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, rhs, r, ctx->ldm, rstride, bnorm, nb,
-                               w_out + (size_t)p0 * r * 2, (long long)r * 2, act, st));
-    ev_end(ctx, kClsSolve, evs, st);
   }
   return GWC_OK;
 }
@@ -573,7 +597,8 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   // workspace
   ctx->batch = choose_batch(s, o, z);
   ctx->batch_cap = ctx->batch;
-  ctx->mats_bytes = (size_t)ctx->batch * s->n_aux * z.ldm * z.elem_c;
+  ctx->border_max = std::min(s->n_core, 64);
+  ctx->mats_bytes = (size_t)ctx->batch * (s->n_aux + ctx->border_max) * z.ldm * z.elem_c;
   {
     char* p = nullptr;
     CTRY(dalloc(ctx, &p, ctx->mats_bytes));
@@ -700,7 +725,7 @@ gwc_status gwc_screen(gwc_ctx* ctx, const double* z, int F, const double* rhs, i
     }
     res = run_chi0(ctx, true, nb, z + 2 * (size_t)f0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st);
     if (res != GWC_OK) break;
-    int n1 = launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st);
+    int n1 = launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st);
     int n2 = launch_rhs_gather(ck, rhs, ctx->n_aux, d_rows, nb, n_rhs, ctx->n_aux, d_r, ctx->ldm,
                                (long long)n_rhs * ctx->ldm, d_bn, st);
     int n3 = launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, d_r, n_rhs, ctx->ldm,

@@ -117,10 +117,17 @@ int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* 
                    double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
                    unsigned* status, cudaStream_t s);
 
-// Batched in-place LDL^T (unit lower L, diagonal D in the diagonal slot) of F matrices
-// [n][ldm] (lower triangle read and written). Zero pivot -> status |= kStatSingular.
-int launch_ldlt(MatKind kind, void* mats, int n, long long ldm, long long mat_stride, int F, const int* active,
+// Batched in-place LDL^T of F matrices [nrow][ldm]: the first n columns are factored (W = L D below
+// the diagonal, d on it, L^T above it); rows n..nrow-1 are appended right-hand sides that the row
+// solves turn into y = L^-1 b. Zero pivot -> status |= kStatSingular.
+int launch_ldlt(MatKind kind, void* mats, int n, int nrow, long long ldm, long long mat_stride, int F, const int* active,
                 unsigned* status, cudaStream_t s);
+// Appended rows: row n+q of matrix f = o_core row row_of[f*r+q]; bnorm2 = |b|^2.
+int launch_border_rows(MatKind kind, void* mats, int n, long long ldm, long long stride, const double* src,
+                       long long src_row_stride, const int* row_of, int F, int r, double* bnorm2, cudaStream_t s);
+// w[f][q] = sum_k y_k^2 / d_k - bnorm2[f][q] from the factored appended rows (FP64 accumulation).
+int launch_border_w(MatKind kind, const void* mats, int n, long long ldm, long long stride, int F, int r,
+                    const double* bnorm2, double* w, long long w_stride, const int* active, cudaStream_t s);
 
 // Right-hand sides: rhs (S type) [F][r][ldr] overwritten by y = L^{-1} b; then
 // w[f][q] = sum_k y_k^2 / d_k - bnorm2[f][q] (FP64 complex out, interleaved).
@@ -233,6 +240,7 @@ struct gwc_ctx {
   int batch = 0;            // matrices per batch
   void* d_mats = nullptr;   // batch * n_aux * ldm elements of the widest kind
   long long ldm = 0;        // leading dimension of matrices
+  int border_max = 0;       // right-hand sides that may be appended as rows (matrix rows n_aux + border_max)
   size_t mats_bytes = 0;
   void* d_dtab = nullptr;   // [batch][2][ld_dtab] FP64-sized
   int ld_dtab = 0;

@@ -58,8 +58,9 @@ struct FactorSmem {
   static constexpr size_t bytes() { return LKK_BYTES + sizeof(S) * (2 * STAGE + CS); }
 };
 
-// A[i][j] -= sum_{l in [k0, k0+klen)} W[i][l] L[j][l] for rows [r0, n), columns [c0, c1), j <= i.
-// W is read from the lower part (row i), L from the upper part (row l, column j).
+// A[i][j] -= sum_{l in [k0, k0+klen)} W[i][l] L[j][l] for rows [r0, n), columns [c0, c1), j <= i
+// (n counts every row, including appended right-hand-side rows; c1 never exceeds the factored
+// columns). W is read from the lower part (row i), L from the upper part (row l, column j).
 template <typename S>
 __device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, int c0, int c1, int k0, int klen,
                               S* __restrict__ stages) {
@@ -106,7 +107,7 @@ __device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, i
       for (int e = tid; e < TT * CPR; e += blockDim.x) {
         const int ii = e / CPR, jj = (e % CPR) * PER;
         const int gi = i0 + ii, gj = j0 + jj;
-        const bool ok = gi < n && gj < n;
+        const bool ok = gi < n && gj < c1;
         const S* src = ok ? A + (long long)gi * ldm + gj : A;
         cp_async16(Cs + ii * TT + jj, src, ok);
       }
@@ -125,7 +126,7 @@ __device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, i
     for (int e = tid; e < KC * YPR; e += blockDim.x) {
       const int l = e / YPR, jj = (e % YPR) * PER;
       const int gj = j0 + jj;
-      const bool ok = (kc + l) < k0 + klen && gj < n;
+      const bool ok = (kc + l) < k0 + klen && gj < c1;
       const S* src = ok ? A + (long long)(kc + l) * ldm + gj : A;
       cp_async16(Y + l * TT + jj, src, ok);
     }
@@ -192,7 +193,8 @@ __device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, i
 // Factor the NB-wide sub-panel starting at column c0 (its columns already hold the Schur
 // complement): diagonal block, then W (lower) and L^T (upper) for the rows below.
 template <typename S>
-__device__ void factor_subpanel(S* __restrict__ A, int n, long long ldm, int c0, S (*lkk)[NB + 1], S* dinv, int& sing) {
+__device__ void factor_subpanel(S* __restrict__ A, int n, int nrow, long long ldm, int c0, S (*lkk)[NB + 1], S* dinv,
+                                int& sing) {
   const int tid = threadIdx.x;
   const int kb = min(NB, n - c0);
   __syncthreads();
@@ -232,7 +234,7 @@ __device__ void factor_subpanel(S* __restrict__ A, int n, long long ldm, int c0,
     }
   }
   // rows below: w = a L_kk^-T (= W row), L row = w D^-1
-  for (int i = c0 + kb + tid; i < n; i += blockDim.x) {
+  for (int i = c0 + kb + tid; i < nrow; i += blockDim.x) {
     S w[NB];
     S* row = A + (long long)i * ldm + c0;
 #pragma unroll
@@ -250,14 +252,14 @@ __device__ void factor_subpanel(S* __restrict__ A, int n, long long ldm, int c0,
     for (int j = 0; j < NB; ++j)
       if (j < kb) {
         row[j] = w[j];
-        A[(long long)(c0 + j) * ldm + i] = smul(w[j], dinv[j]);
+        if (i < n) A[(long long)(c0 + j) * ldm + i] = smul(w[j], dinv[j]);
       }
   }
   __syncthreads();
 }
 
 template <typename S>
-__global__ void __launch_bounds__(256) ldlt_kernel(S* __restrict__ mats, int n, long long ldm, long long stride,
+__global__ void __launch_bounds__(256) ldlt_kernel(S* __restrict__ mats, int n, int nrow, long long ldm, long long stride,
                                                     const int* __restrict__ active, unsigned* __restrict__ status) {
   const int f = blockIdx.x;
   if (active && !active[f]) return;
@@ -272,14 +274,14 @@ __global__ void __launch_bounds__(256) ldlt_kernel(S* __restrict__ mats, int n, 
 
   for (int k0 = 0; k0 < n; k0 += PW) {
     const int kb = min(PW, n - k0);
-    factor_subpanel(A, n, ldm, k0, lkk, dinv, sing);
+    factor_subpanel(A, n, nrow, ldm, k0, lkk, dinv, sing);
     if (kb > NB) {
       // first sub-panel applied to the second: rows >= k0+NB, columns [k0+NB, k0+kb)
-      update_region(A, n, ldm, k0 + NB, k0 + NB, k0 + kb, k0, NB, stages);
-      factor_subpanel(A, n, ldm, k0 + NB, lkk, dinv, sing);
+      update_region(A, nrow, ldm, k0 + NB, k0 + NB, k0 + kb, k0, NB, stages);
+      factor_subpanel(A, n, nrow, ldm, k0 + NB, lkk, dinv, sing);
     }
-    // rank-kb trailing update of the lower triangle beyond the panel
-    if (k0 + kb < n) update_region(A, n, ldm, k0 + kb, k0 + kb, n, k0, kb, stages);
+    // rank-kb trailing update of the lower triangle beyond the panel (and of appended rows)
+    if (k0 + kb < n) update_region(A, nrow, ldm, k0 + kb, k0 + kb, n, k0, kb, stages);
   }
   __syncthreads();
   if (threadIdx.x == 0 && sing) atomicOr(status, kStatSingular);
@@ -395,14 +397,15 @@ size_t solve_smem() {
 }
 
 template <typename S>
-int run_ldlt(S* mats, int n, long long ldm, long long stride, int F, const int* active, unsigned* status, cudaStream_t s) {
+int run_ldlt(S* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active, unsigned* status,
+             cudaStream_t s) {
   static bool attr = false;
   const size_t sm = FactorSmem<S>::bytes();
   if (!attr) {
     if (cudaFuncSetAttribute(ldlt_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
     attr = true;
   }
-  ldlt_kernel<S><<<F, 256, sm, s>>>(mats, n, ldm, stride, active, status);
+  ldlt_kernel<S><<<F, 256, sm, s>>>(mats, n, nrow, ldm, stride, active, status);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
@@ -423,16 +426,121 @@ int run_solve(const S* mats, int n, long long ldm, long long stride, S* rhs, int
 
 }  // namespace
 
-int launch_ldlt(MatKind kind, void* mats, int n, long long ldm, long long stride, int F, const int* active,
+int launch_ldlt(MatKind kind, void* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active,
                 unsigned* status, cudaStream_t s) {
   // 16-byte staging needs even leading dimensions and 16-byte aligned matrices
-  if ((ldm % 4) || (stride % 4) || (reinterpret_cast<uintptr_t>(mats) & 15)) return -1;
+  if ((ldm % 4) || (stride % 4) || (reinterpret_cast<uintptr_t>(mats) & 15) || nrow < n) return -1;
   switch (kind) {
-    case MatKind::RealF32: return run_ldlt((float*)mats, n, ldm, stride, F, active, status, s);
-    case MatKind::CplxF32: return run_ldlt((float2*)mats, n, ldm, stride, F, active, status, s);
-    case MatKind::RealF64: return run_ldlt((double*)mats, n, ldm, stride, F, active, status, s);
-    default: return run_ldlt((double2*)mats, n, ldm, stride, F, active, status, s);
+    case MatKind::RealF32: return run_ldlt((float*)mats, n, nrow, ldm, stride, F, active, status, s);
+    case MatKind::CplxF32: return run_ldlt((float2*)mats, n, nrow, ldm, stride, F, active, status, s);
+    case MatKind::RealF64: return run_ldlt((double*)mats, n, nrow, ldm, stride, F, active, status, s);
+    default: return run_ldlt((double2*)mats, n, nrow, ldm, stride, F, active, status, s);
   }
+}
+
+// ---- appended right-hand-side rows ("bordered" matrix) -------------------------------------------
+// With the r vectors b_q appended as rows n..n+r-1 of the lower triangle, the factorisation's row
+// solves give W[n+q][k] = (L^-1 b_q)_k = y_k, so W^c_q = sum_k y_k^2 / d_k - |b_q|^2 follows from
+// the factored rows without a separate forward substitution.
+template <typename S>
+__global__ void border_rows_kernel(S* __restrict__ mats, int n, long long ldm, long long stride,
+                                   const double* __restrict__ src, long long src_row_stride, const int* __restrict__ row_of,
+                                   int r, double* __restrict__ bnorm2) {
+  const int f = blockIdx.y, q = blockIdx.x;
+  const double* b = src + (size_t)row_of[f * r + q] * src_row_stride;
+  S* row = mats + f * stride + (long long)(n + q) * ldm;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double v = b[k];
+    row[k] = sfrom<S>(v, 0.0);
+    acc += v * v;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    bnorm2[f * r + q] = t;
+  }
+}
+
+template <typename S>
+__global__ void border_w_kernel(const S* __restrict__ mats, int n, long long ldm, long long stride, int r,
+                                const double* __restrict__ bnorm2, double* __restrict__ w, long long w_stride,
+                                const int* __restrict__ active) {
+  const int f = blockIdx.y, q = blockIdx.x;
+  if (active && !active[f]) return;
+  const S* A = mats + f * stride;
+  const S* y = A + (long long)(n + q) * ldm;
+  double sr = 0.0, si = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const S yk = y[k];
+    const S t = smul(smul(yk, yk), sinv(A[(long long)k * ldm + k]));
+    sr += sre(t);
+    si += sim(t);
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_down_sync(0xffffffffu, sr, o);
+    si += __shfl_down_sync(0xffffffffu, si, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sr;
+    red[1][threadIdx.x >> 5] = si;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int v = 0; v < (int)(blockDim.x >> 5); ++v) {
+      a += red[0][v];
+      b += red[1][v];
+    }
+    double* o = w + f * w_stride + (long long)q * 2;
+    o[0] = a - bnorm2[(long long)f * r + q];
+    o[1] = b;
+  }
+}
+
+int launch_border_rows(MatKind kind, void* mats, int n, long long ldm, long long stride, const double* src,
+                       long long src_row_stride, const int* row_of, int F, int r, double* bnorm2, cudaStream_t s) {
+  dim3 g(r, F);
+  switch (kind) {
+    case MatKind::CplxF32:
+      border_rows_kernel<float2><<<g, 256, 0, s>>>((float2*)mats, n, ldm, stride, src, src_row_stride, row_of, r, bnorm2);
+      break;
+    case MatKind::CplxF64:
+      border_rows_kernel<double2><<<g, 256, 0, s>>>((double2*)mats, n, ldm, stride, src, src_row_stride, row_of, r, bnorm2);
+      break;
+    case MatKind::RealF32:
+      border_rows_kernel<float><<<g, 256, 0, s>>>((float*)mats, n, ldm, stride, src, src_row_stride, row_of, r, bnorm2);
+      break;
+    default:
+      border_rows_kernel<double><<<g, 256, 0, s>>>((double*)mats, n, ldm, stride, src, src_row_stride, row_of, r, bnorm2);
+      break;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_border_w(MatKind kind, const void* mats, int n, long long ldm, long long stride, int F, int r,
+                    const double* bnorm2, double* w, long long w_stride, const int* active, cudaStream_t s) {
+  dim3 g(r, F);
+  switch (kind) {
+    case MatKind::CplxF32:
+      border_w_kernel<float2><<<g, 256, 0, s>>>((const float2*)mats, n, ldm, stride, r, bnorm2, w, w_stride, active);
+      break;
+    case MatKind::CplxF64:
+      border_w_kernel<double2><<<g, 256, 0, s>>>((const double2*)mats, n, ldm, stride, r, bnorm2, w, w_stride, active);
+      break;
+    case MatKind::RealF32:
+      border_w_kernel<float><<<g, 256, 0, s>>>((const float*)mats, n, ldm, stride, r, bnorm2, w, w_stride, active);
+      break;
+    default:
+      border_w_kernel<double><<<g, 256, 0, s>>>((const double*)mats, n, ldm, stride, r, bnorm2, w, w_stride, active);
+      break;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_ldlt_solve_w(MatKind kind, const void* mats, int n, long long ldm, long long stride, void* rhs, int r,
