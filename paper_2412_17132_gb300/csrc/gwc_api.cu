@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <map>
@@ -236,14 +237,17 @@ size_t resident_bytes(const gwc_system* s, const gwc_options* o, const Sizes& z)
   return b;
 }
 
-int choose_batch(const gwc_system* s, const gwc_options* o, const Sizes& z) {
+// Matrices per residue batch. One factorisation occupies one SM, so a batch is a whole number of
+// SM-waves (a ragged last wave idles SMs for a full factorisation time).
+int choose_batch(const gwc_system* s, const gwc_options* o, const Sizes& z, int n_sm) {
   if (o->batch > 0) return o->batch;
   size_t freeb = 0, totalb = 0;
   size_t budget = (size_t)8 << 30;
   if (cudaMemGetInfo(&freeb, &totalb) == cudaSuccess) budget = std::min<size_t>((size_t)(0.35 * freeb), (size_t)24 << 30);
   size_t per = per_matrix_bytes(s, z);
   long long f = (long long)(budget / per);
-  f = std::max(1LL, std::min(512LL, f));
+  f = std::max(1LL, std::min(std::max(512LL, 4LL * n_sm), f));
+  if (f >= n_sm) f -= f % n_sm;
   return (int)f;
 }
 
@@ -316,6 +320,17 @@ gwc_status run_chi0_any(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, 
   return GWC_OK;
 }
 
+// Complex factorisations: the tensor-core kernel in the mixed-precision modes, else the SIMT one.
+int launch_factor(gwc_ctx* ctx, MatKind kind, void* mats, int n, int nrow, long long stride, int F, const int* act,
+                  cudaStream_t st) {
+  const bool mixed = ctx->opt.prec == GWC_PREC_BF16 || ctx->opt.prec == GWC_PREC_BF16X3;
+  if (kind == MatKind::CplxF32 && mixed && ctx->factor_tc) {
+    const int r = launch_ldlt_tc(mats, n, nrow, ctx->ldm, stride, F, act, ctx->d_status, st);
+    if (r != -2) return r;
+  }
+  return launch_ldlt(kind, mats, n, nrow, ctx->ldm, stride, F, act, ctx->d_status, st);
+}
+
 double factor_flop(int n, bool cplx, int F) {
   return (double)F * (cplx ? 8.0 : 2.0) * (double)n * n * n / 3.0;
 }
@@ -351,18 +366,23 @@ gwc_status enqueue_wim(gwc_ctx* ctx, cudaStream_t st) {
     ev_end(ctx, kClsFactor, ev, st);
     ctx->stats.factor_flop += factor_flop(ctx->n_aux, false, nb);
     ctx->stats.factorizations += nb;
-    for (int u = 0; u < nb; ++u) {
-      const int k = k0 + u;
-      LAUNCH(launch_rhs_gather(rk, ctx->d_o_core, ctx->n_aux, ctx->d_rowmap, 1, r, ctx->n_aux, ctx->d_rhs_im, ctx->ldm, 0,
-                               ctx->d_bnorm, st));
-      char* mat = (char*)ctx->d_mats + (size_t)u * stride * mat_elem_bytes(rk);
+    // W^c for ng nodes per solve launch (one RHS buffer per node)
+    const size_t ebytes = mat_elem_bytes(rk);
+    for (int u0 = 0; u0 < nb; u0 += ctx->wim_group) {
+      const int ng = std::min(ctx->wim_group, nb - u0);
+      for (int u = 0; u < ng; ++u)
+        LAUNCH(launch_rhs_gather(rk, ctx->d_o_core, ctx->n_aux, ctx->d_rowmap, 1, r, ctx->n_aux,
+                                 (char*)ctx->d_rhs_im + (size_t)u * plane * ctx->ldm * ebytes, ctx->ldm, 0,
+                                 ctx->d_bnorm + (size_t)u * plane, st));
+      char* mat = (char*)ctx->d_mats + (size_t)u0 * stride * ebytes;
       cudaEvent_t evs = ev_begin(ctx, st);
-      LAUNCH(launch_ldlt_solve_w(rk, mat, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs_im, r, ctx->ldm, 0, ctx->d_bnorm, 1,
-                                 ctx->d_wtmp, 0, nullptr, st));
+      LAUNCH(launch_ldlt_solve_w(rk, mat, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs_im, r, ctx->ldm,
+                                 (long long)plane * ctx->ldm, ctx->d_bnorm, ng, ctx->d_wtmp, (long long)plane * 2, nullptr,
+                                 st));
       ev_end(ctx, kClsSolve, evs, st);
-      // real part of w -> W table plane k
-      CU(cudaMemcpy2DAsync(ctx->d_wim + (size_t)k * plane, sizeof(double), ctx->d_wtmp, 2 * sizeof(double), sizeof(double),
-                           plane, cudaMemcpyDeviceToDevice, st));
+      // real parts of w -> W table planes k0+u0 .. k0+u0+ng-1
+      CU(cudaMemcpy2DAsync(ctx->d_wim + (size_t)(k0 + u0) * plane, sizeof(double), ctx->d_wtmp, 2 * sizeof(double),
+                           sizeof(double), (size_t)ng * plane, cudaMemcpyDeviceToDevice, st));
     }
   }
   return GWC_OK;
@@ -385,6 +405,7 @@ gwc_status residue_batches_buf(gwc_ctx* ctx, int n_pairs, const double* z_dev, c
   const long long stride = (long long)(ctx->n_aux + (border ? r : 0)) * ctx->ldm;
   const long long rstride = (long long)r * ctx->ldm;
   chunk = std::max(1, std::min(chunk, ctx->batch));
+  if (chunk >= ctx->n_sm) chunk -= chunk % ctx->n_sm;  // whole SM-waves; only the last batch is ragged
   for (int p0 = 0; p0 < n_pairs; p0 += chunk) {
     const int nb = std::min(chunk, n_pairs - p0);
     const int* act = active ? active + p0 : nullptr;
@@ -396,14 +417,14 @@ gwc_status residue_batches_buf(gwc_ctx* ctx, int n_pairs, const double* z_dev, c
       LAUNCH(launch_border_rows(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, ctx->d_o_core, ctx->n_aux, rows, nb, r,
                                 ctx->d_bnorm, st));
       cudaEvent_t ev = ev_begin(ctx, st);
-      LAUNCH(launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->n_aux + r, ctx->ldm, stride, nb, act, ctx->d_status, st));
+      LAUNCH(launch_factor(ctx, ck, ctx->d_mats, ctx->n_aux, ctx->n_aux + r, stride, nb, act, st));
       ev_end(ctx, kClsFactor, ev, st);
       LAUNCH(launch_border_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, nb, r, ctx->d_bnorm, wout, (long long)r * 2,
                              act, st));
     } else {
       TRY(run_chi0(ctx, true, nb, z_dev + 2 * (size_t)p0, act, ctx->d_mats, -1.0, 1.0, 0, st));
       cudaEvent_t ev = ev_begin(ctx, st);
-      LAUNCH(launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->n_aux, ctx->ldm, stride, nb, act, ctx->d_status, st));
+      LAUNCH(launch_factor(ctx, ck, ctx->d_mats, ctx->n_aux, ctx->n_aux, stride, nb, act, st));
       ev_end(ctx, kClsFactor, ev, st);
       LAUNCH(launch_rhs_gather(ck, ctx->d_o_core, ctx->n_aux, rows, nb, r, ctx->n_aux, rhs, ctx->ldm, rstride, bnorm, st));
       cudaEvent_t evs = ev_begin(ctx, st);
@@ -525,6 +546,13 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   cudaStream_t st = (cudaStream_t)stream;
   gwc_ctx* ctx = new gwc_ctx();
   cudaGetDevice(&ctx->device);
+  if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || ctx->n_sm < 1)
+    ctx->n_sm = 1;
+  {
+    // GWC_FACTOR=tc moves complex factorisations of the mixed modes to the tensor-core kernel
+    const char* fe = std::getenv("GWC_FACTOR");
+    ctx->factor_tc = fe && std::strcmp(fe, "tc") == 0;
+  }
   ctx->n_states = s->n_states;
   ctx->n_occ = s->n_occ;
   ctx->n_virt = s->n_states - s->n_occ;
@@ -595,7 +623,7 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   const size_t plane = (size_t)s->n_states * s->n_core;
   CTRY(dalloc(ctx, &ctx->d_wim, (size_t)(o->n_im + 1) * plane));
   // workspace
-  ctx->batch = choose_batch(s, o, z);
+  ctx->batch = choose_batch(s, o, z, ctx->n_sm);
   ctx->batch_cap = ctx->batch;
   ctx->border_max = std::min(s->n_core, 64);
   ctx->mats_bytes = (size_t)ctx->batch * (s->n_aux + ctx->border_max) * z.ldm * z.elem_c;
@@ -610,14 +638,19 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
     char* r = nullptr;
     CTRY(dalloc(ctx, &r, ctx->rhs_bytes));
     ctx->d_rhs = r;
+    // imaginary-axis solves: one right-hand-side buffer per node solved in the same launch (<= 1 GiB)
+    const size_t per_node = plane * z.ldm * z.elem_r;
+    ctx->wim_group = (int)std::max<size_t>(1, std::min<size_t>(((size_t)1 << 30) / per_node,
+                                                               (size_t)std::min(ctx->batch, o->n_im + 1)));
     char* ri = nullptr;
-    CTRY(dalloc(ctx, &ri, plane * z.ldm * z.elem_r));
+    CTRY(dalloc(ctx, &ri, (size_t)ctx->wim_group * per_node));
     ctx->d_rhs_im = ri;
   }
+  const size_t wim_rows = (size_t)ctx->wim_group * plane;
   CTRY(dalloc(ctx, &ctx->d_z, 2 * (size_t)ctx->batch));
   CTRY(dalloc(ctx, &ctx->d_active, ctx->batch));
-  CTRY(dalloc(ctx, &ctx->d_bnorm, std::max(plane, (size_t)ctx->batch * s->n_core)));
-  CTRY(dalloc(ctx, &ctx->d_wtmp, 2 * std::max(plane, (size_t)ctx->batch * s->n_core)));
+  CTRY(dalloc(ctx, &ctx->d_bnorm, std::max(wim_rows, (size_t)ctx->batch * s->n_core)));
+  CTRY(dalloc(ctx, &ctx->d_wtmp, 2 * std::max(wim_rows, (size_t)ctx->batch * s->n_core)));
   CTRY(dalloc(ctx, &ctx->d_rowmap, plane));
   {
     std::vector<int> ident(plane);
@@ -725,7 +758,7 @@ gwc_status gwc_screen(gwc_ctx* ctx, const double* z, int F, const double* rhs, i
     }
     res = run_chi0(ctx, true, nb, z + 2 * (size_t)f0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st);
     if (res != GWC_OK) break;
-    int n1 = launch_ldlt(ck, ctx->d_mats, ctx->n_aux, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st);
+    int n1 = launch_factor(ctx, ck, ctx->d_mats, ctx->n_aux, ctx->n_aux, stride, nb, nullptr, st);
     int n2 = launch_rhs_gather(ck, rhs, ctx->n_aux, d_rows, nb, n_rhs, ctx->n_aux, d_r, ctx->ldm,
                                (long long)n_rhs * ctx->ldm, d_bn, st);
     int n3 = launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, d_r, n_rhs, ctx->ldm,
@@ -1085,10 +1118,12 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   gwc_status res = GWC_OK;
-  // candidates 16, 32, ... and the capacity; each timed on ONE residue batch of that size (its
-  // per-build time), after one warm-up launch, so tuning costs a few batches, not whole steps
+  // candidates 16, 32, ... below one SM-wave, whole SM-waves, and the capacity; each timed on ONE
+  // residue batch of that size (its per-build time), after one warm-up launch, so tuning costs a
+  // few batches, not whole steps
   std::vector<int> cands;
-  for (int f = 16; f < ctx->batch_cap; f *= 2) cands.push_back(f);
+  for (int f = 16; f < std::min(ctx->batch_cap, ctx->n_sm); f *= 2) cands.push_back(f);
+  for (int f = ctx->n_sm; f < ctx->batch_cap; f += ctx->n_sm) cands.push_back(f);
   cands.push_back(ctx->batch_cap);
   const int np = ctx->req_n_pairs;
   for (int f : cands) {

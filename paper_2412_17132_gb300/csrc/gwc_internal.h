@@ -122,6 +122,10 @@ int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* 
 // solves turn into y = L^-1 b. Zero pivot -> status |= kStatSingular.
 int launch_ldlt(MatKind kind, void* mats, int n, int nrow, long long ldm, long long mat_stride, int F, const int* active,
                 unsigned* status, cudaStream_t s);
+// Same contract for complex FP32 matrices, trailing updates on the tensor cores (3xTF32).
+// Returns -2 if the device has no tcgen05.
+int launch_ldlt_tc(void* mats, int n, int nrow, long long ldm, long long mat_stride, int F, const int* active,
+                   unsigned* status, cudaStream_t s);
 // Appended rows: row n+q of matrix f = o_core row row_of[f*r+q]; bnorm2 = |b|^2.
 int launch_border_rows(MatKind kind, void* mats, int n, long long ldm, long long stride, const double* src,
                        long long src_row_stride, const int* row_of, int F, int r, double* bnorm2, cudaStream_t s);
@@ -240,6 +244,9 @@ struct gwc_ctx {
   int batch = 0;            // matrices per batch
   void* d_mats = nullptr;   // batch * n_aux * ldm elements of the widest kind
   long long ldm = 0;        // leading dimension of matrices
+  int n_sm = 1;             // streaming multiprocessors of the device
+  int wim_group = 1;        // imaginary-axis nodes whose solves share one launch
+  bool factor_tc = true;    // complex FP32 factorisations on the tensor cores (mixed-precision modes)
   int border_max = 0;       // right-hand sides that may be appended as rows (matrix rows n_aux + border_max)
   size_t mats_bytes = 0;
   void* d_dtab = nullptr;   // [batch][2][ld_dtab] FP64-sized
@@ -250,8 +257,8 @@ struct gwc_ctx {
   size_t rhs_bytes = 0;
   double* d_bnorm = nullptr;  // [max(batch*n_core, rhs_im)]
   int* d_rowmap = nullptr;    // [batch * n_core]
-  double* d_wtmp = nullptr;   // [batch][n_core][2]
-  void* d_rhs_im = nullptr;   // imaginary-axis RHS [n_states*n_core][n_aux] (widest real kind)
+  double* d_wtmp = nullptr;   // [max(batch*n_core, wim_group*n_states*n_core)][2]
+  void* d_rhs_im = nullptr;   // imaginary-axis RHS [wim_group][n_states*n_core][ldm] (widest real kind)
   unsigned* d_status = nullptr;
 
   // residue grid plan
