@@ -13,12 +13,15 @@
 //   strictly upper part  L^T       (A[j][i] = L_ij; scratch used by the trailing updates)
 //
 // One CTA factors one matrix, right-looking and blocked:
-//   * 64-wide panels, each factored as two 32-wide sub-panels: the 32 x 32 diagonal block in
-//     shared memory, then every row below solves against it (one thread per row) and stores
-//     W (lower) and L (upper); a narrow update applies the first sub-panel to the second.
+//   * 64-wide panels, each factored as two 32-wide halves: the two 32 x 32 diagonal blocks in
+//     shared memory, then every row below in one pass by one thread (solve against block 1,
+//     apply block 1 to its block-2 columns, solve against block 2), storing W (lower) and L
+//     (upper).
 //   * the trailing lower triangle is updated with the rank-64 product W_panel L_panel^T, in
 //     64 x 64 tiles (4 x 4 per thread); both operands are staged through shared memory by
 //     cp.async in 32-deep chunks, double-buffered across chunks and tiles.
+#include <algorithm>
+
 #include "gwc_internal.h"
 #include "ldlt_simt.cuh"
 
@@ -32,22 +35,16 @@ __global__ void __launch_bounds__(256) ldlt_kernel(S* __restrict__ mats, int n, 
   const int f = blockIdx.x;
   if (active && !active[f]) return;
   S* A = mats + f * stride;
-  using SM = FactorSmem<S>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S(*lkk)[NB + 1] = reinterpret_cast<S(*)[NB + 1]>(smem_raw);
-  S* dinv = reinterpret_cast<S*>(smem_raw + sizeof(S) * NB * (NB + 1));
-  S* stages = reinterpret_cast<S*>(smem_raw + SM::LKK_BYTES);
+  // the panel scratch and the update stages alias (the phases alternate)
+  const PanelSmem<S> ps(smem_raw);
+  S* stages = reinterpret_cast<S*>(smem_raw);
   __shared__ int sing;
   if (threadIdx.x == 0) sing = 0;
 
   for (int k0 = 0; k0 < n; k0 += PW) {
     const int kb = min(PW, n - k0);
-    factor_subpanel(A, n, nrow, ldm, k0, lkk, dinv, sing);
-    if (kb > NB) {
-      // first sub-panel applied to the second: rows >= k0+NB, columns [k0+NB, k0+kb)
-      update_region(A, nrow, ldm, k0 + NB, k0 + NB, k0 + kb, k0, NB, stages);
-      factor_subpanel(A, n, nrow, ldm, k0 + NB, lkk, dinv, sing);
-    }
+    factor_panel(A, n, nrow, ldm, k0, ps, sing);
     // rank-kb trailing update of the lower triangle beyond the panel (and of appended rows)
     if (k0 + kb < n) update_region(A, nrow, ldm, k0 + kb, k0 + kb, n, k0, kb, stages);
   }
@@ -168,7 +165,7 @@ template <typename S>
 int run_ldlt(S* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active, unsigned* status,
              cudaStream_t s) {
   static bool attr = false;
-  const size_t sm = FactorSmem<S>::bytes();
+  const size_t sm = std::max(FactorSmem<S>::bytes(), PanelSmem<S>::bytes());
   if (!attr) {
     if (cudaFuncSetAttribute(ldlt_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
     attr = true;

@@ -1,7 +1,7 @@
 // Blocked SIMT pieces of the complex-symmetric LDL^T (no pivoting), shared by the SIMT kernel
-// and the tensor-core kernel: sub-panel factorisation (32 x 32 diagonal block in shared memory,
-// then one thread per row solving against it) and the tiled rank-k update of a region of the
-// lower triangle. Both run on warps 0-7 (256 threads) and synchronise with named barrier 1.
+// and the tensor-core kernel: the 64-wide panel factorisation (two 32 x 32 diagonal blocks in
+// shared memory, then one thread per row solving against both) and the tiled rank-k update of a
+// region of the lower triangle. Both run on warps 0-7 (256 threads) and synchronise with named barrier 1.
 //
 // Storage (matrix [nrow][ldm], row-major): strictly lower W = L D, diagonal d, strictly upper
 // L^T; rows n..nrow-1 are appended right-hand sides (lower part only).
@@ -26,15 +26,21 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
                "l"(src), "r"(valid ? 16 : 0)
                : "memory");
 }
+// element-sized asynchronous copy (4, 8 or 16 bytes)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src), "n"(BYTES)
+               : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Shared-memory layout of the factor kernel (element type S):
-//   lkk [NB][NB+1], dinv [NB], then 2 stages of { X [TT][KC + PADX], Y [KC][TT] }, then the
-//   prefetched target tile C [TT][TT] of the read-modify-write
+// Shared memory of the tiled update (element type S): 2 stages of { X [TT][KC + PADX], Y [KC][TT] },
+// then the prefetched target tile C [TT][TT] of the read-modify-write
 template <typename S>
 struct FactorSmem {
   static constexpr int PADX = 16 / (int)sizeof(S);
@@ -42,8 +48,7 @@ struct FactorSmem {
   static constexpr int YS = KC * TT;
   static constexpr int STAGE = XS + YS;
   static constexpr int CS = TT * TT;
-  static constexpr size_t LKK_BYTES = ((sizeof(S) * (NB * (NB + 1) + NB)) + 15) / 16 * 16;
-  static constexpr size_t bytes() { return LKK_BYTES + sizeof(S) * (2 * STAGE + CS); }
+  static constexpr size_t bytes() { return sizeof(S) * (2 * STAGE + CS); }
 };
 
 // A[i][j] -= sum_{l in [k0, k0+klen)} W[i][l] L[j][l] for rows [r0, n), columns [c0, c1), j <= i
@@ -178,19 +183,36 @@ __device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, i
   }
 }
 
-// Factor the NB-wide sub-panel starting at column c0 (its columns already hold the Schur
-// complement): diagonal block, then W (lower) and L^T (upper) for the rows below.
+// Shared memory of the panel factorisation: the two diagonal blocks (factored in place: unit L
+// below the diagonal, d on it), their inverse pivots, W / L of the second block's rows against
+// the first block (for the Schur complement of the second block), and per-thread row scratch.
 template <typename S>
-__device__ void factor_subpanel(S* __restrict__ A, int n, int nrow, long long ldm, int c0, S (*lkk)[NB + 1], S* dinv,
-                                int& sing) {
-  const int tid = threadIdx.x;
-  const int kb = min(NB, n - c0);
-  grp_sync();
-  for (int e = tid; e < NB * NB; e += kSimtThreads) {
-    const int i = e / NB, j = e % NB;
-    lkk[i][j] = (i < kb && j <= i) ? A[(long long)(c0 + i) * ldm + (c0 + j)] : szero<S>();
+struct PanelSmem {
+  S (*lkk1)[NB + 1];
+  S (*lkk2)[NB + 1];
+  S (*w1s)[NB + 1];
+  S (*l1s)[NB + 1];
+  S* dinv1;
+  S* dinv2;
+  S* arow;  // [NB][kSimtThreads]: block-2 part of each thread's current row
+  static constexpr size_t bytes() { return sizeof(S) * (4 * NB * (NB + 1) + 2 * NB + NB * kSimtThreads); }
+  __device__ explicit PanelSmem(void* base) {
+    S* p = reinterpret_cast<S*>(base);
+    lkk1 = reinterpret_cast<S(*)[NB + 1]>(p);
+    lkk2 = reinterpret_cast<S(*)[NB + 1]>(p + NB * (NB + 1));
+    w1s = reinterpret_cast<S(*)[NB + 1]>(p + 2 * NB * (NB + 1));
+    l1s = reinterpret_cast<S(*)[NB + 1]>(p + 3 * NB * (NB + 1));
+    dinv1 = p + 4 * NB * (NB + 1);
+    dinv2 = dinv1 + NB;
+    arow = dinv2 + NB;
   }
-  grp_sync();
+};
+
+// In-place LDL^T of the kb x kb block held (lower triangle) in lkk; a zero pivot is replaced by 1
+// and flagged.
+template <typename S>
+__device__ void factor_diag(S (*lkk)[NB + 1], S* dinv, int kb, int& sing) {
+  const int tid = threadIdx.x;
   for (int j = 0; j < kb; ++j) {
     S d = lkk[j][j];
     if (sabs2(d) < 1e-60) {
@@ -211,8 +233,12 @@ __device__ void factor_subpanel(S* __restrict__ A, int n, int nrow, long long ld
     for (int i = j + 1 + tid; i < kb; i += kSimtThreads) lkk[i][j] = smul(lkk[i][j], inv);
     grp_sync();
   }
-  // diagonal block: W = L d below the diagonal, d on it, L^T above it
-  for (int e = tid; e < kb * kb; e += kSimtThreads) {
+}
+
+// diagonal block at (c0, c0): W = L d below the diagonal, d on it, L^T above it
+template <typename S>
+__device__ void store_diag(S* __restrict__ A, long long ldm, int c0, int kb, S (*lkk)[NB + 1]) {
+  for (int e = threadIdx.x; e < kb * kb; e += kSimtThreads) {
     const int i = e / kb, j = e % kb;
     if (j < i) {
       A[(long long)(c0 + i) * ldm + (c0 + j)] = smul(lkk[i][j], lkk[j][j]);
@@ -221,27 +247,123 @@ __device__ void factor_subpanel(S* __restrict__ A, int n, int nrow, long long ld
       A[(long long)(c0 + i) * ldm + (c0 + i)] = lkk[i][i];
     }
   }
-  // rows below: w = a L_kk^-T (= W row), L row = w D^-1
-  for (int i = c0 + kb + tid; i < nrow; i += kSimtThreads) {
-    S w[NB];
-    S* row = A + (long long)i * ldm + c0;
+}
+
+// w <- w L_kk^-T (unit lower L of the factored block): the W values of one row (two partial
+// sums per element to halve the dependent FMA chain)
+template <typename S>
+__device__ __forceinline__ void solve_row(S (&w)[NB], S (*lkk)[NB + 1], int kb) {
 #pragma unroll
-    for (int j = 0; j < NB; ++j) w[j] = j < kb ? row[j] : szero<S>();
+  for (int j = 0; j < NB; ++j) {
+    if (j < kb) {
+      S a0 = w[j], a1 = szero<S>();
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      if (j < kb) {
-        S acc = w[j];
+      for (int l = 0; l + 1 < j; l += 2) {
+        a0 = sfnms(w[l], lkk[j][l], a0);
+        a1 = sfnms(w[l + 1], lkk[j][l + 1], a1);
+      }
+      if (j & 1) a0 = sfnms(w[j - 1], lkk[j][j - 1], a0);
+      w[j] = sadd(a0, a1);
+    }
+  }
+}
+
+// Factor the panel [k0, k0 + min(PW, n - k0)) (its columns already hold the Schur complement) as
+// two NB-wide halves: the diagonal blocks in shared memory, then every row below in one pass by one
+// thread: solve against block 1, apply block 1 to its block-2 columns, solve against block 2, and
+// store W (lower) and L^T (upper). Rows >= n are appended right-hand sides (W only).
+template <typename S>
+__device__ void factor_panel(S* __restrict__ A, int n, int nrow, long long ldm, int k0, const PanelSmem<S>& ps,
+                             int& sing) {
+  const int tid = threadIdx.x;
+  const int kb = min(PW, n - k0);
+  const int kb1 = min(NB, kb), kb2 = kb - kb1;
+  const int c2 = k0 + NB;
+  grp_sync();
+  for (int e = tid; e < NB * NB; e += kSimtThreads) {
+    const int i = e / NB, j = e % NB;
+    ps.lkk1[i][j] = (i < kb1 && j <= i) ? A[(long long)(k0 + i) * ldm + (k0 + j)] : szero<S>();
+  }
+  grp_sync();
+  factor_diag(ps.lkk1, ps.dinv1, kb1, sing);
+  store_diag(A, ldm, k0, kb1, ps.lkk1);
+  if (kb2 > 0) {
+    // rows of block 2 against block 1
+    for (int r = tid; r < kb2; r += kSimtThreads) {
+      const int i = c2 + r;
+      S* row = A + (long long)i * ldm + k0;
+      S w[NB];
 #pragma unroll
-        for (int l = 0; l < j; ++l) acc = sfnms(w[l], lkk[j][l], acc);
-        w[j] = acc;
+      for (int j = 0; j < NB; ++j) w[j] = j < kb1 ? row[j] : szero<S>();
+      solve_row(w, ps.lkk1, kb1);
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const S l = smul(w[j], ps.dinv1[j]);
+        row[j] = w[j];
+        A[(long long)(k0 + j) * ldm + i] = l;
+        ps.w1s[r][j] = w[j];
+        ps.l1s[r][j] = l;
       }
     }
+    grp_sync();
+    // Schur complement of block 2
+    for (int e = tid; e < NB * NB; e += kSimtThreads) {
+      const int r = e / NB, c = e % NB;
+      S v = szero<S>();
+      if (r < kb2 && c <= r) {
+        v = A[(long long)(c2 + r) * ldm + (c2 + c)];
+#pragma unroll 8
+        for (int j = 0; j < NB; ++j) v = sfnms(ps.w1s[r][j], ps.l1s[c][j], v);
+      }
+      ps.lkk2[r][c] = v;
+    }
+    grp_sync();
+    factor_diag(ps.lkk2, ps.dinv2, kb2, sing);
+    store_diag(A, ldm, c2, kb2, ps.lkk2);
+  }
+  // every row below the panel
+  for (int i = k0 + kb + tid; i < nrow; i += kSimtThreads) {
+    S* row = A + (long long)i * ldm + k0;
+    // block-2 values of the row into this thread's scratch, in flight while block 1 is solved
+    S* as = ps.arow + tid;
+    for (int c = 0; c < kb2; ++c) cp_async_elem<(int)sizeof(S)>(as + c * kSimtThreads, row + NB + c);
+    cp_commit();
+    S w[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) w[j] = j < kb1 ? row[j] : szero<S>();
+    solve_row(w, ps.lkk1, kb1);
 #pragma unroll
     for (int j = 0; j < NB; ++j)
-      if (j < kb) {
+      if (j < kb1) {
         row[j] = w[j];
-        if (i < n) A[(long long)(c0 + j) * ldm + i] = smul(w[j], dinv[j]);
+        if (i < n) A[(long long)(k0 + j) * ldm + i] = smul(w[j], ps.dinv1[j]);
       }
+    if (kb2 > 0) {
+      // block-2 columns: a = (row - L1 w) L_22^-T, one column at a time; a is kept per thread in
+      // shared memory (column-major over the threads: conflict-free) so w stays in registers
+      cp_wait<0>();
+#pragma unroll 1
+      for (int c = 0; c < kb2; ++c) {
+        S v0 = as[c * kSimtThreads], v1 = szero<S>(), v2 = szero<S>(), v3 = szero<S>();
+#pragma unroll
+        for (int j = 0; j < NB; j += 4) {
+          v0 = sfnms(w[j], ps.l1s[c][j], v0);
+          v1 = sfnms(w[j + 1], ps.l1s[c][j + 1], v1);
+          v2 = sfnms(w[j + 2], ps.l1s[c][j + 2], v2);
+          v3 = sfnms(w[j + 3], ps.l1s[c][j + 3], v3);
+        }
+        int l = 0;
+        for (; l + 1 < c; l += 2) {
+          v0 = sfnms(as[l * kSimtThreads], ps.lkk2[c][l], v0);
+          v1 = sfnms(as[(l + 1) * kSimtThreads], ps.lkk2[c][l + 1], v1);
+        }
+        if (l < c) v2 = sfnms(as[l * kSimtThreads], ps.lkk2[c][l], v2);
+        const S v = sadd(sadd(v0, v1), sadd(v2, v3));
+        as[c * kSimtThreads] = v;
+        row[NB + c] = v;
+        if (i < n) A[(long long)(c2 + c) * ldm + i] = smul(v, ps.dinv2[c]);
+      }
+    }
   }
   grp_sync();
 }

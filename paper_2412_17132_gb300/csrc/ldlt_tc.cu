@@ -7,11 +7,10 @@
 //   C[i][j] -= sum_l W[i][l] L[j][l],   l in the panel, i >= j beyond the panel.
 //
 // Complex products as real GEMMs over split planes. With A = W rows (Ar, Ai) and B = L rows
-// (Lr, Li), one accumulator of N = 128 columns holds Re (columns 0-63) and Im (64-127) of a
-// 128 x 64 complex tile:
-//     D += Ar [Lr ; Li]^T + Ai [-Li ; Lr]^T,
-// so each shared-memory stage keeps the planes -Li, Lr, Li back to back and the two B operands
-// are the 128-row windows starting at Lr and at -Li.
+// (Lr, Li), one accumulator of 128 columns holds Re (columns 0-63) and Im (64-127) of a
+// 128 x 64 complex tile, each half an N = 64 product:
+//     Re += Ar Lr^T - Ai Li^T   (the minus from the instruction's negate-A bit),
+//     Im += Ar Li^T + Ai Lr^T.
 //
 // FP32 accuracy from TF32 operands (kind::tf32): every value v is split into hi = tf32(v) and
 // lo = tf32(v - hi) (3xTF32; Henry, Tang & Heinecke 2019 for the BF16 analogue), and the tile is
@@ -20,12 +19,17 @@
 // epilogue forms C - D1 - D2 in round-to-nearest FP32.
 //
 // Roles (288 threads, one CTA per matrix):
-//   warps 0-7   panel factorisation (the shared SIMT routines, named barrier 1)
-//   warps 4-7   operand transform: W rows and L^T rows from global memory (L2) -> hi/lo planes
-//               in the 128-byte-swizzled K-major layout, one 32-column half of the panel per stage
+//   warps 0-7   panel factorisation (the shared SIMT routine, named barrier 1)
+//   warps 4-7   operand transform: global memory (L2) -> hi/lo planes in the 128-byte-swizzled
+//               K-major layout. The A operand (W rows of a 128-row tile, all 64 panel columns)
+//               stays resident while the tile row's column tiles pass; the B operand (L rows of a
+//               64-column tile) streams through two stages of 32 panel columns, its global loads
+//               issued one stage ahead.
 //   warp 8      TMEM allocation (512 columns: two tiles in flight x {D1, D2}) and the MMA issuer
-//   warps 0-3   epilogue: TMEM -> registers, read-modify-write of the target tile in global memory
-// The panel scratch of the SIMT routines aliases the two operand stages (the phases alternate).
+//   warps 0-3   epilogue: the target tile passes through shared memory in 32-row x 16-column chunks
+//               per warp (coalesced asynchronous loads one chunk ahead, coalesced stores), each
+//               thread subtracting its row's TMEM accumulators in between
+// The panel scratch of the SIMT routine aliases the operand buffers (the phases alternate).
 // Every mbarrier wait is bounded (one second); on expiry the CTA records kStatTimeout, stops,
 // drains the MMAs it issued and frees TMEM.
 #include "gwc_internal.h"
@@ -37,28 +41,35 @@ namespace gwc {
 namespace {
 
 constexpr int TM = 128;                                  // rows per trailing tile (MMA M)
-constexpr int TN = 64;                                   // complex columns per tile (MMA N = 2 TN)
+constexpr int TN = 64;                                   // complex columns per tile (MMA N per part)
 constexpr int KH = 32;                                   // panel columns per stage (128-byte plane rows)
-constexpr int A_PLANE = TM * 128;                        // 16 KB: Ar, Ai, Ar_lo, Ai_lo
-constexpr int B_PLANE = TN * 128;                        // 8 KB: -Li, Lr, Li, -Li_lo, Lr_lo, Li_lo
-constexpr int STAGE_BYTES = 4 * A_PLANE + 6 * B_PLANE;   // 112 KB
+constexpr int A_PLANE = TM * 128;                        // 16 KB: [half][Ar, Ai, Ar_lo, Ai_lo]
+constexpr int A_BYTES = 8 * A_PLANE;                     // 128 KB: the resident A operand
+constexpr int B_PLANE = TN * 128;                        // 8 KB: Lr, Li, Lr_lo, Li_lo
+constexpr int B_STAGE = 4 * B_PLANE;                     // 32 KB
 constexpr int NSTAGE = 2;
+constexpr int EP_BUF = 32 * 128;                         // 4 KB: 32 rows x 16 complex columns
+constexpr int EP_BYTES = 4 * 2 * EP_BUF;                 // two chunk buffers per epilogue warp
 constexpr int NT_TC = 288;
 constexpr int META_BYTES = 128;
-constexpr int SMEM_TC = 1024 + NSTAGE * STAGE_BYTES + META_BYTES;
+constexpr int OPS_BYTES = A_BYTES + NSTAGE * B_STAGE + EP_BYTES;  // 224 KB
+constexpr int SMEM_TC = 1024 + OPS_BYTES + META_BYTES;
 static_assert(PW == 2 * KH, "one panel is two stages");
-static_assert(FactorSmem<float2>::bytes() <= (size_t)NSTAGE * STAGE_BYTES, "panel scratch fits in the stages");
+static_assert(PanelSmem<float2>::bytes() <= (size_t)OPS_BYTES, "panel scratch fits in the operand buffers");
 
-// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, N = 2 TN, M = TM.
+// kind::tf32 instruction descriptors: D = F32, A = B = TF32, both K-major, N = TN, M = TM;
+// the second negates A (bit 13).
 constexpr uint32_t kIdescTf32 =
-    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t kIdescTf32NegA = kIdescTf32 | (1u << 13);
 
+template <uint32_t IDESC>
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdescTf32), "r"(accum));
+      "l"(a), "l"(b), "n"(IDESC), "r"(accum));
 }
 
 // round to the nearest TF32 value (10 explicit mantissa bits), kept in an FP32 container
@@ -86,99 +97,145 @@ __device__ __forceinline__ int tile_cols(int R0, int n, int tI) {
 }
 
 struct TcSmem {
-  uint8_t* base;
-  uint64_t *full, *empty, *tfull, *tempty, *mma_done;
+  uint8_t* base;  // A operand, then the B stages
+  uint8_t* ep;    // epilogue staging
+  uint64_t *a_full, *a_empty, *b_full, *b_empty, *tfull, *tempty, *mma_done;
   uint32_t* tmem_slot;
   volatile int* abort_flag;
   int* sing;
 };
 
-// ---- operand transform (warps 4-7): one stage = one 32-column half of the panel for one tile ----
-// (A is written by this kernel: plain coherent loads, no read-only path)
-__device__ void transform_role(const TcSmem& sm, const float2* A, int n, int nrow, long long ldm, int k0,
-                               int R0, int n_ti, int seq) {
-  const int tt = threadIdx.x - 128;  // 0..127
-  bool ok = true;
-  for (int tI = 0; tI < n_ti && ok; ++tI) {
-    const int i0 = R0 + TM * tI;
-    const int nc = tile_cols(R0, n, tI);
-    for (int tJ = 0; tJ < nc && ok; ++tJ) {
-      const int j0 = R0 + TN * tJ;
-      for (int h = 0; h < 2; ++h, ++seq) {
-        const int s = seq & 1, us = seq >> 1;
-        if (!mbar_wait(smem_u32(&sm.empty[s]), (us & 1) ^ 1, sm.abort_flag)) {
-          ok = false;
-          break;
-        }
-        uint8_t* st = sm.base + s * STAGE_BYTES;
-        // A planes: row tt of the tile = W[i0 + tt][k0 + KH h .. + KH)
-        {
-          const int r = tt, i = i0 + r, sw = r & 7;
-          uint8_t* rowp = st + r * 128;
-          if (i < nrow) {
-            const float4* src = reinterpret_cast<const float4*>(A + (long long)i * ldm + k0 + KH * h);
-#pragma unroll 2
-            for (int c = 0; c < 8; ++c) {  // chunk c: complex l = 4c .. 4c+3
-              const float4 v0 = src[2 * c], v1 = src[2 * c + 1];
-              const float re[4] = {v0.x, v0.z, v1.x, v1.z};
-              const float im[4] = {v0.y, v0.w, v1.y, v1.w};
-              float4 rh, rl, ih, il;
-              split4(re, rh, rl);
-              split4(im, ih, il);
-              const int off = (c ^ sw) << 4;
-              *reinterpret_cast<float4*>(rowp + off) = rh;
-              *reinterpret_cast<float4*>(rowp + A_PLANE + off) = ih;
-              *reinterpret_cast<float4*>(rowp + 2 * A_PLANE + off) = rl;
-              *reinterpret_cast<float4*>(rowp + 3 * A_PLANE + off) = il;
-            }
-          } else {
-            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-#pragma unroll
-              for (int pl = 0; pl < 4; ++pl) *reinterpret_cast<float4*>(rowp + pl * A_PLANE + (c << 4)) = z;
-          }
-        }
-        // B planes: row jj of the tile = L[j0 + jj][l] = L^T[l][j0 + jj], 16 of the 32 columns l
-        {
-          const int jj = tt & 63, lh = tt >> 6, j = j0 + jj, sw = jj & 7;
-          uint8_t* rowp = st + 4 * A_PLANE + jj * 128;
-          const bool jv = j < n;
-          const float2* colp = A + (long long)(k0 + KH * h + 16 * lh) * ldm + j;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float lr[4], li[4], nli[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float2 v = jv ? colp[(long long)(4 * c + e) * ldm] : make_float2(0.f, 0.f);
-              lr[e] = v.x;
-              li[e] = v.y;
-              nli[e] = -v.y;
-            }
-            float4 rh, rl, ih, il, nh, nl;
-            split4(lr, rh, rl);
-            split4(li, ih, il);
-            split4(nli, nh, nl);
-            const int off = ((4 * lh + c) ^ sw) << 4;
-            *reinterpret_cast<float4*>(rowp + off) = nh;
-            *reinterpret_cast<float4*>(rowp + B_PLANE + off) = rh;
-            *reinterpret_cast<float4*>(rowp + 2 * B_PLANE + off) = ih;
-            *reinterpret_cast<float4*>(rowp + 3 * B_PLANE + off) = nl;
-            *reinterpret_cast<float4*>(rowp + 4 * B_PLANE + off) = rl;
-            *reinterpret_cast<float4*>(rowp + 5 * B_PLANE + off) = il;
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(smem_u32(&sm.full[s]));
+// Iterates the (row tile, column tile, half) stages of one panel in issue order.
+struct StageIt {
+  int R0, n, n_ti;
+  int tI, tJ, h, nc;
+  __device__ void init(int R0_, int n_, int n_ti_) {
+    R0 = R0_;
+    n = n_;
+    n_ti = n_ti_;
+    tI = 0;
+    tJ = 0;
+    h = 0;
+    nc = tile_cols(R0, n, 0);
+  }
+  __device__ bool valid() const { return tI < n_ti; }
+  __device__ void next() {
+    if (++h == 2) {
+      h = 0;
+      if (++tJ == nc) {
+        tJ = 0;
+        ++tI;
+        nc = tI < n_ti ? tile_cols(R0, n, tI) : 0;
       }
+    }
+  }
+};
+
+// B operand values of one stage for this thread: L^T[k0 + KH h + 16 lh + e][j0 + jj], e < 16
+__device__ __forceinline__ void load_b(float2 (&bv)[16], const float2* A, int n, long long ldm, int k0,
+                                       const StageIt& it, int tt) {
+  const int jj = tt & 63, lh = tt >> 6, j = it.R0 + TN * it.tJ + jj;
+  const bool jv = j < n;
+  const float2* colp = A + (long long)(k0 + KH * it.h + 16 * lh) * ldm + (jv ? j : 0);
+#pragma unroll
+  for (int e = 0; e < 16; ++e) bv[e] = jv ? colp[(long long)e * ldm] : make_float2(0.f, 0.f);
+}
+
+// ---- operand transform (warps 4-7) --------------------------------------------------------------
+// (A is written by this kernel: plain coherent loads, no read-only path)
+__device__ void transform_role(const TcSmem& sm, const float2* A, int n, int nrow, long long ldm, int k0, int R0,
+                               int n_ti, int seq, int rt) {
+  const int tt = threadIdx.x - 128;  // 0..127
+  StageIt it;
+  it.init(R0, n, n_ti);
+  float2 bv[16];
+  load_b(bv, A, n, ldm, k0, it, tt);
+  bool ok = true;
+  for (int tI = 0; tI < n_ti && ok; ++tI, ++rt) {
+    // A operand of row tile tI: W[i0 + row][k0 .. k0 + 64), four threads per row (64 bytes each)
+    if (!mbar_wait(smem_u32(sm.a_empty), (rt & 1) ^ 1, sm.abort_flag)) break;
+    {
+      const int rq = tt & 3, rr = tt >> 2;
+      const int i0 = R0 + TM * tI;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        float4 av[16];
+#pragma unroll
+        for (int ps = 0; ps < 4; ++ps) {
+          const int i = i0 + rr + 32 * ps;
+          const float4* src =
+              reinterpret_cast<const float4*>(A + (long long)(i < nrow ? i : 0) * ldm + k0 + KH * h + 8 * rq);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) av[4 * ps + c] = i < nrow ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int ps = 0; ps < 4; ++ps) {
+          const int r = rr + 32 * ps, sw = r & 7;
+          uint8_t* rowp = sm.base + h * 4 * A_PLANE + r * 128;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {  // chunk 2 rq + e: complex l = 8 rq + 4 e .. + 3
+            const float4 v0 = av[4 * ps + 2 * e], v1 = av[4 * ps + 2 * e + 1];
+            const float re[4] = {v0.x, v0.z, v1.x, v1.z};
+            const float im[4] = {v0.y, v0.w, v1.y, v1.w};
+            float4 rh, rl, ih, il;
+            split4(re, rh, rl);
+            split4(im, ih, il);
+            const int off = ((2 * rq + e) ^ sw) << 4;
+            *reinterpret_cast<float4*>(rowp + off) = rh;
+            *reinterpret_cast<float4*>(rowp + A_PLANE + off) = ih;
+            *reinterpret_cast<float4*>(rowp + 2 * A_PLANE + off) = rl;
+            *reinterpret_cast<float4*>(rowp + 3 * A_PLANE + off) = il;
+          }
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive(smem_u32(sm.a_full));
+    // B operand stages of this row tile
+    const int nc = tile_cols(R0, n, tI);
+    for (int q = 0; q < 2 * nc; ++q, ++seq) {
+      float2 cur[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) cur[e] = bv[e];
+      it.next();
+      if (it.valid()) load_b(bv, A, n, ldm, k0, it, tt);  // next stage's loads in flight meanwhile
+      const int s = seq & 1, us = seq >> 1;
+      if (!mbar_wait(smem_u32(&sm.b_empty[s]), (us & 1) ^ 1, sm.abort_flag)) {
+        ok = false;
+        break;
+      }
+      const int jj = tt & 63, lh = tt >> 6, sw = jj & 7;
+      uint8_t* rowp = sm.base + A_BYTES + s * B_STAGE + jj * 128;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float lr[4], li[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          lr[e] = cur[4 * c + e].x;
+          li[e] = cur[4 * c + e].y;
+        }
+        float4 rh, rl, ih, il;
+        split4(lr, rh, rl);
+        split4(li, ih, il);
+        const int off = ((4 * lh + c) ^ sw) << 4;
+        *reinterpret_cast<float4*>(rowp + off) = rh;
+        *reinterpret_cast<float4*>(rowp + B_PLANE + off) = ih;
+        *reinterpret_cast<float4*>(rowp + 2 * B_PLANE + off) = rl;
+        *reinterpret_cast<float4*>(rowp + 3 * B_PLANE + off) = il;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&sm.b_full[s]));
     }
   }
 }
 
 // ---- MMA issuer (one thread of warp 8) ----------------------------------------------------------
-__device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, int n_ti, int seq, int tcount) {
+__device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, int n_ti, int seq, int tcount, int rt) {
   bool ok = true;
-  for (int tI = 0; tI < n_ti && ok; ++tI) {
+  const uint32_t abase = smem_u32(sm.base);
+  for (int tI = 0; tI < n_ti && ok; ++tI, ++rt) {
+    if (!mbar_wait(smem_u32(sm.a_full), rt & 1, sm.abort_flag)) break;
+    tc_fence_after();
     const int nc = tile_cols(R0, n, tI);
     for (int tJ = 0; tJ < nc && ok; ++tJ, ++tcount) {
       const int b = tcount & 1, ub = tcount >> 1;
@@ -188,92 +245,184 @@ __device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, in
       }
       tc_fence_after();
       const uint32_t d1 = tmem_base + (uint32_t)(b * 256), d2 = d1 + 128;
+      const uint32_t d1r = d1, d1i = d1 + TN, d2r = d2, d2i = d2 + TN;  // Re | Im column halves
       for (int h = 0; h < 2; ++h, ++seq) {
         const int s = seq & 1, us = seq >> 1;
-        if (!mbar_wait(smem_u32(&sm.full[s]), us & 1, sm.abort_flag)) {
+        if (!mbar_wait(smem_u32(&sm.b_full[s]), us & 1, sm.abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t st = smem_u32(sm.base + s * STAGE_BYTES);
-        const uint32_t ar = st, ai = st + A_PLANE, arl = st + 2 * A_PLANE, ail = st + 3 * A_PLANE;
-        const uint32_t bb = st + 4 * A_PLANE;
-        const uint32_t b2 = bb, b1 = bb + B_PLANE;                  // [-Li ; Lr], [Lr ; Li]
-        const uint32_t b2l = bb + 3 * B_PLANE, b1l = bb + 4 * B_PLANE;
+        const uint32_t ah = abase + h * 4 * A_PLANE;
+        const uint32_t ar = ah, ai = ah + A_PLANE, arl = ah + 2 * A_PLANE, ail = ah + 3 * A_PLANE;
+        const uint32_t bb = abase + A_BYTES + s * B_STAGE;
+        const uint32_t br = bb, bi = bb + B_PLANE, brl = bb + 2 * B_PLANE, bil = bb + 3 * B_PLANE;
 #pragma unroll
         for (int k = 0; k < KH / 8; ++k) {
           const uint32_t off = k * 32;  // 8 TF32 values = 32 bytes along K inside the 128-B row
           const uint32_t acc = (h == 0 && k == 0) ? 0u : 1u;
-          mma_tf32(d1, sdesc(ar + off), sdesc(b1 + off), acc);
-          mma_tf32(d1, sdesc(ai + off), sdesc(b2 + off), 1u);
-          mma_tf32(d2, sdesc(ar + off), sdesc(b1l + off), acc);
-          mma_tf32(d2, sdesc(arl + off), sdesc(b1 + off), 1u);
-          mma_tf32(d2, sdesc(ai + off), sdesc(b2l + off), 1u);
-          mma_tf32(d2, sdesc(ail + off), sdesc(b2 + off), 1u);
+          const uint64_t a_r = sdesc(ar + off), a_i = sdesc(ai + off), a_rl = sdesc(arl + off), a_il = sdesc(ail + off);
+          const uint64_t b_r = sdesc(br + off), b_i = sdesc(bi + off), b_rl = sdesc(brl + off), b_il = sdesc(bil + off);
+          // hi * hi
+          mma_tf32<kIdescTf32>(d1r, a_r, b_r, acc);
+          mma_tf32<kIdescTf32NegA>(d1r, a_i, b_i, 1u);
+          mma_tf32<kIdescTf32>(d1i, a_r, b_i, acc);
+          mma_tf32<kIdescTf32>(d1i, a_i, b_r, 1u);
+          // hi * lo + lo * hi
+          mma_tf32<kIdescTf32>(d2r, a_r, b_rl, acc);
+          mma_tf32<kIdescTf32>(d2r, a_rl, b_r, 1u);
+          mma_tf32<kIdescTf32NegA>(d2r, a_i, b_il, 1u);
+          mma_tf32<kIdescTf32NegA>(d2r, a_il, b_i, 1u);
+          mma_tf32<kIdescTf32>(d2i, a_r, b_il, acc);
+          mma_tf32<kIdescTf32>(d2i, a_rl, b_i, 1u);
+          mma_tf32<kIdescTf32>(d2i, a_i, b_rl, 1u);
+          mma_tf32<kIdescTf32>(d2i, a_il, b_r, 1u);
         }
-        mma_commit(smem_u32(&sm.empty[s]));
+        mma_commit(smem_u32(&sm.b_empty[s]));
       }
       if (!ok) break;
       mma_commit(smem_u32(&sm.tfull[b]));
     }
+    if (!ok) break;
+    mma_commit(smem_u32(sm.a_empty));  // the row tile's A operand is free once its MMAs complete
   }
 }
 
-// ---- epilogue (warps 0-3): C -= D1 + D2 for rows i0 + 32 q + lane --------------------------------
+// ---- epilogue (warps 0-3): C -= D1 + D2 ---------------------------------------------------------
+// TMEM loads without the implicit wait, so the four accumulator slices of a chunk share one wait
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// first row of this warp's 32-row slice and first column of one 16-column chunk, in issue order
+struct ChunkIt {
+  int R0, n, n_ti, q;
+  int tI, tJ, cc, nc;
+  __device__ void init(int R0_, int n_, int n_ti_, int q_) {
+    R0 = R0_;
+    n = n_;
+    n_ti = n_ti_;
+    q = q_;
+    tI = 0;
+    tJ = 0;
+    cc = 0;
+    nc = tile_cols(R0, n, 0);
+  }
+  __device__ bool valid() const { return tI < n_ti; }
+  __device__ int row0() const { return R0 + TM * tI + 32 * q; }
+  __device__ int jb() const { return R0 + TN * tJ + 16 * cc; }
+  __device__ void next() {
+    if (++cc == TN / 16) {
+      cc = 0;
+      if (++tJ == nc) {
+        tJ = 0;
+        ++tI;
+        nc = tI < n_ti ? tile_cols(R0, n, tI) : 0;
+      }
+    }
+  }
+};
+
+// columns j < jlim of row i are updated: j <= i inside the factored block, every j < n below it
+__device__ __forceinline__ int row_jlim(int i, int n, int nrow) { return i < nrow ? (i < n ? min(n, i + 1) : n) : 0; }
+
+// chunk (32 rows x 16 complex columns) of the target into a warp's staging buffer: 8 pieces of
+// 16 bytes per lane, four full rows per instruction; 16-byte pieces start at even columns and ldm
+// is a multiple of 4, so a piece never crosses the end of its row
+__device__ __forceinline__ void ep_load(uint8_t* buf, const float2* A, int n, int nrow, long long ldm, int row0, int jb,
+                                        int lane) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int pc = lane + 32 * k, rr = pc >> 3, ch = pc & 7;
+    const int i = row0 + rr, col = jb + 2 * ch;
+    const bool v = col < row_jlim(i, n, nrow);
+    cp_async16(buf + rr * 128 + ((ch ^ (rr & 7)) << 4), v ? A + (long long)i * ldm + col : A, v);
+  }
+  cp_commit();
+}
+
+__device__ __forceinline__ void ep_store(const uint8_t* buf, float2* A, int n, int nrow, long long ldm, int row0, int jb,
+                                         int lane) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int pc = lane + 32 * k, rr = pc >> 3, ch = pc & 7;
+    const int i = row0 + rr, col = jb + 2 * ch;
+    const int jl = row_jlim(i, n, nrow);
+    if (col >= jl) continue;
+    const float4 v = *reinterpret_cast<const float4*>(buf + rr * 128 + ((ch ^ (rr & 7)) << 4));
+    float2* dst = A + (long long)i * ldm + col;
+    if (col + 1 < jl)
+      *reinterpret_cast<float4*>(dst) = v;
+    else
+      *dst = make_float2(v.x, v.y);
+  }
+}
+
 __device__ void epilogue_role(const TcSmem& sm, uint32_t tmem_base, float2* __restrict__ A, int n, int nrow,
                               long long ldm, int R0, int n_ti, int tcount) {
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
+  uint8_t* bufs = sm.ep + q * 2 * EP_BUF;
+  ChunkIt ld, cur;
+  ld.init(R0, n, n_ti, q);
+  cur = ld;
+  ep_load(bufs, A, n, nrow, ldm, ld.row0(), ld.jb(), lane);
+  ld.next();
+  int g = 0;  // chunk index within the panel (buffer parity)
   bool ok = true;
   for (int tI = 0; tI < n_ti && ok; ++tI) {
-    const int i0 = R0 + TM * tI;
     const int nc = tile_cols(R0, n, tI);
-    const int i = i0 + 32 * q + lane;
-    // columns j < jlim of row i are updated: j <= i inside the factored block, all j < n below it
-    const int jlim = i < nrow ? (i < n ? min(n, i + 1) : n) : 0;
     for (int tJ = 0; tJ < nc; ++tJ, ++tcount) {
-      const int j0 = R0 + TN * tJ;
       const int b = tcount & 1, ub = tcount >> 1;
       ok = mbar_wait(smem_u32(&sm.tfull[b]), ub & 1, sm.abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
 #pragma unroll 1
-      for (int cc = 0; cc < TN / 16; ++cc) {
-        float d1r[16], d1i[16], d2r[16], d2i[16];
-        const uint32_t col = lane_base + (uint32_t)(b * 256 + 16 * cc);
-        tmem_ld16(col, d1r);
-        tmem_ld16(col + 64, d1i);
-        tmem_ld16(col + 128, d2r);
-        tmem_ld16(col + 192, d2i);
-        const int jb = j0 + 16 * cc;
-        if (jb >= jlim) continue;
-        float2* p = A + (long long)i * ldm + jb;
-        if (jb + 16 <= jlim) {
-#pragma unroll
-          for (int e = 0; e < 16; e += 2) {
-            float4 c = *reinterpret_cast<const float4*>(p + e);
-            c.x = c.x - d1r[e] - d2r[e];
-            c.y = c.y - d1i[e] - d2i[e];
-            c.z = c.z - d1r[e + 1] - d2r[e + 1];
-            c.w = c.w - d1i[e + 1] - d2i[e + 1];
-            *reinterpret_cast<float4*>(p + e) = c;
-          }
+      for (int cc = 0; cc < TN / 16; ++cc, ++g) {
+        uint8_t* buf = bufs + (g & 1) * EP_BUF;
+        // next chunk's loads into the other buffer (its stores finished a chunk ago)
+        if (ld.valid()) {
+          ep_load(bufs + ((g + 1) & 1) * EP_BUF, A, n, nrow, ldm, ld.row0(), ld.jb(), lane);
+          ld.next();
+          cp_wait<1>();
         } else {
-#pragma unroll
-          for (int e = 0; e < 16; ++e)
-            if (jb + e < jlim) {
-              float2 c = p[e];
-              c.x = c.x - d1r[e] - d2r[e];
-              c.y = c.y - d1i[e] - d2i[e];
-              p[e] = c;
-            }
+          cp_wait<0>();
         }
+        uint32_t d1r[16], d1i[16], d2r[16], d2i[16];
+        const uint32_t col = lane_base + (uint32_t)(b * 256 + 16 * cc);
+        tmem_ld16_nw(col, d1r);
+        tmem_ld16_nw(col + 64, d1i);
+        tmem_ld16_nw(col + 128, d2r);
+        tmem_ld16_nw(col + 192, d2i);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        __syncwarp();  // every lane's copies of this chunk have landed
+        // this lane's row: C - D1 - D2 for 16 complex columns
+        uint8_t* rowp = buf + lane * 128;
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) {
+          float4* pv = reinterpret_cast<float4*>(rowp + ((ch ^ (lane & 7)) << 4));
+          float4 c = *pv;
+          c.x = c.x - __uint_as_float(d1r[2 * ch]) - __uint_as_float(d2r[2 * ch]);
+          c.y = c.y - __uint_as_float(d1i[2 * ch]) - __uint_as_float(d2i[2 * ch]);
+          c.z = c.z - __uint_as_float(d1r[2 * ch + 1]) - __uint_as_float(d2r[2 * ch + 1]);
+          c.w = c.w - __uint_as_float(d1i[2 * ch + 1]) - __uint_as_float(d2i[2 * ch + 1]);
+          *pv = c;
+        }
+        __syncwarp();
+        ep_store(buf, A, n, nrow, ldm, cur.row0(), cur.jb(), lane);
+        cur.next();
+        __syncwarp();  // the buffer is free for the chunk after next
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&sm.tempty[b]));
     }
   }
+  cp_wait<0>();  // no copy may still be writing shared memory after the panel
 }
 
 __global__ void __launch_bounds__(NT_TC, 1)
@@ -285,25 +434,27 @@ __global__ void __launch_bounds__(NT_TC, 1)
   extern __shared__ uint8_t smem_raw[];
   TcSmem sm;
   sm.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm.base + NSTAGE * STAGE_BYTES);
-  sm.full = bars;
-  sm.empty = bars + 2;
-  sm.tfull = bars + 4;
-  sm.tempty = bars + 6;
-  sm.mma_done = bars + 8;
-  sm.tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+  sm.ep = sm.base + A_BYTES + NSTAGE * B_STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm.base + OPS_BYTES);
+  sm.a_full = bars;
+  sm.a_empty = bars + 1;
+  sm.b_full = bars + 2;
+  sm.b_empty = bars + 4;
+  sm.tfull = bars + 6;
+  sm.tempty = bars + 8;
+  sm.mma_done = bars + 10;
+  sm.tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
   sm.abort_flag = reinterpret_cast<volatile int*>(sm.tmem_slot + 1);
   sm.sing = reinterpret_cast<int*>(sm.tmem_slot + 2);
-  using FS = FactorSmem<float2>;
-  float2(*lkk)[NB + 1] = reinterpret_cast<float2(*)[NB + 1]>(sm.base);
-  float2* dinv = reinterpret_cast<float2*>(sm.base + sizeof(float2) * NB * (NB + 1));
-  float2* stages = reinterpret_cast<float2*>(sm.base + FS::LKK_BYTES);
+  const PanelSmem<float2> ps(sm.base);  // aliases the operand buffers (the phases alternate)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
+    mbar_init(smem_u32(sm.a_full), 128);
+    mbar_init(smem_u32(sm.a_empty), 1);
     for (int i = 0; i < 2; ++i) {
-      mbar_init(smem_u32(&sm.full[i]), 128);
-      mbar_init(smem_u32(&sm.empty[i]), 1);
+      mbar_init(smem_u32(&sm.b_full[i]), 128);
+      mbar_init(smem_u32(&sm.b_empty[i]), 1);
       mbar_init(smem_u32(&sm.tfull[i]), 1);
       mbar_init(smem_u32(&sm.tempty[i]), 128);
     }
@@ -321,25 +472,20 @@ __global__ void __launch_bounds__(NT_TC, 1)
   tc_fence_after();
   const uint32_t tmem_base = *sm.tmem_slot;
 
-  int seq = 0, tcount = 0;  // stages and tiles issued so far; every role advances them alike
+  // B stages, tiles and row tiles issued so far; every role advances them alike
+  int seq = 0, tcount = 0, rt = 0;
   for (int k0 = 0; k0 < n; k0 += PW) {
     const int kb = min(PW, n - k0);
-    if (warp < 8) {
-      factor_subpanel(A, n, nrow, ldm, k0, lkk, dinv, *sm.sing);
-      if (kb > NB) {
-        update_region(A, nrow, ldm, k0 + NB, k0 + NB, k0 + kb, k0, NB, stages);
-        factor_subpanel(A, n, nrow, ldm, k0 + NB, lkk, dinv, *sm.sing);
-      }
-    }
+    if (warp < 8) factor_panel(A, n, nrow, ldm, k0, ps, *sm.sing);
     __syncthreads();  // panel W / L^T in global memory; the panel scratch is free
     const int R0 = k0 + kb;
     if (R0 < n) {
       const int n_ti = (nrow - R0 + TM - 1) / TM;
       if (warp == 8) {
-        if (lane == 0) mma_role(sm, tmem_base, n, R0, n_ti, seq, tcount);
+        if (lane == 0) mma_role(sm, tmem_base, n, R0, n_ti, seq, tcount, rt);
         __syncwarp();
       } else if (warp >= 4) {
-        transform_role(sm, A, n, nrow, ldm, k0, R0, n_ti, seq);
+        transform_role(sm, A, n, nrow, ldm, k0, R0, n_ti, seq, rt);
       } else {
         epilogue_role(sm, tmem_base, A, n, nrow, ldm, R0, n_ti, tcount);
       }
@@ -347,9 +493,10 @@ __global__ void __launch_bounds__(NT_TC, 1)
       for (int tI = 0; tI < n_ti; ++tI) nt += tile_cols(R0, n, tI);
       seq += 2 * nt;
       tcount += nt;
+      rt += n_ti;
     }
     tc_fence_before();
-    __syncthreads();  // every tile of the panel is written back; the stages are free
+    __syncthreads();  // every tile of the panel is written back; the operand buffers are free
     tc_fence_after();
     if (*sm.abort_flag) break;
   }
