@@ -18,17 +18,16 @@
 // accumulator of the tensor core adds only 16 large partial products into D1 per panel; the
 // epilogue forms C - D1 - D2 in round-to-nearest FP32.
 //
-// Roles (288 threads, one CTA per matrix):
+// Roles (416 threads, one CTA per matrix):
 //   warps 0-7   panel factorisation (the shared SIMT routine, named barrier 1)
 //   warps 4-7   operand transform: global memory (L2) -> hi/lo planes in the 128-byte-swizzled
 //               K-major layout. The A operand (W rows of a 128-row tile, all 64 panel columns)
 //               stays resident while the tile row's column tiles pass; the B operand (L rows of a
-//               64-column tile) streams through two stages of 32 panel columns, its global loads
-//               issued one stage ahead.
-//   warp 8      TMEM allocation (512 columns: two tiles in flight x {D1, D2}) and the MMA issuer
-//   warps 0-3   epilogue: the target tile passes through shared memory in 32-row x 16-column chunks
-//               per warp (coalesced asynchronous loads one chunk ahead, coalesced stores), each
-//               thread subtracting its row's TMEM accumulators in between
+//               64-column tile) streams through two stages of 32 panel columns, the global loads
+//               of a stage issued before the wait for its buffer.
+//   warp 12     TMEM allocation (512 columns: two tiles in flight x {D1, D2}) and the MMA issuer
+//   warps 0-3,  epilogue: one thread per tile row and half of the tile's columns, the target values
+//   8-11        read and written with 16-byte accesses, the next chunk's values loaded ahead
 // The panel scratch of the SIMT routine aliases the operand buffers (the phases alternate).
 // Every mbarrier wait is bounded (one second); on expiry the CTA records kStatTimeout, stops,
 // drains the MMAs it issued and frees TMEM.
@@ -48,11 +47,11 @@ constexpr int A_BYTES = 8 * A_PLANE;                     // 128 KB: the resident
 constexpr int B_PLANE = TN * 128;                        // 8 KB: Lr, Li, Lr_lo, Li_lo
 constexpr int B_STAGE = 4 * B_PLANE;                     // 32 KB
 constexpr int NSTAGE = 2;
-constexpr int EP_BUF = 32 * 128;                         // 4 KB: 32 rows x 16 complex columns
-constexpr int EP_BYTES = 4 * 2 * EP_BUF;                 // two chunk buffers per epilogue warp
-constexpr int NT_TC = 288;
+constexpr int NT_TC = 416;                               // 13 warps
+constexpr int MMA_WARP = 12;
+constexpr int N_EPI = 256;                               // epilogue threads (warps 0-3, 8-11)
 constexpr int META_BYTES = 128;
-constexpr int OPS_BYTES = A_BYTES + NSTAGE * B_STAGE + EP_BYTES;  // 224 KB
+constexpr int OPS_BYTES = A_BYTES + NSTAGE * B_STAGE;    // 192 KB
 constexpr int SMEM_TC = 1024 + OPS_BYTES + META_BYTES;
 static_assert(PW == 2 * KH, "one panel is two stages");
 static_assert(PanelSmem<float2>::bytes() <= (size_t)OPS_BYTES, "panel scratch fits in the operand buffers");
@@ -98,7 +97,6 @@ __device__ __forceinline__ int tile_cols(int R0, int n, int tI) {
 
 struct TcSmem {
   uint8_t* base;  // A operand, then the B stages
-  uint8_t* ep;    // epilogue staging
   uint64_t *a_full, *a_empty, *b_full, *b_empty, *tfull, *tempty, *mma_done;
   uint32_t* tmem_slot;
   volatile int* abort_flag;
@@ -158,23 +156,24 @@ __device__ void transform_role(const TcSmem& sm, const float2* A, int n, int nro
       const int rq = tt & 3, rr = tt >> 2;
       const int i0 = R0 + TM * tI;
 #pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        float4 av[16];
+      for (int hp = 0; hp < 4; ++hp) {  // (half, pair of row passes)
+        const int h = hp >> 1;
+        float4 av[8];
 #pragma unroll
-        for (int ps = 0; ps < 4; ++ps) {
-          const int i = i0 + rr + 32 * ps;
+        for (int pp = 0; pp < 2; ++pp) {
+          const int i = i0 + rr + 32 * (2 * (hp & 1) + pp);
           const float4* src =
               reinterpret_cast<const float4*>(A + (long long)(i < nrow ? i : 0) * ldm + k0 + KH * h + 8 * rq);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) av[4 * ps + c] = i < nrow ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int c = 0; c < 4; ++c) av[4 * pp + c] = i < nrow ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int ps = 0; ps < 4; ++ps) {
-          const int r = rr + 32 * ps, sw = r & 7;
+        for (int pp = 0; pp < 2; ++pp) {
+          const int r = rr + 32 * (2 * (hp & 1) + pp), sw = r & 7;
           uint8_t* rowp = sm.base + h * 4 * A_PLANE + r * 128;
 #pragma unroll
           for (int e = 0; e < 2; ++e) {  // chunk 2 rq + e: complex l = 8 rq + 4 e .. + 3
-            const float4 v0 = av[4 * ps + 2 * e], v1 = av[4 * ps + 2 * e + 1];
+            const float4 v0 = av[4 * pp + 2 * e], v1 = av[4 * pp + 2 * e + 1];
             const float re[4] = {v0.x, v0.z, v1.x, v1.z};
             const float im[4] = {v0.y, v0.w, v1.y, v1.w};
             float4 rh, rl, ih, il;
@@ -194,11 +193,6 @@ __device__ void transform_role(const TcSmem& sm, const float2* A, int n, int nro
     // B operand stages of this row tile
     const int nc = tile_cols(R0, n, tI);
     for (int q = 0; q < 2 * nc; ++q, ++seq) {
-      float2 cur[16];
-#pragma unroll
-      for (int e = 0; e < 16; ++e) cur[e] = bv[e];
-      it.next();
-      if (it.valid()) load_b(bv, A, n, ldm, k0, it, tt);  // next stage's loads in flight meanwhile
       const int s = seq & 1, us = seq >> 1;
       if (!mbar_wait(smem_u32(&sm.b_empty[s]), (us & 1) ^ 1, sm.abort_flag)) {
         ok = false;
@@ -211,8 +205,8 @@ __device__ void transform_role(const TcSmem& sm, const float2* A, int n, int nro
         float lr[4], li[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          lr[e] = cur[4 * c + e].x;
-          li[e] = cur[4 * c + e].y;
+          lr[e] = bv[4 * c + e].x;
+          li[e] = bv[4 * c + e].y;
         }
         float4 rh, rl, ih, il;
         split4(lr, rh, rl);
@@ -225,6 +219,9 @@ __device__ void transform_role(const TcSmem& sm, const float2* A, int n, int nro
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&sm.b_full[s]));
+      // the next stage's loads travel while this thread waits for that stage's buffer
+      it.next();
+      if (it.valid()) load_b(bv, A, n, ldm, k0, it, tt);
     }
   }
 }
@@ -288,8 +285,11 @@ __device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, in
   }
 }
 
-// ---- epilogue (warps 0-3): C -= D1 + D2 ---------------------------------------------------------
-// TMEM loads without the implicit wait, so the four accumulator slices of a chunk share one wait
+// ---- epilogue (warps 0-3 and 8-11): C -= D1 + D2 -----------------------------------------------
+// Warp w serves TMEM lanes 32 (w % 4) .. +31 (rows of the tile) and, with its partner w ^ 8, half
+// of the tile's 64 columns: two 16-column chunks. Each thread owns one row; the target values of
+// its next chunk are loaded (16-byte loads) while the current one is formed.
+// TMEM loads without the implicit wait, so the accumulator slices of a chunk share one wait
 __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -298,81 +298,56 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) 
       : "r"(taddr));
 }
 
-// first row of this warp's 32-row slice and first column of one 16-column chunk, in issue order
+// this thread's chunks in issue order: (row tile, column tile, chunk cc0 or cc0 + 1)
 struct ChunkIt {
-  int R0, n, n_ti, q;
-  int tI, tJ, cc, nc;
-  __device__ void init(int R0_, int n_, int n_ti_, int q_) {
+  int R0, n, nrow, n_ti, r, cc0;
+  int tI, tJ, cc, nc, i, jlim;
+  __device__ void set_row() {
+    i = R0 + TM * tI + r;
+    jlim = i < nrow ? (i < n ? min(n, i + 1) : n) : 0;  // j <= i inside the factored block
+  }
+  __device__ void init(int R0_, int n_, int nrow_, int n_ti_, int r_, int cc0_) {
     R0 = R0_;
     n = n_;
+    nrow = nrow_;
     n_ti = n_ti_;
-    q = q_;
+    r = r_;
+    cc0 = cc0_;
     tI = 0;
     tJ = 0;
-    cc = 0;
+    cc = cc0;
     nc = tile_cols(R0, n, 0);
+    set_row();
   }
   __device__ bool valid() const { return tI < n_ti; }
-  __device__ int row0() const { return R0 + TM * tI + 32 * q; }
   __device__ int jb() const { return R0 + TN * tJ + 16 * cc; }
+  __device__ bool full() const { return valid() && jb() + 16 <= jlim; }
   __device__ void next() {
-    if (++cc == TN / 16) {
-      cc = 0;
+    if (++cc == cc0 + 2) {
+      cc = cc0;
       if (++tJ == nc) {
         tJ = 0;
         ++tI;
         nc = tI < n_ti ? tile_cols(R0, n, tI) : 0;
+        set_row();
       }
     }
   }
 };
 
-// columns j < jlim of row i are updated: j <= i inside the factored block, every j < n below it
-__device__ __forceinline__ int row_jlim(int i, int n, int nrow) { return i < nrow ? (i < n ? min(n, i + 1) : n) : 0; }
-
-// chunk (32 rows x 16 complex columns) of the target into a warp's staging buffer: 8 pieces of
-// 16 bytes per lane, four full rows per instruction; 16-byte pieces start at even columns and ldm
-// is a multiple of 4, so a piece never crosses the end of its row
-__device__ __forceinline__ void ep_load(uint8_t* buf, const float2* A, int n, int nrow, long long ldm, int row0, int jb,
-                                        int lane) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int pc = lane + 32 * k, rr = pc >> 3, ch = pc & 7;
-    const int i = row0 + rr, col = jb + 2 * ch;
-    const bool v = col < row_jlim(i, n, nrow);
-    cp_async16(buf + rr * 128 + ((ch ^ (rr & 7)) << 4), v ? A + (long long)i * ldm + col : A, v);
-  }
-  cp_commit();
-}
-
-__device__ __forceinline__ void ep_store(const uint8_t* buf, float2* A, int n, int nrow, long long ldm, int row0, int jb,
-                                         int lane) {
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int pc = lane + 32 * k, rr = pc >> 3, ch = pc & 7;
-    const int i = row0 + rr, col = jb + 2 * ch;
-    const int jl = row_jlim(i, n, nrow);
-    if (col >= jl) continue;
-    const float4 v = *reinterpret_cast<const float4*>(buf + rr * 128 + ((ch ^ (rr & 7)) << 4));
-    float2* dst = A + (long long)i * ldm + col;
-    if (col + 1 < jl)
-      *reinterpret_cast<float4*>(dst) = v;
-    else
-      *dst = make_float2(v.x, v.y);
-  }
-}
-
 __device__ void epilogue_role(const TcSmem& sm, uint32_t tmem_base, float2* __restrict__ A, int n, int nrow,
                               long long ldm, int R0, int n_ti, int tcount) {
-  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, q = warp & 3, cc0 = 2 * (warp >> 3);
+  const int r = 32 * q + (threadIdx.x & 31);
   const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
-  uint8_t* bufs = sm.ep + q * 2 * EP_BUF;
-  ChunkIt ld, cur;
-  ld.init(R0, n, n_ti, q);
-  cur = ld;
-  ep_load(bufs, A, n, nrow, ldm, ld.row0(), ld.jb(), lane);
-  ld.next();
-  int g = 0;  // chunk index within the panel (buffer parity)
+  ChunkIt it;
+  it.init(R0, n, nrow, n_ti, r, cc0);
+  float4 nxt[8];
+  if (it.full()) {
+    const float2* p = A + (long long)it.i * ldm + it.jb();
+#pragma unroll
+    for (int e = 0; e < 8; ++e) nxt[e] = *reinterpret_cast<const float4*>(p + 2 * e);
+  }
   bool ok = true;
   for (int tI = 0; tI < n_ti && ok; ++tI) {
     const int nc = tile_cols(R0, n, tI);
@@ -383,46 +358,62 @@ __device__ void epilogue_role(const TcSmem& sm, uint32_t tmem_base, float2* __re
       if (!ok) break;
       tc_fence_after();
 #pragma unroll 1
-      for (int cc = 0; cc < TN / 16; ++cc, ++g) {
-        uint8_t* buf = bufs + (g & 1) * EP_BUF;
-        // next chunk's loads into the other buffer (its stores finished a chunk ago)
-        if (ld.valid()) {
-          ep_load(bufs + ((g + 1) & 1) * EP_BUF, A, n, nrow, ldm, ld.row0(), ld.jb(), lane);
-          ld.next();
-          cp_wait<1>();
-        } else {
-          cp_wait<0>();
-        }
-        uint32_t d1r[16], d1i[16], d2r[16], d2i[16];
-        const uint32_t col = lane_base + (uint32_t)(b * 256 + 16 * cc);
-        tmem_ld16_nw(col, d1r);
-        tmem_ld16_nw(col + 64, d1i);
-        tmem_ld16_nw(col + 128, d2r);
-        tmem_ld16_nw(col + 192, d2i);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        __syncwarp();  // every lane's copies of this chunk have landed
-        // this lane's row: C - D1 - D2 for 16 complex columns
-        uint8_t* rowp = buf + lane * 128;
+      for (int cc = cc0; cc < cc0 + 2; ++cc) {
+        const bool full = it.full();
+        const int jb = it.jb(), jlim = it.jlim, i = it.i;
+        float4 cur[8];
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
-          float4* pv = reinterpret_cast<float4*>(rowp + ((ch ^ (lane & 7)) << 4));
-          float4 c = *pv;
-          c.x = c.x - __uint_as_float(d1r[2 * ch]) - __uint_as_float(d2r[2 * ch]);
-          c.y = c.y - __uint_as_float(d1i[2 * ch]) - __uint_as_float(d2i[2 * ch]);
-          c.z = c.z - __uint_as_float(d1r[2 * ch + 1]) - __uint_as_float(d2r[2 * ch + 1]);
-          c.w = c.w - __uint_as_float(d1i[2 * ch + 1]) - __uint_as_float(d2i[2 * ch + 1]);
-          *pv = c;
+        for (int e = 0; e < 8; ++e) cur[e] = nxt[e];
+        it.next();
+        if (it.full()) {  // the next chunk's target values, in flight while this one is formed
+          const float2* pn = A + (long long)it.i * ldm + it.jb();
+#pragma unroll
+          for (int e = 0; e < 8; ++e) nxt[e] = *reinterpret_cast<const float4*>(pn + 2 * e);
         }
-        __syncwarp();
-        ep_store(buf, A, n, nrow, ldm, cur.row0(), cur.jb(), lane);
-        cur.next();
-        __syncwarp();  // the buffer is free for the chunk after next
+        float2* p = A + (long long)i * ldm + jb;
+        const bool part = !full && jb < jlim;
+        if (part) {  // ragged chunk: the valid columns only
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float2 u = jb + 2 * e < jlim ? p[2 * e] : make_float2(0.f, 0.f);
+            const float2 v = jb + 2 * e + 1 < jlim ? p[2 * e + 1] : make_float2(0.f, 0.f);
+            cur[e] = make_float4(u.x, u.y, v.x, v.y);
+          }
+        }
+        // Re parts (accumulator columns 16 cc .. of D1 and D2), then Im parts (64 columns on)
+        const uint32_t col = lane_base + (uint32_t)(b * 256 + 16 * cc);
+        uint32_t t1[16], t2[16];
+        tmem_ld16_nw(col, t1);
+        tmem_ld16_nw(col + 128, t2);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          cur[e].x = cur[e].x - __uint_as_float(t1[2 * e]) - __uint_as_float(t2[2 * e]);
+          cur[e].z = cur[e].z - __uint_as_float(t1[2 * e + 1]) - __uint_as_float(t2[2 * e + 1]);
+        }
+        tmem_ld16_nw(col + 64, t1);
+        tmem_ld16_nw(col + 192, t2);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          cur[e].y = cur[e].y - __uint_as_float(t1[2 * e]) - __uint_as_float(t2[2 * e]);
+          cur[e].w = cur[e].w - __uint_as_float(t1[2 * e + 1]) - __uint_as_float(t2[2 * e + 1]);
+        }
+        if (full) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) *reinterpret_cast<float4*>(p + 2 * e) = cur[e];
+        } else if (part) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            if (jb + 2 * e < jlim) p[2 * e] = make_float2(cur[e].x, cur[e].y);
+            if (jb + 2 * e + 1 < jlim) p[2 * e + 1] = make_float2(cur[e].z, cur[e].w);
+          }
+        }
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&sm.tempty[b]));
     }
   }
-  cp_wait<0>();  // no copy may still be writing shared memory after the panel
 }
 
 __global__ void __launch_bounds__(NT_TC, 1)
@@ -434,7 +425,6 @@ __global__ void __launch_bounds__(NT_TC, 1)
   extern __shared__ uint8_t smem_raw[];
   TcSmem sm;
   sm.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  sm.ep = sm.base + A_BYTES + NSTAGE * B_STAGE;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm.base + OPS_BYTES);
   sm.a_full = bars;
   sm.a_empty = bars + 1;
@@ -456,14 +446,14 @@ __global__ void __launch_bounds__(NT_TC, 1)
       mbar_init(smem_u32(&sm.b_full[i]), 128);
       mbar_init(smem_u32(&sm.b_empty[i]), 1);
       mbar_init(smem_u32(&sm.tfull[i]), 1);
-      mbar_init(smem_u32(&sm.tempty[i]), 128);
+      mbar_init(smem_u32(&sm.tempty[i]), N_EPI);
     }
     mbar_init(smem_u32(sm.mma_done), 1);
     *sm.abort_flag = 0;
     *sm.sing = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) {
+  if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(sm.tmem_slot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -481,10 +471,10 @@ __global__ void __launch_bounds__(NT_TC, 1)
     const int R0 = k0 + kb;
     if (R0 < n) {
       const int n_ti = (nrow - R0 + TM - 1) / TM;
-      if (warp == 8) {
+      if (warp == MMA_WARP) {
         if (lane == 0) mma_role(sm, tmem_base, n, R0, n_ti, seq, tcount, rt);
         __syncwarp();
-      } else if (warp >= 4) {
+      } else if (warp >= 4 && warp < 8) {
         transform_role(sm, A, n, nrow, ldm, k0, R0, n_ti, seq, rt);
       } else {
         epilogue_role(sm, tmem_base, A, n, nrow, ldm, R0, n_ti, tcount);
@@ -501,7 +491,7 @@ __global__ void __launch_bounds__(NT_TC, 1)
     if (*sm.abort_flag) break;
   }
   // every MMA issued has completed before TMEM is freed (immediate unless a wait gave up)
-  if (warp == 8) {
+  if (warp == MMA_WARP) {
     if (lane == 0) {
       mma_commit(smem_u32(sm.mma_done));
       mbar_drain(smem_u32(sm.mma_done), 0);
@@ -514,7 +504,7 @@ __global__ void __launch_bounds__(NT_TC, 1)
     if (*sm.abort_flag) atomicOr(status, kStatTimeout);
     if (*sm.sing) atomicOr(status, kStatSingular);
   }
-  if (warp == 8) {
+  if (warp == MMA_WARP) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base));
   }
