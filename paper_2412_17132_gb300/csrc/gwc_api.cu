@@ -549,9 +549,10 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || ctx->n_sm < 1)
     ctx->n_sm = 1;
   {
-    // GWC_FACTOR=tc moves complex factorisations of the mixed modes to the tensor-core kernel
+    // complex factorisations of the mixed modes run on the tensor-core kernel; GWC_FACTOR=simt
+    // keeps them on the SIMT kernel (A/B measurements)
     const char* fe = std::getenv("GWC_FACTOR");
-    ctx->factor_tc = fe && std::strcmp(fe, "tc") == 0;
+    ctx->factor_tc = !(fe && std::strcmp(fe, "simt") == 0);
   }
   ctx->n_states = s->n_states;
   ctx->n_occ = s->n_occ;
