@@ -361,13 +361,29 @@ def run_gpu(args):
             clk_mhz = peaks.get("sm_max_mhz", 2070.0)
             fp32_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
             fac_alg = st["factor_flop"] / fac_t if fac_t > 0 else 0.0
-            peak = fp32_peak if args.prec != "fp64" else 1.2
-            roof = {"kernel": "ldlt_kernel (batched complex-symmetric LDL^T, " + ("FP64" if args.prec == "fp64" else "FP32") + ")",
-                    "bound": "alu", "achieved": fac_alg / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": fac_alg / 1e12 / peak,
-                    "traffic": load_traffic("ldlt_kernel", mol.name, st["factorizations"] / max(1, st["factor_launches"])),
-                    "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 flop x max SM clock" if args.prec != "fp64"
-                                    else "FP64 FMA loop measured on this GB300 (1.20 TFLOP/s)"),
-                    "share_of_step": fac_t / (total_ms * 1e-3 / ws)}
+            units = st["factorizations"] / max(1, st["factor_launches"])
+            tc_factor = args.prec in ("bf16x3", "bf16") and os.environ.get("GWC_FACTOR", "") != "simt"
+            if tc_factor:
+                # trailing updates on the tensor cores in 3xTF32: three TF32 products per FP32-accurate one
+                tf32 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")) * 1.1 / 2.25
+                peak = tf32 / 3.0
+                roof = {"kernel": "ldlt_tc_kernel (batched complex-symmetric LDL^T, FP32: tcgen05 3xTF32 trailing "
+                                  "updates + SIMT panels)",
+                        "bound": "tensor", "achieved": fac_alg / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": fac_alg / 1e12 / peak, "alu_frac": fac_alg / 1e12 / fp32_peak,
+                        "traffic": load_traffic("ldlt_tc_kernel", mol.name, units),
+                        "peak_source": f"{src} bf16 sustained x 1.1/2.25 (nominal TF32/BF16 dense) / 3 (3xTF32)",
+                        "share_of_step": fac_t / (total_ms * 1e-3 / ws)}
+            else:
+                peak = fp32_peak if args.prec != "fp64" else 1.2
+                roof = {"kernel": "ldlt_kernel (batched complex-symmetric LDL^T, " +
+                                  ("FP64" if args.prec == "fp64" else "FP32") + ")",
+                        "bound": "alu", "achieved": fac_alg / 1e12, "peak": peak, "unit": "TFLOP/s",
+                        "frac": fac_alg / 1e12 / peak,
+                        "traffic": load_traffic("ldlt_kernel", mol.name, units),
+                        "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 flop x max SM clock" if args.prec != "fp64"
+                                        else "FP64 FMA loop measured on this GB300 (1.20 TFLOP/s)"),
+                        "share_of_step": fac_t / (total_ms * 1e-3 / ws)}
         lat = sorted(times)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
