@@ -37,14 +37,14 @@ __global__ void __launch_bounds__(256) ldlt_kernel(S* __restrict__ mats, int n, 
   S* A = mats + f * stride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // the panel scratch and the update stages alias (the phases alternate)
-  const PanelSmem<S> ps(smem_raw);
+  const PanelSmem<S, kSimtThreads> ps(smem_raw);
   S* stages = reinterpret_cast<S*>(smem_raw);
   __shared__ int sing;
   if (threadIdx.x == 0) sing = 0;
 
   for (int k0 = 0; k0 < n; k0 += PW) {
     const int kb = min(PW, n - k0);
-    factor_panel(A, n, nrow, ldm, k0, ps, sing);
+    factor_panel<S, kSimtThreads>(A, n, nrow, ldm, k0, ps, sing);
     // rank-kb trailing update of the lower triangle beyond the panel (and of appended rows)
     if (k0 + kb < n) update_region(A, nrow, ldm, k0 + kb, k0 + kb, n, k0, kb, stages);
   }
@@ -165,7 +165,7 @@ template <typename S>
 int run_ldlt(S* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active, unsigned* status,
              cudaStream_t s) {
   static bool attr = false;
-  const size_t sm = std::max(FactorSmem<S>::bytes(), PanelSmem<S>::bytes());
+  const size_t sm = std::max(FactorSmem<S>::bytes(), PanelSmem<S, kSimtThreads>::bytes());
   if (!attr) {
     if (cudaFuncSetAttribute(ldlt_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
     attr = true;

@@ -183,10 +183,17 @@ __device__ void update_region(S* __restrict__ A, int n, long long ldm, int r0, i
   }
 }
 
-// Shared memory of the panel factorisation: the two diagonal blocks (factored in place: unit L
-// below the diagonal, d on it), their inverse pivots, W / L of the second block's rows against
-// the first block (for the Schur complement of the second block), and per-thread row scratch.
-template <typename S>
+// Barrier over the first NT threads of the CTA (named barrier 1).
+template <int NT>
+__device__ __forceinline__ void grp_sync_n() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
+// Shared memory of the panel factorisation (NT threads): the two diagonal blocks (factored in
+// place: unit L below the diagonal, d on it), their inverse pivots, W / L of the second block's
+// rows against the first block (for the Schur complement of the second block), and per-thread row
+// scratch.
+template <typename S, int NT>
 struct PanelSmem {
   S (*lkk1)[NB + 1];
   S (*lkk2)[NB + 1];
@@ -194,8 +201,8 @@ struct PanelSmem {
   S (*l1s)[NB + 1];
   S* dinv1;
   S* dinv2;
-  S* arow;  // [NB][kSimtThreads]: block-2 part of each thread's current row
-  static constexpr size_t bytes() { return sizeof(S) * (4 * NB * (NB + 1) + 2 * NB + NB * kSimtThreads); }
+  S* arow;  // [NB][NT]: block-2 part of each thread's current row
+  static constexpr size_t bytes() { return sizeof(S) * (4 * NB * (NB + 1) + 2 * NB + NB * NT); }
   __device__ explicit PanelSmem(void* base) {
     S* p = reinterpret_cast<S*>(base);
     lkk1 = reinterpret_cast<S(*)[NB + 1]>(p);
@@ -208,37 +215,38 @@ struct PanelSmem {
   }
 };
 
-// In-place LDL^T of the kb x kb block held (lower triangle) in lkk; a zero pivot is replaced by 1
-// and flagged.
+// In-place LDL^T of the kb x kb block held (lower triangle) in lkk, by one warp (lane i owns row
+// i; no block-wide barrier per column); a zero pivot is replaced by 1 and flagged.
 template <typename S>
-__device__ void factor_diag(S (*lkk)[NB + 1], S* dinv, int kb, int& sing) {
-  const int tid = threadIdx.x;
+__device__ void factor_diag_warp(S (*lkk)[NB + 1], S* dinv, int kb, int& sing) {
+  const int i = threadIdx.x & 31;
   for (int j = 0; j < kb; ++j) {
+    __syncwarp();
     S d = lkk[j][j];
-    if (sabs2(d) < 1e-60) {
-      if (tid == 0) sing = 1;
-      d = sfrom<S>(1.0, 0.0);
-    }
+    const bool zero = sabs2(d) < 1e-60;
+    if (zero) d = sfrom<S>(1.0, 0.0);
     const S inv = sinv(d);
-    const int m = kb - 1 - j;
-    for (int e = tid; e < m * m; e += kSimtThreads) {
-      const int i = j + 1 + e / m, l = j + 1 + e % m;
-      if (l <= i) lkk[i][l] = sfnms(smul(lkk[i][j], inv), lkk[l][j], lkk[i][l]);
+    S lij = szero<S>();
+    if (i > j && i < kb) {
+      // row i of the Schur complement: a_il -= (a_ij / d_j) a_lj for j < l <= i (column j unscaled)
+      lij = smul(lkk[i][j], inv);
+      for (int l = j + 1; l <= i; ++l) lkk[i][l] = sfnms(lij, lkk[l][j], lkk[i][l]);
     }
-    grp_sync();
-    if (tid == 0) {
+    __syncwarp();
+    if (i > j && i < kb) lkk[i][j] = lij;
+    if (i == j) {
       lkk[j][j] = d;
       dinv[j] = inv;
+      if (zero) sing = 1;
     }
-    for (int i = j + 1 + tid; i < kb; i += kSimtThreads) lkk[i][j] = smul(lkk[i][j], inv);
-    grp_sync();
   }
+  __syncwarp();
 }
 
 // diagonal block at (c0, c0): W = L d below the diagonal, d on it, L^T above it
-template <typename S>
+template <typename S, int NT>
 __device__ void store_diag(S* __restrict__ A, long long ldm, int c0, int kb, S (*lkk)[NB + 1]) {
-  for (int e = threadIdx.x; e < kb * kb; e += kSimtThreads) {
+  for (int e = threadIdx.x; e < kb * kb; e += NT) {
     const int i = e / kb, j = e % kb;
     if (j < i) {
       A[(long long)(c0 + i) * ldm + (c0 + j)] = smul(lkk[i][j], lkk[j][j]);
@@ -269,27 +277,29 @@ __device__ __forceinline__ void solve_row(S (&w)[NB], S (*lkk)[NB + 1], int kb) 
 }
 
 // Factor the panel [k0, k0 + min(PW, n - k0)) (its columns already hold the Schur complement) as
-// two NB-wide halves: the diagonal blocks in shared memory, then every row below in one pass by one
-// thread: solve against block 1, apply block 1 to its block-2 columns, solve against block 2, and
-// store W (lower) and L^T (upper). Rows >= n are appended right-hand sides (W only).
-template <typename S>
-__device__ void factor_panel(S* __restrict__ A, int n, int nrow, long long ldm, int k0, const PanelSmem<S>& ps,
+// two NB-wide halves, on the first NT threads: the diagonal blocks in shared memory (one warp each),
+// then every row below in one pass by one thread: solve against block 1, apply block 1 to its
+// block-2 columns, solve against block 2, and store W (lower) and L^T (upper). Rows >= n are
+// appended right-hand sides (W only).
+template <typename S, int NT>
+__device__ void factor_panel(S* __restrict__ A, int n, int nrow, long long ldm, int k0, const PanelSmem<S, NT>& ps,
                              int& sing) {
   const int tid = threadIdx.x;
   const int kb = min(PW, n - k0);
   const int kb1 = min(NB, kb), kb2 = kb - kb1;
   const int c2 = k0 + NB;
-  grp_sync();
-  for (int e = tid; e < NB * NB; e += kSimtThreads) {
+  grp_sync_n<NT>();
+  for (int e = tid; e < NB * NB; e += NT) {
     const int i = e / NB, j = e % NB;
     ps.lkk1[i][j] = (i < kb1 && j <= i) ? A[(long long)(k0 + i) * ldm + (k0 + j)] : szero<S>();
   }
-  grp_sync();
-  factor_diag(ps.lkk1, ps.dinv1, kb1, sing);
-  store_diag(A, ldm, k0, kb1, ps.lkk1);
+  grp_sync_n<NT>();
+  if (tid < 32) factor_diag_warp(ps.lkk1, ps.dinv1, kb1, sing);
+  grp_sync_n<NT>();
+  store_diag<S, NT>(A, ldm, k0, kb1, ps.lkk1);
   if (kb2 > 0) {
     // rows of block 2 against block 1
-    for (int r = tid; r < kb2; r += kSimtThreads) {
+    for (int r = tid; r < kb2; r += NT) {
       const int i = c2 + r;
       S* row = A + (long long)i * ldm + k0;
       S w[NB];
@@ -305,9 +315,9 @@ __device__ void factor_panel(S* __restrict__ A, int n, int nrow, long long ldm, 
         ps.l1s[r][j] = l;
       }
     }
-    grp_sync();
+    grp_sync_n<NT>();
     // Schur complement of block 2
-    for (int e = tid; e < NB * NB; e += kSimtThreads) {
+    for (int e = tid; e < NB * NB; e += NT) {
       const int r = e / NB, c = e % NB;
       S v = szero<S>();
       if (r < kb2 && c <= r) {
@@ -317,16 +327,17 @@ __device__ void factor_panel(S* __restrict__ A, int n, int nrow, long long ldm, 
       }
       ps.lkk2[r][c] = v;
     }
-    grp_sync();
-    factor_diag(ps.lkk2, ps.dinv2, kb2, sing);
-    store_diag(A, ldm, c2, kb2, ps.lkk2);
+    grp_sync_n<NT>();
+    if (tid < 32) factor_diag_warp(ps.lkk2, ps.dinv2, kb2, sing);
+    grp_sync_n<NT>();
+    store_diag<S, NT>(A, ldm, c2, kb2, ps.lkk2);
   }
   // every row below the panel
-  for (int i = k0 + kb + tid; i < nrow; i += kSimtThreads) {
+  for (int i = k0 + kb + tid; i < nrow; i += NT) {
     S* row = A + (long long)i * ldm + k0;
     // block-2 values of the row into this thread's scratch, in flight while block 1 is solved
     S* as = ps.arow + tid;
-    for (int c = 0; c < kb2; ++c) cp_async_elem<(int)sizeof(S)>(as + c * kSimtThreads, row + NB + c);
+    for (int c = 0; c < kb2; ++c) cp_async_elem<(int)sizeof(S)>(as + c * NT, row + NB + c);
     cp_commit();
     S w[NB];
 #pragma unroll
@@ -344,7 +355,7 @@ __device__ void factor_panel(S* __restrict__ A, int n, int nrow, long long ldm, 
       cp_wait<0>();
 #pragma unroll 1
       for (int c = 0; c < kb2; ++c) {
-        S v0 = as[c * kSimtThreads], v1 = szero<S>(), v2 = szero<S>(), v3 = szero<S>();
+        S v0 = as[c * NT], v1 = szero<S>(), v2 = szero<S>(), v3 = szero<S>();
 #pragma unroll
         for (int j = 0; j < NB; j += 4) {
           v0 = sfnms(w[j], ps.l1s[c][j], v0);
@@ -354,18 +365,18 @@ __device__ void factor_panel(S* __restrict__ A, int n, int nrow, long long ldm, 
         }
         int l = 0;
         for (; l + 1 < c; l += 2) {
-          v0 = sfnms(as[l * kSimtThreads], ps.lkk2[c][l], v0);
-          v1 = sfnms(as[(l + 1) * kSimtThreads], ps.lkk2[c][l + 1], v1);
+          v0 = sfnms(as[l * NT], ps.lkk2[c][l], v0);
+          v1 = sfnms(as[(l + 1) * NT], ps.lkk2[c][l + 1], v1);
         }
-        if (l < c) v2 = sfnms(as[l * kSimtThreads], ps.lkk2[c][l], v2);
+        if (l < c) v2 = sfnms(as[l * NT], ps.lkk2[c][l], v2);
         const S v = sadd(sadd(v0, v1), sadd(v2, v3));
-        as[c * kSimtThreads] = v;
+        as[c * NT] = v;
         row[NB + c] = v;
         if (i < n) A[(long long)(c2 + c) * ldm + i] = smul(v, ps.dinv2[c]);
       }
     }
   }
-  grp_sync();
+  grp_sync_n<NT>();
 }
 
 }  // namespace

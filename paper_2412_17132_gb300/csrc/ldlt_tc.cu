@@ -19,7 +19,7 @@
 // epilogue forms C - D1 - D2 in round-to-nearest FP32.
 //
 // Roles (416 threads, one CTA per matrix):
-//   warps 0-7   panel factorisation (the shared SIMT routine, named barrier 1)
+//   warps 0-11  panel factorisation (the shared SIMT routine, named barrier 1)
 //   warps 4-7   operand transform: global memory (L2) -> hi/lo planes in the 128-byte-swizzled
 //               K-major layout. The A operand (W rows of a 128-row tile, all 64 panel columns)
 //               stays resident while the tile row's column tiles pass; the B operand (L rows of a
@@ -54,7 +54,8 @@ constexpr int META_BYTES = 128;
 constexpr int OPS_BYTES = A_BYTES + NSTAGE * B_STAGE;    // 192 KB
 constexpr int SMEM_TC = 1024 + OPS_BYTES + META_BYTES;
 static_assert(PW == 2 * KH, "one panel is two stages");
-static_assert(PanelSmem<float2>::bytes() <= (size_t)OPS_BYTES, "panel scratch fits in the operand buffers");
+constexpr int NT_PANEL = 384;                            // warps 0-11 factor the panels
+static_assert(PanelSmem<float2, NT_PANEL>::bytes() <= (size_t)OPS_BYTES, "panel scratch fits in the operand buffers");
 
 // kind::tf32 instruction descriptors: D = F32, A = B = TF32, both K-major, N = TN, M = TM;
 // the second negates A (bit 13).
@@ -436,7 +437,7 @@ __global__ void __launch_bounds__(NT_TC, 1)
   sm.tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
   sm.abort_flag = reinterpret_cast<volatile int*>(sm.tmem_slot + 1);
   sm.sing = reinterpret_cast<int*>(sm.tmem_slot + 2);
-  const PanelSmem<float2> ps(sm.base);  // aliases the operand buffers (the phases alternate)
+  const PanelSmem<float2, NT_PANEL> ps(sm.base);  // aliases the operand buffers (the phases alternate)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(NT_TC, 1)
   int seq = 0, tcount = 0, rt = 0;
   for (int k0 = 0; k0 < n; k0 += PW) {
     const int kb = min(PW, n - k0);
-    if (warp < 8) factor_panel(A, n, nrow, ldm, k0, ps, *sm.sing);
+    if (warp < NT_PANEL / 32) factor_panel<float2, NT_PANEL>(A, n, nrow, ldm, k0, ps, *sm.sing);
     __syncthreads();  // panel W / L^T in global memory; the panel scratch is free
     const int R0 = k0 + kb;
     if (R0 < n) {
