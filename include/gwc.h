@@ -101,8 +101,12 @@ typedef struct {
 /* GWC_QP_SECANT: iterate the G_dH W0 QP equation (eq quasiparticle_equation with the shifted
  *   self-energy of eq hedin_sigma_spectral) by the secant method from eps_n;
  * GWC_QP_HEDIN: the GW+C QP energy of eq QPGWC, eps_n + dH_n, which is the exact fixed point of
- *   that equation (one self-energy evaluation per core instead of one per iterate). */
-typedef enum { GWC_QP_SECANT = 0, GWC_QP_HEDIN = 1 } gwc_qp_mode;
+ *   that equation (one self-energy evaluation per core instead of one per iterate);
+ * GWC_QP_G0W0: the plain G0W0 QP equation (eq quasiparticle_equation, Sigma^c at eps itself), by
+ *   the same secant from eps_n; for core levels it has several solutions (Sec. "Satellites in the
+ *   G0W0 approximation") and the secant returns the one it reaches — gwc_g0w0_solutions lists all
+ *   of them on a grid. dH is still returned. */
+typedef enum { GWC_QP_SECANT = 0, GWC_QP_HEDIN = 1, GWC_QP_G0W0 = 2 } gwc_qp_mode;
 
 typedef struct {
   long long chi0_builds;     /* polarizability builds launched (one per frequency)            */
@@ -188,6 +192,20 @@ gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, vo
  *   (DIAG decoupled Im Sigma from the fitted W^c_nn) or NULL. Allocates scratch; synchronises `stream`. */
 gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
                               double* sigma_c, double* im_sigma_dec, void* stream);
+
+/* Graphical solutions of the plain G0W0 QP equation (eq quasiparticle_equation; Sec. "Satellites
+ * in the G0W0 approximation": for 1s levels the equation has several solutions). On the ascending
+ * grid omega, f(w) = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n(w) - w; a grid point with f = 0 is a
+ * root; where f changes sign between w_j and w_{j+1} the root is the linear interpolant, and each
+ * root carries Z = 1/(1 - dRe Sigma^c/dw) from the slope over that interval. A crossing of a pole
+ * of Re Sigma^c appears with Z < 0; the quasiparticle-like solutions have 0 < Z < 1.
+ *   omega  : DEVICE [n_omega] ascending absolute frequencies (Ha)
+ *   sigma_c: DEVICE [n_core][n_omega][2] (as gwc_sigma_core returns it on that grid)
+ *   roots  : DEVICE [n_core][max_roots][2] = (w*, Z), ascending in w*
+ *   n_roots: DEVICE [n_core] number of roots found (only the first max_roots are stored)
+ * Asynchronous on `stream`; INVALID_ARG for n_omega < 2 or max_roots < 1. */
+gwc_status gwc_g0w0_solutions(gwc_ctx* ctx, const double* omega, int n_omega, const double* sigma_c, int max_roots,
+                              double* roots, int* n_roots, void* stream);
 
 /* G_dH W0 spectral function beside GW+C (Sec. "G0W0 approximation": eqs gw_full_propagator,
  * A_definition, A_explicit_real_imaginary, with the shifted self-energy of eq hedin_sigma_spectral):

@@ -21,7 +21,9 @@ Readings taken where the paper is silent (all listed in the design notes):
   * Sigma^x runs over occupied m only.
   * The imaginary-axis integral uses a modified Gauss-Legendre grid
     xi = xi0 (1+x)/(1-x) with analytic subtraction of W^c(i0).
-  * The G_dH W0 quasiparticle equation is solved by the secant method from eps_n.
+  * The G_dH W0 quasiparticle equation is solved by the secant method from eps_n; so is the
+    plain G0W0 equation, whose several solutions are also listed by a sign-change scan of the
+    equation on a frequency grid (linear interpolation, Z from the local slope).
   * v^xc defaults to Sigma^x (zero static shift) when not given.
 """
 from __future__ import annotations
@@ -242,10 +244,13 @@ class System:
             out[c] = self.sigma_c_core(c, float(self.eps[n])).real + sx[c] - vxc[c]
         return out
 
-    def qp_solve(self, tol=1e-7, max_iter=50, cores=None):
+    def qp_solve(self, tol=1e-7, max_iter=50, cores=None, mode="gdh"):
         """Solve eps = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n(eps - dH_n) by the secant method
         from eps_n (G_dH W0 QP equation). Returns (eps_qp, dH, iterations); with `cores` given
-        only those cores are solved (the other entries are NaN / 0)."""
+        only those cores are solved (the other entries are NaN / 0).
+
+        mode "g0w0": the plain G0W0 QP equation of Eq. quasiparticle_equation, Sigma^c evaluated at
+        eps itself (no shift); the same secant from eps_n, dH still reported."""
         sx, vxc = self.sigma_x(), self.v_xc()
         todo = range(self.n_core) if cores is None else list(cores)
         dh = np.full(self.n_core, np.nan)
@@ -258,8 +263,10 @@ class System:
             n = self.core_idx[c]
             e_n = float(self.eps[n])
 
+            shift = 0.0 if mode == "g0w0" else dh[c]
+
             def g(e):
-                return e_n + sx[c] - vxc[c] + self.sigma_c_core(c, e - dh[c]).real - e
+                return e_n + sx[c] - vxc[c] + self.sigma_c_core(c, e - shift).real - e
 
             x0 = e_n
             g0 = g(x0)
@@ -280,6 +287,33 @@ class System:
             eqp[c] = x1
             iters[c] = it
         return eqp, dh, iters
+
+
+def g0w0_graphical_solutions(omega: np.ndarray, sigma_c: np.ndarray, eps_n: float, sigma_x: float, vxc: float):
+    """All solutions of the plain G0W0 QP equation (Eq. quasiparticle_equation) on a grid — the
+    "graphical solution" of Sec. "Satellites in the G0W0 approximation", which for core levels has
+    several roots. With f(w) = eps_n + Sigma^x - v^xc + Re Sigma^c(w) - w on the ascending grid
+    omega (sigma_c complex on the same grid): a grid point with f = 0 is a root; between points j
+    and j+1 with f_j f_{j+1} < 0 the root is the linear interpolant
+        w* = w_j - f_j (w_{j+1} - w_j) / (f_{j+1} - f_j),
+    and its renormalisation factor is Z = 1 / (1 - dRe Sigma/dw) with the slope of Re Sigma^c over
+    that interval (at a grid root: over the interval to its right, or to its left at the end).
+    Returns a list of (w*, Z) in ascending w*."""
+    w = np.asarray(omega, dtype=np.float64)
+    rs = np.asarray(sigma_c).real.astype(np.float64)
+    f = eps_n + sigma_x - vxc + rs - w
+    out = []
+    n = w.size
+    for j in range(n):
+        if f[j] == 0.0:
+            k = j if j + 1 < n else j - 1
+            slope = (rs[k + 1] - rs[k]) / (w[k + 1] - w[k])
+            out.append((float(w[j]), float(1.0 / (1.0 - slope))))
+        elif j + 1 < n and f[j] * f[j + 1] < 0.0:
+            ws = w[j] - f[j] * (w[j + 1] - w[j]) / (f[j + 1] - f[j])
+            slope = (rs[j + 1] - rs[j]) / (w[j + 1] - w[j])
+            out.append((float(ws), float(1.0 / (1.0 - slope))))
+    return out
 
 
 # ----------------------------------------------------------------------------------------

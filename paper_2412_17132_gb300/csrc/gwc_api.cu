@@ -197,7 +197,7 @@ gwc_status validate_options(const gwc_options* o, int n_core) {
   if (o->max_qp_iter < 2 || o->max_qp_iter > 200) return fail(nullptr, GWC_ERR_INVALID_ARG, "max_qp_iter must be in 2..200");
   if (!(o->qp_tol > 0.0)) return fail(nullptr, GWC_ERR_INVALID_ARG, "qp_tol must be > 0");
   if (o->batch < 0 || o->batch > 4096) return fail(nullptr, GWC_ERR_INVALID_ARG, "batch must be in 0..4096");
-  if (o->qp_mode < 0 || o->qp_mode > 1) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad qp_mode");
+  if (o->qp_mode < 0 || o->qp_mode > 2) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad qp_mode");
   (void)n_core;
   return GWC_OK;
 }
@@ -458,8 +458,8 @@ gwc_status enqueue_qp(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, bool
     TRY(residue_batches(ctx, np, ctx->d_qp_z, ctx->d_qp_rowmap, 1, ctx->d_qp_w, ctx->d_qp_active, st));
     LAUNCH(launch_qp_assemble_update(ctx->d_eps, ctx->n_states, no, nc, ctx->d_core_idx, ctx->eps_f, ctx->d_xi,
                                      ctx->d_wxi, ctx->opt.n_im, ctx->d_wim, ctx->d_qp_w, ctx->d_qp_fac, ctx->d_sx,
-                                     ctx->d_vxc_eff, ctx->opt.qp_tol, ctx->opt.max_qp_iter, ctx->d_qp, ctx->d_all_done,
-                                     st));
+                                     ctx->d_vxc_eff, ctx->opt.qp_tol, ctx->opt.max_qp_iter,
+                                     ctx->opt.qp_mode == GWC_QP_G0W0 ? 1 : 0, ctx->d_qp, ctx->d_all_done, st));
     if (poll && (r & 3) == 3) {
       int done = 0;
       CU(cudaMemcpyAsync(&done, ctx->d_all_done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -962,6 +962,17 @@ gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, in
   release();
   if (res != GWC_OK) return res;
   return check_stream_error(ctx);
+}
+
+gwc_status gwc_g0w0_solutions(gwc_ctx* ctx, const double* omega, int n_omega, const double* sigma_c, int max_roots,
+                              double* roots, int* n_roots, void* stream) {
+  if (!ctx) return GWC_ERR_INVALID_ARG;
+  if (!omega || !sigma_c || !roots || !n_roots || n_omega < 2 || max_roots < 1)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "g0w0_solutions: null pointer, n_omega < 2 or max_roots < 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  LAUNCH(launch_g0w0_scan(omega, n_omega, sigma_c, ctx->d_eps, ctx->d_core_idx, ctx->d_sx, ctx->d_vxc_eff, ctx->n_core,
+                          max_roots, roots, n_roots, st));
+  return GWC_OK;
 }
 
 gwc_status gwc_gdh_spectrum(gwc_ctx* ctx, const double* omega, int n_omega, const double* sigma_c, const double* dh,

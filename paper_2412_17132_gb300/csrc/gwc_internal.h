@@ -169,8 +169,13 @@ int launch_qp_pairs(const double* eps, const int* core_idx, int n_core, int n_oc
 int launch_qp_assemble_update(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx,
                               double eps_f, const double* xi, const double* wxi, int n_im, const double* wim,
                               const double* wpair /*[n_core*n_occ][2]*/, const double* fac, const double* sx,
-                              const double* vxc, double tol, int max_iter, QpState* st, int* all_done,
+                              const double* vxc, double tol, int max_iter, int g0w0, QpState* st, int* all_done,
                               cudaStream_t s);
+// Graphical solutions of the plain G0W0 QP equation on a grid: roots [n_core][max_roots][2] = (w, Z),
+// n_roots [n_core] = number found (may exceed max_roots; only the first max_roots stored).
+int launch_g0w0_scan(const double* omega, int n_w, const double* sigma, const double* eps, const int* core_idx,
+                     const double* sx, const double* vxc, int n_core, int max_roots, double* roots, int* n_roots,
+                     cudaStream_t s);
 int launch_qp_finish(const QpState* st, int n_core, double* eps_qp, double* dh, int* iters, unsigned* status,
                      cudaStream_t s);
 // eps_qp = eps_n + dH_n after the phase-0 round (closed form of the G_dH W0 QP equation)

@@ -87,6 +87,8 @@ __global__ void sigma_grid_kernel(const double* __restrict__ eps, int n_states, 
 // hedin_sigma_spectral) by the secant method from eps_n. Phases of the per-core state machine:
 //   0: evaluate Sigma at eps_n -> dH;  1: g(x0), x1 = x0 + g0;  2: g(x1), secant step;
 //   3: final g(x1) after a step below tolerance;  done.
+// With g0w0 set, the plain G0W0 equation (Eq. quasiparticle_equation, Sigma^c at eps itself): the
+// phase-0 evaluation at eps_n already is g(x0) = dH_n, so phase 1 is skipped.
 // ---------------------------------------------------------------------------------------------
 
 __global__ void qp_init_kernel(const double* __restrict__ eps, const int* __restrict__ core_idx, int n_core,
@@ -125,7 +127,7 @@ __global__ void qp_update_kernel(const double* __restrict__ eps, int n_states, i
                                  const double* __restrict__ wxi, int n_im, const double* __restrict__ wim,
                                  const double* __restrict__ wpair, const double* __restrict__ fac,
                                  const double* __restrict__ sx, const double* __restrict__ vxc, double tol, int max_iter,
-                                 QpState* __restrict__ st, const int* __restrict__ all_done) {
+                                 int g0w0, QpState* __restrict__ st, const int* __restrict__ all_done) {
   if (*all_done) return;
   const int c = blockIdx.x;
   const int lane = threadIdx.x;
@@ -154,8 +156,16 @@ __global__ void qp_update_kernel(const double* __restrict__ eps, int n_states, i
     case 0: {
       s.dh = re_sigma + stat;
       s.x0 = e_n;
-      s.w_eval = s.x0 - s.dh;
-      s.phase = 1;
+      if (g0w0) {
+        s.g0 = s.dh;  // e_n + stat + Re Sigma(e_n) - e_n
+        s.x1 = s.x0 + s.g0;
+        s.it = 1;
+        s.w_eval = s.x1;
+        s.phase = 2;
+      } else {
+        s.w_eval = s.x0 - s.dh;
+        s.phase = 1;
+      }
       break;
     }
     case 1: {
@@ -178,7 +188,7 @@ __global__ void qp_update_kernel(const double* __restrict__ eps, int n_states, i
       s.x0 = s.x1;
       s.g0 = s.g1;
       s.x1 = x2;
-      s.w_eval = s.x1 - s.dh;
+      s.w_eval = g0w0 ? s.x1 : s.x1 - s.dh;
       if (fabs(s.x1 - s.x0) < tol) s.phase = 3;
       break;
     }
@@ -365,6 +375,57 @@ int launch_gdh_spectrum(const double* eps, const int* core_idx, int n_core, cons
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+// Graphical solutions of the plain G0W0 QP equation (Eq. quasiparticle_equation) on a grid:
+// f(w) = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n(w) - w; a grid point with f = 0 is a root; a sign
+// change between j and j+1 gives the linear interpolant w* = w_j - f_j (w_{j+1} - w_j)/(f_{j+1} - f_j)
+// with Z = 1/(1 - dRe Sigma/dw) from the slope over that interval. One block per core; lane 0 scans
+// the grid in order so the roots come out ascending. n_roots = all roots found (only the first
+// max_roots are stored).
+__global__ void g0w0_scan_kernel(const double* __restrict__ omega, int n_w, const double* __restrict__ sigma,
+                                 const double* __restrict__ eps, const int* __restrict__ core_idx,
+                                 const double* __restrict__ sx, const double* __restrict__ vxc, int max_roots,
+                                 double* __restrict__ roots, int* __restrict__ n_roots) {
+  const int c = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  const double* sg = sigma + (size_t)c * n_w * 2;
+  const double base = eps[core_idx[c]] + sx[c] - vxc[c];
+  double* out = roots + (size_t)c * max_roots * 2;
+  int k = 0;
+  for (int j = 0; j < n_w; ++j) {
+    const double fj = base + sg[2 * j] - omega[j];
+    double ws = 0.0, slope = 0.0;
+    bool root = false;
+    if (fj == 0.0) {
+      const int a = j + 1 < n_w ? j : j - 1;
+      slope = (sg[2 * (a + 1)] - sg[2 * a]) / (omega[a + 1] - omega[a]);
+      ws = omega[j];
+      root = n_w > 1;
+    } else if (j + 1 < n_w) {
+      const double fk = base + sg[2 * (j + 1)] - omega[j + 1];
+      if (fj * fk < 0.0) {
+        ws = omega[j] - fj * (omega[j + 1] - omega[j]) / (fk - fj);
+        slope = (sg[2 * (j + 1)] - sg[2 * j]) / (omega[j + 1] - omega[j]);
+        root = true;
+      }
+    }
+    if (root) {
+      if (k < max_roots) {
+        out[2 * k] = ws;
+        out[2 * k + 1] = 1.0 / (1.0 - slope);
+      }
+      ++k;
+    }
+  }
+  n_roots[c] = k;
+}
+
+int launch_g0w0_scan(const double* omega, int n_w, const double* sigma, const double* eps, const int* core_idx,
+                     const double* sx, const double* vxc, int n_core, int max_roots, double* roots, int* n_roots,
+                     cudaStream_t s) {
+  g0w0_scan_kernel<<<n_core, 32, 0, s>>>(omega, n_w, sigma, eps, core_idx, sx, vxc, max_roots, roots, n_roots);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 int launch_qp_finish_hedin(const QpState* st, const double* eps, const int* core_idx, int n_core, double* eps_qp,
                            double* dh, int* iters, cudaStream_t s) {
   qp_finish_hedin_kernel<<<(n_core + 63) / 64, 64, 0, s>>>(st, eps, core_idx, n_core, eps_qp, dh, iters);
@@ -404,9 +465,9 @@ int launch_qp_pairs(const double* eps, const int* core_idx, int n_core, int n_oc
 int launch_qp_assemble_update(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx, double eps_f,
                               const double* xi, const double* wxi, int n_im, const double* wim, const double* wpair,
                               const double* fac, const double* sx, const double* vxc, double tol, int max_iter,
-                              QpState* st, int* all_done, cudaStream_t s) {
+                              int g0w0, QpState* st, int* all_done, cudaStream_t s) {
   qp_update_kernel<<<n_core, 32, 0, s>>>(eps, n_states, n_occ, n_core, core_idx, eps_f, xi, wxi, n_im, wim, wpair, fac,
-                                         sx, vxc, tol, max_iter, st, all_done);
+                                         sx, vxc, tol, max_iter, g0w0, st, all_done);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

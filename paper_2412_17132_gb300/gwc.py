@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libgwc.so")
 
 PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "fp32": 3}
 DEC = {"none": 0, "diag": 1, "group": 2}
-QP = {"secant": 0, "hedin": 1}
+QP = {"secant": 0, "hedin": 1, "g0w0": 2}
 STATUS = {
     0: "ok",
     1: "invalid argument",
@@ -112,6 +112,8 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_gdh_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_g0w0_solutions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_request_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "gwc_request_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_request_copy_results": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_void_p]),
@@ -335,6 +337,18 @@ class Context:
         _check(lib().gwc_gdh_spectrum(self._ctx, _ptr(omega), nw, _ptr(sigma_c), _ptr(dh), _ptr(a), _ptr(w),
                                       _stream(stream)), self._ctx)
         return a, w
+
+    def g0w0_solutions(self, omega, sigma_c, max_roots=32, stream=None):
+        """All grid solutions of the plain G0W0 QP equation per core: (roots [n_core][max_roots][2] =
+        (w, Z), counts [n_core]) from Sigma^c on the ascending grid omega (CUDA tensors)."""
+        import torch
+
+        nw = int(omega.shape[0])
+        roots = torch.zeros((self.n_core, max_roots, 2), dtype=torch.float64, device="cuda")
+        cnt = torch.zeros((self.n_core,), dtype=torch.int32, device="cuda")
+        _check(lib().gwc_g0w0_solutions(self._ctx, _ptr(omega), nw, _ptr(sigma_c), max_roots, _ptr(roots), _ptr(cnt),
+                                        _stream(stream)), self._ctx)
+        return roots, cnt
 
     # -- request mode (decoupled spectra + QP as one capturable step) -------------------------
     def request_plan(self, omega_rel, stream=None):

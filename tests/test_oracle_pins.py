@@ -478,3 +478,43 @@ def test_cdwac_equals_cd_when_w_has_few_poles():
     wac = G.sigma_c_wac(s, m.omega, xref)
     cd = np.array([s.sigma_c(float(w))[0] for w in m.omega]).T
     assert np.max(np.abs(wac - cd)) < 1e-7 * max(1.0, np.max(np.abs(cd)))
+
+
+# ---- plain G0W0 QP equation: several solutions (Sec. "Satellites in the G0W0 approximation") -----
+def test_g0w0_graphical_solutions_single_pole_closed_form():
+    """Re Sigma(w) = rho^2 (w - p) / ((w - p)^2 + eta^2) (one pole, eta far below the grid step): the
+    G0W0 equation eps + Re Sigma(w) = w has the two closed-form solutions
+    w = [(eps + p) +- sqrt((eps - p)^2 + 4 rho^2)] / 2 with Z = 1 / (1 + rho^2 / (w - p)^2), whose Z sum
+    to 1; the crossing of the pole itself comes out with Z < 0."""
+    eps, p, rho2, eta = -10.0, -11.0, 0.1, 1e-6
+    w = np.linspace(-12.0, -9.0, 30001)
+    re = rho2 * (w - p) / ((w - p) ** 2 + eta ** 2)
+    roots = G.g0w0_graphical_solutions(w, re + 0j, eps, 0.0, 0.0)
+    phys = [(x, z) for x, z in roots if z > 0]
+    assert len(phys) == 2 and len(roots) == 3
+    s = math.sqrt((eps - p) ** 2 + 4 * rho2)
+    exact = sorted([((eps + p) - s) / 2, ((eps + p) + s) / 2])
+    for (x, z), xe in zip(phys, exact):
+        ze = 1.0 / (1.0 + rho2 / (xe - p) ** 2)
+        assert abs(x - xe) < 1e-7, (x, xe)
+        assert abs(z - ze) < 5e-3 * ze, (z, ze)
+    assert abs(sum(1.0 / (1.0 + rho2 / (xe - p) ** 2) for xe in exact) - 1.0) < 1e-12
+    pole = [x for x, z in roots if z < 0]
+    assert len(pole) == 1 and abs(pole[0] - p) < 2e-4
+
+
+def test_g0w0_secant_root_is_a_graphical_solution():
+    """The secant solution of the plain G0W0 equation satisfies it and lies within one grid step of
+    a graphical solution with Z > 0 (a small system, 201-point grid around the core level)."""
+    m = synth.small(n_states=20, n_occ=5, n_core=1, n_aux=14, seed=9)
+    s = G.System.from_molecule(m)
+    eqp, dh, it = s.qp_solve(mode="g0w0")
+    sx, vxc = s.sigma_x(), s.v_xc()
+    e_n = float(m.eps[m.core_idx[0]])
+    resid = e_n + sx[0] - vxc[0] + s.sigma_c_core(0, float(eqp[0])).real - eqp[0]
+    assert abs(resid) < 1e-6
+    grid = np.linspace(min(e_n, eqp[0]) - 0.5, max(e_n, eqp[0]) + 0.5, 201)
+    sig, _ = s.sigma_c_grid(grid)
+    roots = G.g0w0_graphical_solutions(grid, sig[0], e_n, sx[0], vxc[0])
+    step = grid[1] - grid[0]
+    assert any(z > 0 and abs(x - eqp[0]) < step for x, z in roots), (eqp[0], roots)
