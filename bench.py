@@ -522,10 +522,18 @@ def run_pentacene(args):
             "cores": gold["cores"],
             "dH_err_eV": {p: [float((res[p]["dh"][c] - gold["dH"][k]) * HARTREE_EV) for k, c in enumerate(gold["cores"])]
                           for p in res if res[p]["dh"] is not None},
-            "sigma_err_Ha_max": {p: float(max(np.max(np.abs(res[p]["sig"][:, j, 0] + 1j * res[p]["sig"][:, j, 1]
-                                                         - np.array([complex(*v) for v in gold["points"][j]["sigma_c"]])))
-                                             for j in range(res[p]["sig"].shape[1]))) for p in res},
         }
+        # Sigma at the grid points both the run and the oracle file have (matched by grid index)
+        errs = {}
+        for p in res:
+            e = []
+            for j, gi in enumerate(pts_idx[: res[p]["sig"].shape[1]]):
+                if gi in gold.get("omega_idx", []):
+                    ref = np.array([complex(*v) for v in gold["points"][gold["omega_idx"].index(gi)]["sigma_c"]])
+                    e.append(float(np.max(np.abs(res[p]["sig"][:, j, 0] + 1j * res[p]["sig"][:, j, 1] - ref))))
+            if e:
+                errs[p] = max(e)
+        out["vs_oracle"]["sigma_err_Ha_max"] = errs
     print(json.dumps(out), flush=True)
     return 0
 
