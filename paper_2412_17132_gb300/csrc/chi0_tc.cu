@@ -43,7 +43,23 @@ constexpr int NA_ST = 3;                   // scaled-A slots (one part each)
 constexpr int TILE = BM * BK * 2;          // 16 KB: one BF16 128 x 64 operand tile
 constexpr int RAW = BM * BK * 4;           // 32 KB: FP32 128 x 64 rows (two 128-B swizzled halves)
 constexpr int DSL = kParts * BK * 4;       // 512 B: D slices of one chunk
-constexpr int NTHREADS = 512;              // warp 0 TMA, 1 MMA, 2 TMEM, 4-11 transform, 12-15 fold
+constexpr int NTHREADS = 512;              // warp 0 TMA, 1 MMA, 2 TMEM then transform, 12-15 fold
+// Transform warps: none on the MMA warp's scheduler (warp % 4 == 1). A single issuing thread
+// shares its sub-partition's issue slots with the warps there, and ALU-heavy neighbours starve
+// it (measured: 322 instead of 64 cycles per 128x128x16 MMA beside two FMA-bound warps).
+__device__ __forceinline__ int transform_rank(int warp) {
+  switch (warp) {
+    case 2: return 0;
+    case 3: return 1;
+    case 4: return 2;
+    case 6: return 3;
+    case 7: return 4;
+    case 8: return 5;
+    case 10: return 6;
+    case 11: return 7;
+    default: return -1;
+  }
+}
 constexpr int NXF = 256;                   // transform threads (two per row of the P tile)
 constexpr int NFOLD = 128;                 // fold threads
 constexpr int SMEM_BYTES = 1024 + NB_ST * 2 * TILE + NB_ST * RAW + NA_ST * 2 * TILE + NB_ST * DSL + 256;
@@ -189,6 +205,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       int a = 0;
       bool ok = true;
+      const bool split3 = p.split3 != 0;
       for (int kc = 0; kc < p.n_kc && ok; ++kc) {
         const int s = kc % NB_ST, u = kc / NB_ST;
         if (!mbar_wait(smem_u32(&b_full[s]), u & 1, abort_flag)) {
@@ -207,14 +224,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tc_fence_after();
           const uint32_t ah = smem_u32(a_ring + t * 2 * TILE), al = ah + TILE;
           const uint32_t d = tmem_base + (uint32_t)(part * BN);  // fresh accumulator of this part
+          // descriptors once; a k step moves the start address by 32 bytes = 2 units of the
+          // 16-byte address field (few instructions per MMA for the issuing thread)
+          const uint64_t dah = sdesc(ah), dal = sdesc(al), dbh = sdesc(bh), dbl = sdesc(bl);
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
-            const uint32_t off = k * 32;  // 16 BF16 = 32 bytes along K inside the 128-B row
+            const uint64_t o = 2u * k;  // 16 BF16 = 32 bytes along K inside the 128-B row
             const uint32_t acc = (seg_start && k == 0) ? 0u : 1u;
-            mma_bf16(d, sdesc(ah + off), sdesc(bh + off), acc);
-            if (p.split3) {
-              mma_bf16(d, sdesc(ah + off), sdesc(bl + off), 1u);
-              mma_bf16(d, sdesc(al + off), sdesc(bh + off), 1u);
+            mma_bf16(d, dah + o, dbh + o, acc);
+            if (split3) {
+              mma_bf16(d, dah + o, dbl + o, 1u);
+              mma_bf16(d, dal + o, dbh + o, 1u);
             }
           }
           mma_commit(smem_u32(&a_empty[t]));
@@ -235,9 +255,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       mma_commit(smem_u32(mma_done));  // fires when every MMA issued above has completed
     }
-  } else if (warp >= 4 && warp < 12) {
+  } else if (transform_rank(warp) >= 0) {
     // ---------------- transform: A = O[P][k] D_p(k), split into BF16 hi / lo -------------------
-    const int tt = threadIdx.x - 128;
+    const int tt = 32 * transform_rank(warp) + lane;
     const int r = tt & 127, h = tt >> 7;  // row of the P tile, half of the 64-wide chunk
     int a = 0;
     for (int kc = 0; kc < p.n_kc; ++kc) {
