@@ -255,12 +255,16 @@ __device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, in
         const uint32_t ar = ah, ai = ah + A_PLANE, arl = ah + 2 * A_PLANE, ail = ah + 3 * A_PLANE;
         const uint32_t bb = abase + A_BYTES + s * B_STAGE;
         const uint32_t br = bb, bi = bb + B_PLANE, brl = bb + 2 * B_PLANE, bil = bb + 3 * B_PLANE;
+        // descriptors once per stage; a k step moves the start address by 32 bytes = 2 units of the
+        // 16-byte address field (few instructions per MMA for the issuing thread)
+        const uint64_t dar = sdesc(ar), dai = sdesc(ai), darl = sdesc(arl), dail = sdesc(ail);
+        const uint64_t dbr = sdesc(br), dbi = sdesc(bi), dbrl = sdesc(brl), dbil = sdesc(bil);
 #pragma unroll
         for (int k = 0; k < KH / 8; ++k) {
-          const uint32_t off = k * 32;  // 8 TF32 values = 32 bytes along K inside the 128-B row
+          const uint64_t o = 2u * k;  // 8 TF32 values = 32 bytes along K inside the 128-B row
           const uint32_t acc = (h == 0 && k == 0) ? 0u : 1u;
-          const uint64_t a_r = sdesc(ar + off), a_i = sdesc(ai + off), a_rl = sdesc(arl + off), a_il = sdesc(ail + off);
-          const uint64_t b_r = sdesc(br + off), b_i = sdesc(bi + off), b_rl = sdesc(brl + off), b_il = sdesc(bil + off);
+          const uint64_t a_r = dar + o, a_i = dai + o, a_rl = darl + o, a_il = dail + o;
+          const uint64_t b_r = dbr + o, b_i = dbi + o, b_rl = dbrl + o, b_il = dbil + o;
           // hi * hi
           mma_tf32<kIdescTf32>(d1r, a_r, b_r, acc);
           mma_tf32<kIdescTf32NegA>(d1r, a_i, b_i, 1u);
