@@ -7,16 +7,14 @@
 //   C[i][j] -= sum_l W[i][l] L[j][l],   l in the panel, i >= j beyond the panel.
 //
 // Complex products as real GEMMs over split planes. With A = W rows (Ar, Ai) and B = L rows
-// (Lr, Li), one accumulator of 128 columns holds Re (columns 0-63) and Im (64-127) of a
-// 128 x 64 complex tile, each half an N = 64 product:
-//     Re += Ar Lr^T - Ai Li^T   (the minus from the instruction's negate-A bit),
-//     Im += Ar Li^T + Ai Lr^T.
+// (Lr, Li) stored as the 128-row window [Lr ; Li], two accumulators of N = 128 columns take
+//     P = Ar [Lr ; Li]^T = [Ar Lr^T | Ar Li^T],   Q = Ai [Lr ; Li]^T = [Ai Lr^T | Ai Li^T],
+// and the epilogue forms Re = Ar Lr^T - Ai Li^T and Im = Ar Li^T + Ai Lr^T from them (N = 128 MMAs
+// run at full rate; N = 64 ones at about 60 %).
 //
 // FP32 accuracy from TF32 operands (kind::tf32): every value v is split into hi = tf32(v) and
-// lo = tf32(v - hi) (3xTF32; Henry, Tang & Heinecke 2019 for the BF16 analogue), and the tile is
-// D1 = hi*hi (one accumulator) plus D2 = hi*lo + lo*hi (a second one), so the truncating
-// accumulator of the tensor core adds only 16 large partial products into D1 per panel; the
-// epilogue forms C - D1 - D2 in round-to-nearest FP32.
+// lo = tf32(v - hi) (3xTF32; Henry, Tang & Heinecke 2019 for the BF16 analogue): each accumulator
+// takes hi*hi + hi*lo + lo*hi, and the epilogue forms C - (P and Q terms) in round-to-nearest FP32.
 //
 // Roles (416 threads, one CTA per matrix):
 //   warps 0-11  panel factorisation (the shared SIMT routine, named barrier 1)
@@ -57,19 +55,16 @@ static_assert(PW == 2 * KH, "one panel is two stages");
 constexpr int NT_PANEL = 384;                            // warps 0-11 factor the panels
 static_assert(PanelSmem<float2, NT_PANEL>::bytes() <= (size_t)OPS_BYTES, "panel scratch fits in the operand buffers");
 
-// kind::tf32 instruction descriptors: D = F32, A = B = TF32, both K-major, N = TN, M = TM;
-// the second negates A (bit 13).
+// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, N = 2 TN, M = TM.
 constexpr uint32_t kIdescTf32 =
-    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-constexpr uint32_t kIdescTf32NegA = kIdescTf32 | (1u << 13);
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(2 * TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
-template <uint32_t IDESC>
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "n"(IDESC), "r"(accum));
+      "l"(a), "l"(b), "n"(kIdescTf32), "r"(accum));
 }
 
 // round to the nearest TF32 value (10 explicit mantissa bits), kept in an FP32 container
@@ -242,8 +237,7 @@ __device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, in
         break;
       }
       tc_fence_after();
-      const uint32_t d1 = tmem_base + (uint32_t)(b * 256), d2 = d1 + 128;
-      const uint32_t d1r = d1, d1i = d1 + TN, d2r = d2, d2i = d2 + TN;  // Re | Im column halves
+      const uint32_t dp = tmem_base + (uint32_t)(b * 256), dq = dp + 128;  // P and Q accumulators
       for (int h = 0; h < 2; ++h, ++seq) {
         const int s = seq & 1, us = seq >> 1;
         if (!mbar_wait(smem_u32(&sm.b_full[s]), us & 1, sm.abort_flag)) {
@@ -264,21 +258,13 @@ __device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, in
           const uint64_t o = 2u * k;  // 8 TF32 values = 32 bytes along K inside the 128-B row
           const uint32_t acc = (h == 0 && k == 0) ? 0u : 1u;
           const uint64_t a_r = dar + o, a_i = dai + o, a_rl = darl + o, a_il = dail + o;
-          const uint64_t b_r = dbr + o, b_i = dbi + o, b_rl = dbrl + o, b_il = dbil + o;
-          // hi * hi
-          mma_tf32<kIdescTf32>(d1r, a_r, b_r, acc);
-          mma_tf32<kIdescTf32NegA>(d1r, a_i, b_i, 1u);
-          mma_tf32<kIdescTf32>(d1i, a_r, b_i, acc);
-          mma_tf32<kIdescTf32>(d1i, a_i, b_r, 1u);
-          // hi * lo + lo * hi
-          mma_tf32<kIdescTf32>(d2r, a_r, b_rl, acc);
-          mma_tf32<kIdescTf32>(d2r, a_rl, b_r, 1u);
-          mma_tf32<kIdescTf32NegA>(d2r, a_i, b_il, 1u);
-          mma_tf32<kIdescTf32NegA>(d2r, a_il, b_i, 1u);
-          mma_tf32<kIdescTf32>(d2i, a_r, b_il, acc);
-          mma_tf32<kIdescTf32>(d2i, a_rl, b_i, 1u);
-          mma_tf32<kIdescTf32>(d2i, a_i, b_rl, 1u);
-          mma_tf32<kIdescTf32>(d2i, a_il, b_r, 1u);
+          const uint64_t bh = dbr + o, bl = dbrl + o;  // [Lr ; Li] hi and lo windows (N = 128)
+          mma_tf32(dp, a_r, bh, acc);
+          mma_tf32(dp, a_r, bl, 1u);
+          mma_tf32(dp, a_rl, bh, 1u);
+          mma_tf32(dq, a_i, bh, acc);
+          mma_tf32(dq, a_i, bl, 1u);
+          mma_tf32(dq, a_il, bh, 1u);
         }
         mma_commit(smem_u32(&sm.b_empty[s]));
       }
@@ -385,19 +371,20 @@ __device__ void epilogue_role(const TcSmem& sm, uint32_t tmem_base, float2* __re
             cur[e] = make_float4(u.x, u.y, v.x, v.y);
           }
         }
-        // Re parts (accumulator columns 16 cc .. of D1 and D2), then Im parts (64 columns on)
+        // Re = Ar Lr^T - Ai Li^T: P columns 16 cc.., Q columns 64 + 16 cc..
         const uint32_t col = lane_base + (uint32_t)(b * 256 + 16 * cc);
         uint32_t t1[16], t2[16];
         tmem_ld16_nw(col, t1);
-        tmem_ld16_nw(col + 128, t2);
+        tmem_ld16_nw(col + 128 + 64, t2);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          cur[e].x = cur[e].x - __uint_as_float(t1[2 * e]) - __uint_as_float(t2[2 * e]);
-          cur[e].z = cur[e].z - __uint_as_float(t1[2 * e + 1]) - __uint_as_float(t2[2 * e + 1]);
+          cur[e].x = cur[e].x - __uint_as_float(t1[2 * e]) + __uint_as_float(t2[2 * e]);
+          cur[e].z = cur[e].z - __uint_as_float(t1[2 * e + 1]) + __uint_as_float(t2[2 * e + 1]);
         }
+        // Im = Ar Li^T + Ai Lr^T: P columns 64 + 16 cc.., Q columns 16 cc..
         tmem_ld16_nw(col + 64, t1);
-        tmem_ld16_nw(col + 192, t2);
+        tmem_ld16_nw(col + 128, t2);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
