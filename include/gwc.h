@@ -135,7 +135,10 @@ gwc_status gwc_workspace_bytes(const gwc_system* sys, const gwc_options* opt, in
 /* Creates a context on the current device: validates, allocates, copies the system
  * (host->device if memory == GWC_MEM_HOST), builds the resident precision copies of
  * O_ov (BF16 hi/lo and FP32), and computes the imaginary-axis grid. Enqueued on
- * `stream`; gwc_create synchronises that stream once before returning. */
+ * `stream`; gwc_create synchronises that stream once before returning.
+ * In the BF16 and BF16X3 modes the complex dielectric matrices are factored by the tensor-core
+ * kernel (3xTF32 trailing updates, FP32-accurate); the environment variable GWC_FACTOR=simt,
+ * read here, keeps them on the FP32 SIMT kernel instead (for comparisons). */
 gwc_status gwc_create(gwc_ctx** ctx, const gwc_system* sys, const gwc_options* opt, void* stream);
 
 /* Replaces the system of an existing context by another of the SAME sizes (serving
