@@ -53,7 +53,6 @@ constexpr int OPS_BYTES = A_BYTES + NSTAGE * B_STAGE;    // 192 KB
 constexpr int SMEM_TC = 1024 + OPS_BYTES + META_BYTES;
 static_assert(PW == 2 * KH, "one panel is two stages");
 constexpr int NT_PANEL = 384;                            // warps 0-11 factor the panels
-static_assert(PanelSmem<float2, NT_PANEL>::bytes() <= (size_t)OPS_BYTES, "panel scratch fits in the operand buffers");
 
 // kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, N = 2 TN, M = TM.
 constexpr uint32_t kIdescTf32 =
@@ -83,6 +82,199 @@ __device__ __forceinline__ void split4(const float (&v)[4], float4& hi, float4& 
   }
   hi = make_float4(h[0], h[1], h[2], h[3]);
   lo = make_float4(l[0], l[1], l[2], l[3]);
+}
+
+// ---- panel factorisation (warps 0-11) -----------------------------------------------------------
+// The kb x kb diagonal block (kb <= 64) is factored right-looking by all 384 threads, one barrier per
+// step, and the same kb steps form X = L^-1 of its unit lower factor. Every element (i, c <= i) of
+// the lower triangle is owned by one thread and held in a register: while c > j it is the Schur
+// complement entry, a_ic -= W_ij d_j^-1 W_cj, final after step c - 1 and then published to shared
+// memory as W_ic (d_i on the diagonal); from step c on the same register accumulates
+// X_ic -= l_ij X_jc (c <= j < i, X_jj = 1, l_ij = W_ij / d_j), published after step i - 1. Step j
+// reads only column j of W and row j of X, both published before the barrier that opens it.
+// The rows below then need no dependent chain: W_rows = A_rows X^T (a product over the panel
+// columns, X^T upper triangular) and L^T_rows = (W_rows D^-1)^T.
+struct PanelInv {
+  static constexpr int LDP = PW + 1;                  // padded row (conflict-free column access)
+  static constexpr int CH = 16 * (NT_PANEL / 32);     // 192 staged rows: 6 blocks of 32 x 2 group pairs
+  float2 (*dm)[LDP];   // [64][65] W below the diagonal, d on it
+  float2 (*xg)[PW];    // [64][64] xg[l][c] = X_cl (zero for c < l), 16-byte rows for broadcast loads
+  float2* dinv;        // [64] 1 / d
+  float2* dpiv;        // [64] d (a zero pivot replaced by 1)
+  float2 (*xr)[LDP];   // [64][65] X by rows while the block is factored ...
+  float2 (*ach)[LDP];  // [CH][65] ... then, aliased, the staged rows below the panel
+  static constexpr size_t bytes() {
+    return sizeof(float2) * ((size_t)PW * LDP + PW * PW + 2 * PW + (size_t)CH * LDP);
+  }
+  __device__ explicit PanelInv(void* base) {
+    float2* p = reinterpret_cast<float2*>(base);
+    dm = reinterpret_cast<float2(*)[LDP]>(p);
+    p += PW * LDP;
+    xg = reinterpret_cast<float2(*)[PW]>(p);
+    p += PW * PW;
+    dinv = p;
+    dpiv = p + PW;
+    p += 2 * PW;
+    xr = reinterpret_cast<float2(*)[LDP]>(p);
+    ach = reinterpret_cast<float2(*)[LDP]>(p);
+  }
+};
+static_assert(PanelInv::bytes() <= (size_t)OPS_BYTES, "panel scratch fits in the operand buffers");
+static_assert(PW * PW <= PanelInv::CH * PanelInv::LDP, "X by rows fits in the staging rows");
+
+__device__ __forceinline__ void panel_sync() { grp_sync_n<NT_PANEL>(); }
+
+// diagonal block [k0, k0 + kb): W / d / L^T stored to A; dinv and xg left in shared memory
+__device__ void factor_diag_block(float2* __restrict__ A, long long ldm, int k0, int kb, const PanelInv& ps,
+                                  int* sing) {
+  constexpr int MAXS = (PW * (PW + 1) / 2 + NT_PANEL - 1) / NT_PANEL;
+  const int tid = threadIdx.x;
+  panel_sync();  // the previous phase's use of the scratch is over
+  for (int e = tid; e < PW * PW; e += NT_PANEL) {
+    const int i = e >> 6, c = e & 63;
+    ps.dm[i][c] = (i < kb && c <= i) ? A[(long long)(k0 + i) * ldm + (k0 + c)] : make_float2(0.f, 0.f);
+    ps.xr[i][c] = make_float2(i == c ? 1.f : 0.f, 0.f);
+  }
+  panel_sync();
+  int si[MAXS], sc[MAXS];
+  float2 v[MAXS];
+  const int tot = kb * (kb + 1) / 2;
+#pragma unroll
+  for (int s = 0; s < MAXS; ++s) {
+    const int e = tid + s * NT_PANEL;
+    int i = -1, c = 0;
+    if (e < tot) {
+      i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while (i * (i + 1) / 2 > e) --i;
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      c = e - i * (i + 1) / 2;
+      v[s] = ps.dm[i][c];
+    } else {
+      v[s] = make_float2(0.f, 0.f);
+    }
+    si[s] = i;
+    sc[s] = c;
+  }
+  for (int j = 0; j < kb; ++j) {
+    float2 d = ps.dm[j][j];
+    const bool zero = fabsf(d.x) + fabsf(d.y) < 1e-30f;
+    if (zero) d = make_float2(1.f, 0.f);
+    const float2 inv = sinv(d);
+    if (tid == 0) {
+      ps.dinv[j] = inv;
+      ps.dpiv[j] = d;
+      if (zero) *sing = 1;
+    }
+#pragma unroll
+    for (int s = 0; s < MAXS; ++s) {
+      const int i = si[s], c = sc[s];
+      if (i > j) {
+        const float2 wij = ps.dm[i][j];
+        if (c > j) {
+          v[s] = sfnms(wij, smul(inv, ps.dm[c][j]), v[s]);
+          if (c == j + 1) ps.dm[i][c] = v[s];
+        } else {
+          if (c == j) v[s] = make_float2(0.f, 0.f);
+          v[s] = sfnms(wij, smul(inv, ps.xr[j][c]), v[s]);
+          if (i == j + 1) ps.xr[i][c] = v[s];
+        }
+      }
+    }
+    panel_sync();
+  }
+  for (int e = tid; e < PW * PW; e += NT_PANEL) {
+    const int l = e >> 6, c = e & 63;
+    ps.xg[l][c] = (c >= l && c < kb) ? ps.xr[c][l] : make_float2(0.f, 0.f);
+  }
+  for (int e = tid; e < kb * kb; e += NT_PANEL) {
+    const int i = e / kb, c = e % kb;
+    if (c < i) {
+      const float2 w = ps.dm[i][c];
+      A[(long long)(k0 + i) * ldm + (k0 + c)] = w;
+      A[(long long)(k0 + c) * ldm + (k0 + i)] = smul(w, ps.dinv[c]);
+    } else if (c == i) {
+      A[(long long)(k0 + i) * ldm + (k0 + i)] = ps.dpiv[i];
+    }
+  }
+  panel_sync();  // xg, dinv complete; xr may be overwritten by the staged rows
+}
+
+// One warp's share of a staged chunk: rows r0 .. r0 + 31 (one per lane), the 16 columns of group g,
+// w_c = sum_{l <= c} a_l X_cl in packed FP32 pairs (re and im of X per product), then W (row-major,
+// lower part) and L^T (transposed, coalesced over the lanes) stored.
+__device__ __forceinline__ void panel_rows_group(float2* __restrict__ A, int n, long long ldm, int k0, int kb,
+                                                 const PanelInv& ps, int r, int i, bool row_ok, int g) {
+  const int lmax = min(16 * g + 16, kb);
+  float2 pr[16], pi[16];  // pr[c] = sum a.re (X re, X im), pi[c] = sum a.im (X re, X im)
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    pr[c] = make_float2(0.f, 0.f);
+    pi[c] = make_float2(0.f, 0.f);
+  }
+  const float2* arow = ps.ach[r];
+#pragma unroll 2
+  for (int l = 0; l < lmax; ++l) {
+    const float2 a = arow[l];
+    const float2 ar = make_float2(a.x, a.x), ai = make_float2(a.y, a.y);
+    const float4* xp = reinterpret_cast<const float4*>(&ps.xg[l][16 * g]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 x = xp[q];
+      const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+      pr[2 * q] = __ffma2_rn(ar, x0, pr[2 * q]);
+      pi[2 * q] = __ffma2_rn(ai, x0, pi[2 * q]);
+      pr[2 * q + 1] = __ffma2_rn(ar, x1, pr[2 * q + 1]);
+      pi[2 * q + 1] = __ffma2_rn(ai, x1, pi[2 * q + 1]);
+    }
+  }
+  if (!row_ok) return;
+  const int cb = 16 * g, ncol = min(16, kb - cb);
+  float2* rowp = A + (long long)i * ldm + k0 + cb;
+  float2 w[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) w[c] = make_float2(pr[c].x - pi[c].y, pr[c].y + pi[c].x);
+  if (ncol == 16) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      *reinterpret_cast<float4*>(rowp + 2 * q) = make_float4(w[2 * q].x, w[2 * q].y, w[2 * q + 1].x, w[2 * q + 1].y);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < ncol) rowp[c] = w[c];
+  }
+  if (i < n) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < ncol) A[(long long)(k0 + cb + c) * ldm + i] = smul(w[c], ps.dinv[cb + c]);
+  }
+}
+
+// Panel [k0, k0 + kb): the diagonal block, then every row below (appended right-hand-side rows
+// n..nrow-1 included, W only) in chunks of CH staged rows; warp w takes the 32-row block w / 2 of a
+// chunk and the column groups {0, 3} or {1, 2} (equal work: the triangle of X).
+__device__ void factor_panel_tc(float2* __restrict__ A, int n, int nrow, long long ldm, int k0, const PanelInv& ps,
+                                int* sing) {
+  const int kb = min(PW, n - k0);
+  factor_diag_block(A, ldm, k0, kb, ps, sing);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int r = 32 * (warp >> 1) + lane;
+  const int g0 = (warp & 1) ? 1 : 0, g1 = (warp & 1) ? 2 : 3;
+  for (int base = k0 + kb; base < nrow; base += PanelInv::CH) {
+    for (int e = tid; e < PanelInv::CH * PW; e += NT_PANEL) {
+      const int rr = e >> 6, l = e & 63, i = base + rr;
+      if (i < nrow && l < kb) cp_async_elem<8>(&ps.ach[rr][l], A + (long long)i * ldm + k0 + l);
+    }
+    cp_commit();
+    cp_wait<0>();
+    panel_sync();
+    const int i = base + r;
+    const bool row_ok = i < nrow;
+    if (base + 32 * (warp >> 1) < nrow) {  // warp-uniform: the block has rows
+      if (16 * g0 < kb) panel_rows_group(A, n, ldm, k0, kb, ps, r, i, row_ok, g0);
+      if (16 * g1 < kb) panel_rows_group(A, n, ldm, k0, kb, ps, r, i, row_ok, g1);
+    }
+    panel_sync();  // the staging rows are free
+  }
 }
 
 // column tiles of row tile tI: j0 = R0 + TN tJ < min(n, i0 + TM)
@@ -428,7 +620,7 @@ __global__ void __launch_bounds__(NT_TC, 1)
   sm.tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
   sm.abort_flag = reinterpret_cast<volatile int*>(sm.tmem_slot + 1);
   sm.sing = reinterpret_cast<int*>(sm.tmem_slot + 2);
-  const PanelSmem<float2, NT_PANEL> ps(sm.base);  // aliases the operand buffers (the phases alternate)
+  const PanelInv ps(sm.base);  // aliases the operand buffers (the phases alternate)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -458,7 +650,7 @@ __global__ void __launch_bounds__(NT_TC, 1)
   int seq = 0, tcount = 0, rt = 0;
   for (int k0 = 0; k0 < n; k0 += PW) {
     const int kb = min(PW, n - k0);
-    if (warp < NT_PANEL / 32) factor_panel<float2, NT_PANEL>(A, n, nrow, ldm, k0, ps, *sm.sing);
+    if (warp < NT_PANEL / 32) factor_panel_tc(A, n, nrow, ldm, k0, ps, sm.sing);
     __syncthreads();  // panel W / L^T in global memory; the panel scratch is free
     const int R0 = k0 + kb;
     if (R0 < n) {
