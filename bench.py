@@ -234,6 +234,22 @@ def load_traffic(kernel, workload, units_per_launch):
     return None
 
 
+def job_throughput(local_ms, local_units, pg=None, device=None):
+    """Whole-job aggregate over the ranks of a replica run: the slowest rank's time (max over ranks)
+    and the units all ranks processed; value = units / slowest time (units/s). Each rank's units
+    are its own (no data exchange), so the sum is the job's work. pg: torch.distributed or None."""
+    if pg is None:
+        return float(local_ms), float(local_units), local_units / (local_ms * 1e-3)
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(u, op=pg.ReduceOp.SUM)
+    ms, units = float(t.item()), float(u.item())
+    return ms, units, units / (ms * 1e-3)
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -314,13 +330,7 @@ def run_gpu(args):
     clk = clocks.stop()
     ctx.sync()
     st = ctx.stats()
-    total_ms = sum(times)
-    if pg is not None:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    points = nc * nw * args.steps * ws
-    value = points / (total_ms * 1e-3)
+    total_ms, points, value = job_throughput(sum(times), nc * nw * args.steps, pg, dev)
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region ---------------
     e2e = None
@@ -332,14 +342,10 @@ def run_gpu(args):
             step(host=True)
         e1.record(stream)
         e1.synchronize()
-        e2e_ms = e0.elapsed_time(e1)
-        if pg is not None:
-            t = torch.tensor([e2e_ms], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        _, _, e2e_value = job_throughput(e0.elapsed_time(e1), nc * nw * args.steps, pg, dev)
         h2d = mol.eps.nbytes + mol.o_ov.nbytes + mol.o_core.nbytes
         d2h = sig.numel() * 8 + eqp.numel() * 8 + a.numel() * 8
-        e2e = {"value": nc * nw * args.steps * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     out = None
@@ -363,7 +369,7 @@ def run_gpu(args):
                     "traffic": load_traffic("chi0_tc_kernel", mol.name, st["chi0_builds"] / max(1, st["chi0_launches"])),
                     "mma_frac": mma_mult * chi0_alg / 1e12 / peak,
                     "peak_source": f"{src} bf16 sustained (kernel timed inside a long step)",
-                    "share_of_step": chi0_t / (total_ms * 1e-3 / ws)}
+                    "share_of_step": chi0_t / (total_ms * 1e-3)}
         else:
             clk_mhz = peaks.get("sm_max_mhz", 2070.0)
             fp32_peak = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
@@ -380,7 +386,7 @@ def run_gpu(args):
                         "frac": fac_alg / 1e12 / peak, "alu_frac": fac_alg / 1e12 / fp32_peak,
                         "traffic": load_traffic("ldlt_tc_kernel", mol.name, units),
                         "peak_source": f"{src} bf16 sustained x 1.1/2.25 (nominal TF32/BF16 dense) / 3 (3xTF32)",
-                        "share_of_step": fac_t / (total_ms * 1e-3 / ws)}
+                        "share_of_step": fac_t / (total_ms * 1e-3)}
             else:
                 peak = fp32_peak if args.prec != "fp64" else 1.2
                 roof = {"kernel": "ldlt_kernel (batched complex-symmetric LDL^T, " +
@@ -390,7 +396,7 @@ def run_gpu(args):
                         "traffic": load_traffic("ldlt_kernel", mol.name, units),
                         "peak_source": ("FP32 ALU: 152 SMs x 128 lanes x 2 flop x max SM clock" if args.prec != "fp64"
                                         else "FP64 FMA loop measured on this GB300 (1.20 TFLOP/s)"),
-                        "share_of_step": fac_t / (total_ms * 1e-3 / ws)}
+                        "share_of_step": fac_t / (total_ms * 1e-3)}
         lat = sorted(times)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
