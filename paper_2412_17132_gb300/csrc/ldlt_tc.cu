@@ -17,7 +17,7 @@
 // takes hi*hi + hi*lo + lo*hi, and the epilogue forms C - (P and Q terms) in round-to-nearest FP32.
 //
 // Roles (416 threads, one CTA per matrix):
-//   warps 0-11  panel factorisation (the shared SIMT routine, named barrier 1)
+//   warps 0-11  panel factorisation (factor_panel_tc below, named barrier 1)
 //   warps 4-7   operand transform: global memory (L2) -> hi/lo planes in the 128-byte-swizzled
 //               K-major layout. The A operand (W rows of a 128-row tile, all 64 panel columns)
 //               stays resident while the tile row's column tiles pass; the B operand (L rows of a
@@ -26,7 +26,7 @@
 //   warp 12     TMEM allocation (512 columns: two tiles in flight x {D1, D2}) and the MMA issuer
 //   warps 0-3,  epilogue: one thread per tile row and half of the tile's columns, the target values
 //   8-11        read and written with 16-byte accesses, the next chunk's values loaded ahead
-// The panel scratch of the SIMT routine aliases the operand buffers (the phases alternate).
+// The panel scratch aliases the operand buffers (the phases alternate).
 // Every mbarrier wait is bounded (one second); on expiry the CTA records kStatTimeout, stops,
 // drains the MMAs it issued and frees TMEM.
 #include "gwc_internal.h"
