@@ -18,8 +18,10 @@
 //     bias that grows with the number of accumulations into one accumulator. Each part
 //     therefore accumulates only kSeg chunks into a "fresh" TMEM accumulator; 4 fold warps
 //     then add it (round-to-nearest FP32) into a running sum kept in TMEM and release the
-//     accumulator. The last fold writes alpha * Pi + beta * I (eps = 1 - Pi for alpha = -1,
-//     beta = 1) to global memory.
+//     accumulator. Each part has its own segment and fold barriers: the fold of part 0 runs
+//     while the MMAs of part 1 finish the chunk, and the fold of part 1 while the next
+//     segment's part-0 MMAs run, so the tensor pipe does not wait for a whole fold. The last
+//     fold writes alpha * Pi + beta * I (eps = 1 - Pi for alpha = -1, beta = 1) to global memory.
 //
 // Every wait on an mbarrier is bounded (one second); on expiry the CTA records kStatTimeout,
 // stops issuing work, drains the copies and MMAs it issued and frees TMEM.
@@ -99,6 +101,17 @@ __device__ __forceinline__ void tile_pair(int t, int& ip, int& iq) {
   iq = t - a * (a + 1) / 2;
 }
 
+// TMEM load without the implicit wait: several loads share one tcgen05.wait::ld
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
@@ -121,9 +134,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* r_empty = r_full + NB_ST;
   uint64_t* a_full = r_empty + NB_ST;
   uint64_t* a_empty = a_full + NA_ST;
-  uint64_t* seg_full = a_empty + NA_ST;
-  uint64_t* fold_done = seg_full + 1;
-  uint64_t* mma_done = fold_done + 1;
+  uint64_t* seg_full = a_empty + NA_ST;      // [part]: the part's fresh accumulator is complete
+  uint64_t* fold_done = seg_full + kParts;   // [part]: the part's fresh accumulator is folded
+  uint64_t* mma_done = fold_done + kParts;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -152,8 +165,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(smem_u32(&a_full[i]), NXF);
       mbar_init(smem_u32(&a_empty[i]), 1);
     }
-    mbar_init(smem_u32(seg_full), 1);
-    mbar_init(smem_u32(fold_done), NFOLD);
+    for (int i = 0; i < kParts; ++i) {
+      mbar_init(smem_u32(&seg_full[i]), 1);
+      mbar_init(smem_u32(&fold_done[i]), NFOLD);
+    }
     mbar_init(smem_u32(mma_done), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -215,8 +230,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc_fence_after();
         const uint32_t bh = smem_u32(b_ring + s * 2 * TILE), bl = bh + TILE;
         const bool seg_start = (kc % kSeg) == 0;
+        const bool seg_end = (kc % kSeg) == kSeg - 1 || kc == p.n_kc - 1;
         for (int part = 0; part < n_parts; ++part, ++a) {
           const int t = a % NA_ST, ua = a / NA_ST;
+          // a new segment overwrites this part's fresh accumulator: its previous fold must be done
+          if (seg_start && kc > 0 && !mbar_wait(smem_u32(&fold_done[part]), (kc / kSeg - 1) & 1, abort_flag)) {
+            ok = false;
+            break;
+          }
           if (!mbar_wait(smem_u32(&a_full[t]), ua & 1, abort_flag)) {
             ok = false;
             break;
@@ -238,20 +259,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
           mma_commit(smem_u32(&a_empty[t]));
+          if (seg_end) mma_commit(smem_u32(&seg_full[part]));  // the fold of this part may start
         }
         if (!ok) break;
         mma_commit(smem_u32(&b_empty[s]));
-        const bool seg_end = (kc % kSeg) == kSeg - 1 || kc == p.n_kc - 1;
-        if (seg_end) {
-          const int seg = kc / kSeg;
-          mma_commit(smem_u32(seg_full));
-          // the next segment overwrites the fresh accumulators: wait until they are folded
-          if (seg < n_seg - 1 && !mbar_wait(smem_u32(fold_done), seg & 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-        }
       }
       mma_commit(smem_u32(mma_done));  // fires when every MMA issued above has completed
     }
@@ -313,25 +324,53 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int P = P0 + row;
     const uint32_t lane_base = tmem_base + ((uint32_t)(32 * q) << 16);
     bool ok = true;
-    for (int seg = 0; seg < n_seg; ++seg) {
-      ok = mbar_wait(smem_u32(seg_full), seg & 1, abort_flag);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
-      tc_fence_after();
+    for (int seg = 0; seg < n_seg && ok; ++seg) {
       const bool last = seg == n_seg - 1;
       if (!last) {
-        for (int part = 0; part < n_parts; ++part)
-          for (int cc = 0; cc < BN / 16; ++cc) {
-            float fr[16], run[16];
-            tmem_ld16(lane_base + (uint32_t)(part * BN + cc * 16), fr);
+        for (int part = 0; part < n_parts; ++part) {
+          ok = mbar_wait(smem_u32(&seg_full[part]), seg & 1, abort_flag);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+          tc_fence_after();
+          // 32 columns per round trip: the fresh and running slices are loaded, then one wait
+          for (int cc = 0; cc < BN / 16; cc += 2) {
+            const uint32_t fa = lane_base + (uint32_t)(part * BN + cc * 16), ra = fa + (uint32_t)(2 * BN);
+            uint32_t f0[16], f1[16];
+            float s0[16], s1[16];
+            tmem_ld16_async(fa, f0);
+            tmem_ld16_async(fa + 16, f1);
             if (seg > 0) {
-              tmem_ld16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), run);
+              uint32_t r0[16], r1[16];
+              tmem_ld16_async(ra, r0);
+              tmem_ld16_async(ra + 16, r1);
+              tmem_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 16; ++i) fr[i] += run[i];
+              for (int i = 0; i < 16; ++i) {
+                s0[i] = __uint_as_float(f0[i]) + __uint_as_float(r0[i]);
+                s1[i] = __uint_as_float(f1[i]) + __uint_as_float(r1[i]);
+              }
+            } else {
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                s0[i] = __uint_as_float(f0[i]);
+                s1[i] = __uint_as_float(f1[i]);
+              }
             }
-            tmem_st16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), fr);
+            tmem_st16(ra, s0);
+            tmem_st16(ra + 16, s1);
           }
+          tmem_wait_st();
+          tc_fence_before();
+          mbar_arrive(smem_u32(&fold_done[part]));
+        }
       } else {
+        for (int part = 0; part < n_parts && ok; ++part) {
+          ok = mbar_wait(smem_u32(&seg_full[part]), seg & 1, abort_flag);
+          ok = __all_sync(0xffffffffu, ok);
+        }
+        if (!ok) break;
+        tc_fence_after();
         // final fold fused with the store: per frequency, 16 columns at a time, 16-byte stores
         const int nfl = n_parts / p.ppf;
         for (int fl = 0; fl < nfl; ++fl) {
@@ -339,15 +378,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const bool write = (!p.active || p.active[f]) && P < p.n_aux;
           for (int cc = 0; cc < BN / 16; ++cc) {
             float v[CPLX ? 2 : 1][16];
+            {  // the fresh (and running) slices of both parts, then one wait
+              uint32_t fr[CPLX ? 2 : 1][16];
+              const uint32_t fa = lane_base + (uint32_t)(fl * p.ppf * BN + cc * 16);
 #pragma unroll
-            for (int comp = 0; comp < (CPLX ? 2 : 1); ++comp) {
-              const int part = fl * p.ppf + comp;
-              float run[16];
-              tmem_ld16(lane_base + (uint32_t)(part * BN + cc * 16), v[comp]);
+              for (int comp = 0; comp < (CPLX ? 2 : 1); ++comp) tmem_ld16_async(fa + (uint32_t)(comp * BN), fr[comp]);
               if (seg > 0) {
-                tmem_ld16(lane_base + (uint32_t)(2 * BN + part * BN + cc * 16), run);
+                uint32_t rn[CPLX ? 2 : 1][16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[comp][i] += run[i];
+                for (int comp = 0; comp < (CPLX ? 2 : 1); ++comp)
+                  tmem_ld16_async(fa + (uint32_t)((2 + comp) * BN), rn[comp]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int comp = 0; comp < (CPLX ? 2 : 1); ++comp)
+#pragma unroll
+                  for (int i = 0; i < 16; ++i) v[comp][i] = __uint_as_float(fr[comp][i]) + __uint_as_float(rn[comp][i]);
+              } else {
+                tmem_wait_ld();
+#pragma unroll
+                for (int comp = 0; comp < (CPLX ? 2 : 1); ++comp)
+#pragma unroll
+                  for (int i = 0; i < 16; ++i) v[comp][i] = __uint_as_float(fr[comp][i]);
               }
             }
             if (!write) continue;
@@ -382,11 +433,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
         }
-      }
-      if (!last) {
-        tmem_wait_st();
-        tc_fence_before();
-        mbar_arrive(smem_u32(fold_done));
       }
     }
   }
