@@ -204,48 +204,54 @@ __device__ void factor_diag_block(float2* __restrict__ A, long long ldm, int k0,
 // lower part) and L^T (transposed, coalesced over the lanes) stored.
 __device__ __forceinline__ void panel_rows_group(float2* __restrict__ A, int n, long long ldm, int k0, int kb,
                                                  const PanelInv& ps, int r, int i, bool row_ok, int g) {
-  const int lmax = min(16 * g + 16, kb);
-  float2 pr[16], pi[16];  // pr[c] = sum a.re (X re, X im), pi[c] = sum a.im (X re, X im)
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    pr[c] = make_float2(0.f, 0.f);
-    pi[c] = make_float2(0.f, 0.f);
-  }
-  const float2* arow = ps.ach[r];
-#pragma unroll 2
-  for (int l = 0; l < lmax; ++l) {
-    const float2 a = arow[l];
-    const float2 ar = make_float2(a.x, a.x), ai = make_float2(a.y, a.y);
-    const float4* xp = reinterpret_cast<const float4*>(&ps.xg[l][16 * g]);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 x = xp[q];
-      const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
-      pr[2 * q] = __ffma2_rn(ar, x0, pr[2 * q]);
-      pi[2 * q] = __ffma2_rn(ai, x0, pi[2 * q]);
-      pr[2 * q + 1] = __ffma2_rn(ar, x1, pr[2 * q + 1]);
-      pi[2 * q + 1] = __ffma2_rn(ai, x1, pi[2 * q + 1]);
-    }
-  }
-  if (!row_ok) return;
   const int cb = 16 * g, ncol = min(16, kb - cb);
+  const float2* arow = ps.ach[r];
   float2* rowp = A + (long long)i * ldm + k0 + cb;
-  float2 w[16];
+  // two passes of 8 columns (c0 = 0, 8): 16 float2 accumulators per pass keep the loop in registers
+#pragma unroll 1
+  for (int c0 = 0; c0 < 16; c0 += 8) {
+    if (c0 >= ncol) break;
+    const int lmax = min(cb + c0 + 8, kb);  // X_cl = 0 for l > c
+    float2 pr[8], pi[8];  // pr[c] = sum a.re (X re, X im), pi[c] = sum a.im (X re, X im)
 #pragma unroll
-  for (int c = 0; c < 16; ++c) w[c] = make_float2(pr[c].x - pi[c].y, pr[c].y + pi[c].x);
-  if (ncol == 16) {
+    for (int c = 0; c < 8; ++c) {
+      pr[c] = make_float2(0.f, 0.f);
+      pi[c] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 4
+    for (int l = 0; l < lmax; ++l) {
+      const float2 a = arow[l];
+      const float2 ar = make_float2(a.x, a.x), ai = make_float2(a.y, a.y);
+      const float4* xp = reinterpret_cast<const float4*>(&ps.xg[l][cb + c0]);
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      *reinterpret_cast<float4*>(rowp + 2 * q) = make_float4(w[2 * q].x, w[2 * q].y, w[2 * q + 1].x, w[2 * q + 1].y);
-  } else {
+      for (int q = 0; q < 4; ++q) {
+        const float4 x = xp[q];
+        const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+        pr[2 * q] = __ffma2_rn(ar, x0, pr[2 * q]);
+        pi[2 * q] = __ffma2_rn(ai, x0, pi[2 * q]);
+        pr[2 * q + 1] = __ffma2_rn(ar, x1, pr[2 * q + 1]);
+        pi[2 * q + 1] = __ffma2_rn(ai, x1, pi[2 * q + 1]);
+      }
+    }
+    if (!row_ok) continue;
+    float2 w[8];
 #pragma unroll
-    for (int c = 0; c < 16; ++c)
-      if (c < ncol) rowp[c] = w[c];
-  }
-  if (i < n) {
+    for (int c = 0; c < 8; ++c) w[c] = make_float2(pr[c].x - pi[c].y, pr[c].y + pi[c].x);
+    const int nc8 = min(8, ncol - c0);
+    if (nc8 == 8) {
 #pragma unroll
-    for (int c = 0; c < 16; ++c)
-      if (c < ncol) A[(long long)(k0 + cb + c) * ldm + i] = smul(w[c], ps.dinv[cb + c]);
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4*>(rowp + c0 + 2 * q) = make_float4(w[2 * q].x, w[2 * q].y, w[2 * q + 1].x, w[2 * q + 1].y);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c < nc8) rowp[c0 + c] = w[c];
+    }
+    if (i < n) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c < nc8) A[(long long)(k0 + cb + c0 + c) * ldm + i] = smul(w[c], ps.dinv[cb + c0 + c]);
+    }
   }
 }
 
