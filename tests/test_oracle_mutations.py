@@ -1,0 +1,111 @@
+"""The oracle's pins catch plausible mistakes (CPU only).
+
+Each test plants one mistake in the oracle (a flipped sign, a dropped term, a wrong weight or
+threshold), on the CPU and for the duration of the test only, and checks that at least one pin
+of tests/test_oracle_pins.py then fails. A pin that passed on a broken oracle would pin nothing.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import test_oracle_pins as P
+from oracle import gwc_oracle as G
+from oracle import sop as S
+from paper_2412_17132_gb300 import synth
+
+
+def _small_sop():
+    # the data of the pins' small_sop fixture, built under the planted mistake
+    m = synth.small(n_states=16, n_occ=4, n_core=1, n_aux=12, seed=5, n_high=2)
+    s = G.System.from_molecule(m, n_im=32)
+    om, xpy = S.casida_sop(s.o_ov, s.delta)
+    rho = np.array([S.transition_moments(s.o_ov, xpy, s.o_core[mm, 0]) for mm in range(m.n_states)])
+    return m, s, om, xpy, rho
+
+
+def _fails(pin, *args):
+    with pytest.raises(AssertionError):
+        pin(*args)
+
+
+def test_pins_pass_on_the_unmodified_oracle():
+    P.test_chi0_imaginary_axis_nsd(synth.tiny())
+    P.test_w_ri_solve_equals_sum_over_poles(_small_sop(), 0.7j)
+    P.test_sigma_continuous_at_residue_threshold(_small_sop())
+    P.test_gl_grid_is_exact_for_lorentzian_kernel()
+    P.test_sum_rule_is_one()
+    P.test_cumulant_single_pole_is_exact()
+    P.test_sigma_cd_converges_to_closed_form(_small_sop())
+
+
+def test_flipped_sign_of_the_pair_response(monkeypatch):
+    orig = G.d_factor
+    monkeypatch.setattr(G, "d_factor", lambda delta, z: -orig(delta, z))
+    _fails(P.test_chi0_imaginary_axis_nsd, synth.tiny())
+
+
+def test_dropped_antiresonant_term(monkeypatch):
+    monkeypatch.setattr(G, "d_factor", lambda delta, z: 2.0 / (complex(z) - delta))
+    _fails(P.test_w_ri_solve_equals_sum_over_poles, _small_sop(), 0.7j)
+
+
+def test_missing_spin_factor(monkeypatch):
+    orig = G.d_factor
+    monkeypatch.setattr(G, "d_factor", lambda delta, z: 0.5 * orig(delta, z))
+    _fails(P.test_w_ri_solve_equals_sum_over_poles, _small_sop(), 2.5 + 1e-3j)
+
+
+def test_bare_coulomb_part_left_in_w(monkeypatch):
+    def wc_total(pi, rhs):  # b^T eps^-1 b instead of b^T (eps^-1 - 1) b
+        x = np.linalg.solve(np.eye(pi.shape[0]) - pi, rhs.astype(complex))
+        return np.einsum("pk,pk->k", rhs, x)
+
+    monkeypatch.setattr(G, "screened_wc", wc_total)
+    _fails(P.test_w_ri_solve_equals_sum_over_poles, _small_sop(), 0.7j)
+
+
+def test_theta_of_zero_taken_as_one(monkeypatch):
+    monkeypatch.setattr(G, "heaviside", lambda x: 1.0 if x >= 0 else 0.0)
+    _fails(P.test_sigma_continuous_at_residue_threshold, _small_sop())
+
+
+def test_imaginary_axis_term_with_the_wrong_sign(monkeypatch):
+    orig = G.System.imag_axis_term
+    monkeypatch.setattr(G.System, "imag_axis_term", lambda self, omega: -orig(self, omega))
+    _fails(P.test_sigma_cd_converges_to_closed_form, _small_sop())
+
+
+def test_grid_weights_without_the_jacobian_scale(monkeypatch):
+    def grid(n, xi0=1.0):
+        x, w = np.polynomial.legendre.leggauss(n)
+        return xi0 * (1.0 + x) / (1.0 - x), w / (1.0 - x) ** 2  # 2 xi0 dropped
+
+    monkeypatch.setattr(G, "modified_gl_grid", grid)
+    _fails(P.test_gl_grid_is_exact_for_lorentzian_kernel)
+
+
+def test_full_trapezoid_weight_at_t0(monkeypatch):
+    def spectrum(ct, dt, eta, direct=False):  # weight 1 at k = 0 instead of 1/2
+        n = ct.size
+        k = np.arange(n)
+        g = np.exp(ct - eta * dt * k)
+        x = dt * n * np.fft.ifft(g)
+        j = np.where(k < n // 2, k, k - n)
+        nu = 2.0 * math.pi * j / (n * dt)
+        order = np.argsort(nu, kind="stable")
+        return nu[order], (x.real / math.pi)[order]
+
+    monkeypatch.setattr(G, "spectrum_from_cumulant", spectrum)
+    _fails(P.test_sum_rule_is_one)
+
+
+def test_cumulant_phase_with_the_wrong_sign(monkeypatch):
+    def ct(omega_rel, beta, t):  # e^{+i w t} instead of e^{-i w t}
+        wq = G.trapezoid_weights(omega_rel)
+        keep = omega_rel != 0.0
+        c = (wq * beta)[keep] / omega_rel[keep] ** 2
+        return (np.exp(1j * np.outer(t, omega_rel[keep])) - 1.0) @ c
+
+    monkeypatch.setattr(G, "cumulant_ct", ct)
+    _fails(P.test_cumulant_single_pole_is_exact)
