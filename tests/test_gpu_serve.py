@@ -35,7 +35,9 @@ def _requests(serve, sizes, arrival=0.0):
 
 
 GRID = np.linspace(-25.0 / EV, 5.0 / EV, 161)
-SIZES = [60, 90, 75, 120, 66, 101]
+# 20 requests of uneven size (log-uniform in [60, 160] states, seeded), as in the serving recipe's
+# equality check of 20 requests alone and in the mix
+SIZES = [int(round(math.exp(x))) for x in np.random.default_rng(7).uniform(math.log(60), math.log(160), 20)]
 
 
 def test_results_same_alone_and_in_the_mix(serve):
@@ -45,7 +47,7 @@ def test_results_same_alone_and_in_the_mix(serve):
         (d,) = srv1.run([r])
         assert d.status == 0
         alone[d.rid] = d
-    srv = serve.SpectrumServer(GRID, budget_bytes=1 << 40, slots=4, n_t=1 << 14)
+    srv = serve.SpectrumServer(GRID, budget_bytes=1 << 40, slots=8, n_t=1 << 14)
     done = srv.run(_requests(serve, SIZES))
     assert len(done) == len(SIZES)
     # at least two requests were on the GPU at the same time
