@@ -172,6 +172,8 @@ def oracle_sample(mol, n_points=2, qp_builds=0):
 
 
 def cpu_threads():
+    """Threads the oracle's BLAS runs on: threadpoolctl's answer, else the thread-count variables
+    the BLAS libraries honour, else every host core."""
     try:
         from threadpoolctl import threadpool_info
 
@@ -180,7 +182,9 @@ def cpu_threads():
             return int(n[0])
     except Exception:
         pass
-    return os.cpu_count()
+    env = [int(os.environ[k]) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+           if os.environ.get(k, "").isdigit() and int(os.environ[k]) > 0]
+    return min(env) if env else os.cpu_count()
 
 
 def run_reference(args):
