@@ -111,3 +111,17 @@ def test_null_context_calls_are_rejected(libgwc):
     assert libgwc.gwc_cumulant_spectrum(None, None, 0, None, None, None, None) == 1
     assert libgwc.gwc_build_chi0(None, None, 0, None, None) == 1
     assert libgwc.gwc_screen(None, None, 0, None, 0, None, None) == 1
+
+
+@pytest.mark.parametrize(
+    "n_core,n_omega,n_t",
+    [(1, 100, 1 << 19), (2, 100, 1 << 18), (64, 2048, 4096), (1, 0, 1024), (1, 100, 1000), (0, 100, 1024)],
+)
+def test_noalloc_rejects_bad_sizes_without_gpu(libgwc, n_core, n_omega, n_t):
+    # the limits of the static scratch (n_core n_t <= 2^18, n_core n_omega <= 2^16) and the shape
+    # rules are checked before any CUDA call; the pointers are never touched on rejection
+    buf = (ctypes.c_double * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    st = libgwc.gwc_cumulant_spectrum_noalloc(p, n_omega, p, n_core, n_t, 2000.0, 1e-3, p, p, None)
+    assert st == 1
+    assert libgwc.gwc_last_error(None)
