@@ -11,7 +11,6 @@ from __future__ import annotations
 import ctypes
 import math
 import os
-from typing import Optional
 
 import numpy as np
 
