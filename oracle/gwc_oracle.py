@@ -28,6 +28,7 @@ Readings taken where the paper is silent (all listed in the design notes):
 """
 from __future__ import annotations
 
+import copy
 import math
 
 import numpy as np
@@ -131,6 +132,9 @@ class System:
         self.xi0 = float(xi0)
         self.vxc = None if vxc is None else np.asarray(vxc, dtype=np.float64)
         self.eps_f = fermi_level(self.eps, self.n_occ) if eps_f is None else float(eps_f)
+        # orbital energies in G (the poles of the Green's function); the input energies unless an
+        # eigenvalue-self-consistent scheme replaces them (see evgw0). W always uses self.eps.
+        self.eps_g = self.eps
         self.delta = transition_energies(self.eps, self.n_occ)
         self.xi, self.w_xi = modified_gl_grid(self.n_im, self.xi0)
         self._w_im = None
@@ -179,7 +183,7 @@ class System:
         tab, w0 = self.w_imag_table()
         out = np.zeros(self.n_core)
         for m in range(self.n_states):
-            a = omega - self.eps[m]
+            a = omega - self.eps_g[m]
             if a == 0.0:
                 continue
             kern = self.w_xi * a / (a * a + self.xi**2) / math.pi  # [n_im]
@@ -193,10 +197,10 @@ class System:
         out = np.zeros(self.n_core, dtype=np.complex128)
         per_m = {}
         for m in range(self.n_states):
-            f = residue_prefactor(self.eps[m], omega, self.eps_f)
+            f = residue_prefactor(self.eps_g[m], omega, self.eps_f)
             if f == 0.0:
                 continue
-            w = self.w_residue(m, abs(self.eps[m] - omega))
+            w = self.w_residue(m, abs(self.eps_g[m] - omega))
             per_m[m] = (f, w)
             out += f * w
         return out, per_m
@@ -225,6 +229,17 @@ class System:
     def sigma_c_core(self, c: int, omega: float) -> complex:
         """Sigma^c of core c alone at w (the same formulas, one core's right-hand sides)."""
         return complex(self.sigma_c(omega)[0][c])
+
+    def with_g_energies(self, eps_g, eps_f=None):
+        """The same system with the orbital energies in G replaced by eps_g (W, the exchange and
+        the RI data unchanged; the imaginary-axis W table is shared). eps_f: the Fermi level used in
+        the residue prefactors, default the midpoint of the HOMO and LUMO of eps_g."""
+        other = copy.copy(self)
+        other.eps_g = np.asarray(eps_g, dtype=np.float64)
+        other.eps_f = fermi_level(other.eps_g, self.n_occ) if eps_f is None else float(eps_f)
+        self.w_imag_table()
+        other._w_im = self._w_im
+        return other
 
     # -- Exchange (Eq. sigma_x) -----------------------------------------------------------------
     def sigma_x(self) -> np.ndarray:
@@ -287,6 +302,33 @@ class System:
             eqp[c] = x1
             iters[c] = it
         return eqp, dh, iters
+
+
+def evgw0(system: "System", tol: float = 1e-8, max_iter: int = 100):
+    """Eigenvalue self-consistency in G with W fixed (evGW0; Sec. "GW for core-levels: beyond
+    G0W0", Eq. ev_sigma_spectral): the orbital energies in G are replaced by the current QP
+    energies of EVERY state while W keeps the RPA excitations of the input energies, so the
+    system must list every state in core_idx (in state order) with o_core = O^P_{m,n} for all n.
+
+    Reading of the iteration (the paper gives the scheme, not the update rule): starting from the
+    input energies eps^(0) = eps, every state is updated at once,
+        eps^(k+1)_n = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n[G(eps^(k))](eps^(k)_n),
+    so that the first step is eps_n + dH_n (the Hedin shift of Eq. hedin_shift is the first
+    iteration of evGW0), with eps_F the midpoint of the current QP HOMO and LUMO, until
+    max_n |eps^(k+1)_n - eps^(k)_n| < tol. Returns (eps_qp [n_states], iterations)."""
+    n = system.n_states
+    if system.n_core != n or np.any(system.core_idx != np.arange(n)):
+        raise ValueError("evgw0 needs every state as a core (core_idx = 0..n_states-1)")
+    sx, vxc = system.sigma_x(), system.v_xc()
+    e = system.eps.copy()
+    for it in range(1, max_iter + 1):
+        s = system.with_g_energies(e)
+        new = np.array([system.eps[c] + sx[c] - vxc[c] + s.sigma_c(float(e[c]))[0][c].real for c in range(n)])
+        done = np.max(np.abs(new - e)) < tol
+        e = new
+        if done:
+            return e, it
+    return e, max_iter
 
 
 def g0w0_graphical_solutions(omega: np.ndarray, sigma_c: np.ndarray, eps_n: float, sigma_x: float, vxc: float):

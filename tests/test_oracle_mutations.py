@@ -109,3 +109,36 @@ def test_cumulant_phase_with_the_wrong_sign(monkeypatch):
 
     monkeypatch.setattr(G, "cumulant_ct", ct)
     _fails(P.test_cumulant_single_pole_is_exact)
+
+
+def test_g_energies_ignored_in_the_imaginary_axis_term(monkeypatch):
+    def imag_axis_term(self, omega):  # poles of G taken from the input energies, not eps_g
+        tab, w0 = self.w_imag_table()
+        out = np.zeros(self.n_core)
+        for m in range(self.n_states):
+            a = omega - self.eps[m]
+            if a == 0.0:
+                continue
+            kern = self.w_xi * a / (a * a + self.xi**2) / math.pi
+            out += kern @ (tab[:, m, :] - w0[m][None, :]) + 0.5 * math.copysign(1.0, a) * w0[m]
+        return out
+
+    monkeypatch.setattr(G.System, "imag_axis_term", imag_axis_term)
+    _fails(P.test_sigma_invariant_under_a_common_shift_of_g_energies)
+
+
+def test_g_energies_ignored_in_the_residues(monkeypatch):
+    def residue_term(self, omega):  # residue positions and occupations from the input energies
+        out = np.zeros(self.n_core, dtype=np.complex128)
+        per_m = {}
+        for m in range(self.n_states):
+            f = G.residue_prefactor(self.eps[m], omega, self.eps_f)
+            if f == 0.0:
+                continue
+            w = self.w_residue(m, abs(self.eps[m] - omega))
+            per_m[m] = (f, w)
+            out += f * w
+        return out, per_m
+
+    monkeypatch.setattr(G.System, "residue_term", residue_term)
+    _fails(P.test_evgw0_sigma_matches_sum_over_poles_with_qp_energies)

@@ -518,3 +518,76 @@ def test_g0w0_secant_root_is_a_graphical_solution():
     roots = G.g0w0_graphical_solutions(grid, sig[0], e_n, sx[0], vxc[0])
     step = grid[1] - grid[0]
     assert any(z > 0 and abs(x - eqp[0]) < step for x, z in roots), (eqp[0], roots)
+
+
+# ----------------------------------------------------------------------------------------
+# evGW0: QP energies of every state in G, W at the RPA level of the input energies
+# (Sec. "GW for core-levels: beyond G0W0", Eqs. ev_sigma_spectral, hedin_shift)
+# ----------------------------------------------------------------------------------------
+
+
+def _all_state_system(seed=21, n_occ=3, n_virt=7, n_aux=8, scale=0.06, n_im=32):
+    # every state is a "core" (its self-energy is computed): O^P_mn symmetric in m, n
+    rng = np.random.default_rng(seed)
+    eps = np.concatenate([np.sort(rng.uniform(-1.2, -0.3, n_occ)), np.sort(rng.uniform(0.1, 2.5, n_virt))])
+    n = eps.size
+    o = rng.normal(0.0, scale, (n_aux, n, n))
+    o = 0.5 * (o + o.transpose(0, 2, 1))
+    o_ov = o[:, :n_occ, n_occ:].reshape(n_aux, -1)
+    o_core = np.ascontiguousarray(np.transpose(o, (1, 2, 0)))  # [m][n][P] = O^P_{m,n}
+    return G.System(eps, n_occ, np.arange(n), o_ov, o_core, 1e-3, n_im=n_im)
+
+
+def test_sigma_invariant_under_a_common_shift_of_g_energies():
+    # CD depends on the poles of G only through w - eps~_m and the occupations: shifting every
+    # eps~_m, eps_F and w by the same amount leaves Sigma^c unchanged (both terms, all states)
+    s = _all_state_system()
+    d = 0.37
+    s2 = s.with_g_energies(s.eps + d, eps_f=s.eps_f + d)
+    for w in (-0.95, -0.5, 0.05, 0.8, 1.7):
+        a = s.sigma_c(w)[0]
+        b = s2.sigma_c(w + d)[0]
+        assert np.max(np.abs(a - b)) < 1e-10 * max(1.0, np.max(np.abs(a)))
+
+
+def test_evgw0_sigma_matches_sum_over_poles_with_qp_energies():
+    # Eq. ev_sigma_spectral: sum over m, nu of rho^2 / (w - eps~_m + (Omega - i eta) sgn(eps_F - eps~_m))
+    # with Omega, rho from the Casida problem of the input energies; CD with G(eps~) must agree
+    # within the anti-resonant eta bound (as for G0W0) plus quadrature error
+    s = _all_state_system(n_im=800, scale=0.15)  # coupling strong enough that G(eps) instead of G(eps~) fails
+    rng = np.random.default_rng(3)
+    eps_t = s.eps + rng.uniform(-0.05, 0.05, s.n_states)
+    st = s.with_g_energies(eps_t)
+    om, xpy = S.casida_sop(s.o_ov, s.delta)
+    for n in (0, 2, 3, 8):
+        rho = np.array([S.transition_moments(s.o_ov, xpy, s.o_core[m, n]) for m in range(s.n_states)])
+        for w in (eps_t[n] - 0.45, eps_t[n] + 0.2, eps_t[n]):
+            cd = st.sigma_c(float(w))[0][n]
+            sp = S.sigma_c_sop(eps_t, st.eps_f, rho, om, float(w), s.eta)
+            bound = sum(np.sum(rho[m] ** 2 * 2 * s.eta / (abs(eps_t[m] - w) + om) ** 2) for m in range(s.n_states))
+            assert abs(cd - sp) <= bound + 1e-6, (n, w, abs(cd - sp), bound)
+
+
+def test_evgw0_first_iteration_is_the_hedin_shift():
+    s = _all_state_system()
+    e1, it = G.evgw0(s, max_iter=1)
+    assert it == 1
+    assert np.max(np.abs(e1 - (s.eps + s.hedin_shift()))) < 1e-12
+
+
+def test_evgw0_converges_to_a_fixed_point():
+    s = _all_state_system()
+    e, it = G.evgw0(s, tol=1e-9)
+    assert it < 100
+    st = s.with_g_energies(e)
+    sx, vxc = s.sigma_x(), s.v_xc()
+    res = [e[n] - (s.eps[n] + sx[n] - vxc[n] + st.sigma_c(float(e[n]))[0][n].real) for n in range(s.n_states)]
+    assert np.max(np.abs(res)) < 1e-7
+    assert np.all(e[: s.n_occ] < st.eps_f) and np.all(e[s.n_occ :] > st.eps_f)  # occupations kept
+    # not the G0W0 / Hedin-shift answer: the QP energies in G moved the result
+    assert np.max(np.abs(e - (s.eps + s.hedin_shift()))) > 1e-6
+
+
+def test_evgw0_rejects_a_core_only_system(tiny_mol):
+    with pytest.raises(ValueError):
+        G.evgw0(G.System.from_molecule(tiny_mol))
