@@ -72,7 +72,10 @@ typedef struct {
   int n_occ;             /* occupied orbitals are 0..n_occ-1, 1 <= n_occ < n_states            */
   int n_aux;             /* auxiliary (RI) basis size, >= 1                                    */
   int n_core;            /* number of core states whose self-energy is computed, >= 1          */
-  const int* core_idx;   /* HOST [n_core]: orbital index of each core state, each < n_occ      */
+  const int* core_idx;   /* HOST [n_core]: orbital index of each state whose self-energy is
+                            computed, each < n_states. gwc_qp_solve, gwc_sigma_core_wac and the
+                            request mode need occupied (core) states, < n_occ; gwc_evgw0 needs
+                            every state, core_idx = 0..n_states-1                              */
   const double* eps;     /* [n_states] orbital energies, ascending                            */
   const double* o_ov;    /* [n_aux][n_ov]: O^P_ia, column (i, a) = i * n_virt + (a - n_occ)    */
   const double* o_core;  /* [n_states][n_core][n_aux]: O^P_{m, core_idx[c]} for every m       */
@@ -174,6 +177,29 @@ gwc_status gwc_screen(gwc_ctx* ctx, const double* z, int F, const double* rhs, i
  * The G_dH W0 self-energy of Eq. hedin_sigma_spectral is Sigma^c_n(w - dH_n). */
 gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double* sigma_c, double* im_sigma_dec,
                           double* sigma_x, void* stream);
+
+/* Orbital energies in G (the poles of the Green's function) for gwc_sigma_core: Eq. ev_sigma_spectral
+ * (Sec. "GW for core-levels: beyond G0W0") replaces them by QP energies while W keeps the RPA
+ * excitations of the input energies. The residue positions |eps~_m - w| + i eta, the occupations f_m
+ * of Eq. cd_prefactors and the imaginary-axis kernel a_m = w - eps~_m use eps~; chi0 and W use the
+ * input energies. Only gwc_sigma_core (and gwc_evgw0) see the replacement.
+ *   eps_g: HOST [n_states], or NULL to return to the input energies
+ *   eps_f: Fermi level of the replacement; NaN: midpoint of eps_g[n_occ-1] and eps_g[n_occ]
+ * Occupied states must stay below eps_f and virtual ones above (GWC_ERR_INVALID_ARG otherwise).
+ * Copies eps_g; synchronises `stream`. */
+gwc_status gwc_set_g_energies(gwc_ctx* ctx, const double* eps_g, double eps_f, void* stream);
+
+/* Eigenvalue-self-consistent evGW0 (Sec. "GW for core-levels: beyond G0W0", Eq. ev_sigma_spectral):
+ * every state's QP energy is fed back into G while W keeps the RPA excitations of the input energies.
+ * Needs every state as a core (n_core = n_states, core_idx = 0..n_states-1, o_core = O^P_mn for all
+ * m, n). Iteration, all states at once from eps^(0) = eps:
+ *   eps^(k+1)_n = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n[G(eps^(k))](eps^(k)_n),
+ * so the first step gives eps_n + dH_n (Eq. hedin_shift), with eps_F the midpoint of the current QP
+ * HOMO and LUMO, until max_n |eps^(k+1)_n - eps^(k)_n| < tol (Ha). Each step is one gwc_sigma_core on
+ * the grid of the current energies and one update kernel on the device.
+ *   eps_qp: DEVICE [n_states] result; iters: HOST, steps taken
+ * GWC_ERR_NOT_CONVERGED if max_iter (1..1000) steps do not reach tol; synchronises `stream`. */
+gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int* iters, void* stream);
 
 /* Hedin shift and G_dH W0 quasiparticle energies (Eqs. hedin_shift, quasiparticle_equation,
  * hedin_sigma_spectral, QPGWC): dH_n = Re Sigma^c_n(eps_n) + Sigma^x_n - v^xc_n, then

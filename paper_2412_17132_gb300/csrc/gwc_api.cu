@@ -171,15 +171,16 @@ gwc_status dalloc(gwc_ctx* ctx, T** p, size_t count) {
 gwc_status validate_system(const gwc_system* s) {
   if (!s) return fail(nullptr, GWC_ERR_INVALID_ARG, "system is NULL");
   if (s->n_states < 2 || s->n_occ < 1 || s->n_occ >= s->n_states || s->n_aux < 1 || s->n_core < 1 ||
-      s->n_core > s->n_occ)
-    return fail(nullptr, GWC_ERR_INVALID_ARG, "invalid sizes (need n_states>=2, 1<=n_occ<n_states, n_aux>=1, 1<=n_core<=n_occ)");
+      s->n_core > s->n_states)
+    return fail(nullptr, GWC_ERR_INVALID_ARG,
+                "invalid sizes (need n_states>=2, 1<=n_occ<n_states, n_aux>=1, 1<=n_core<=n_states)");
   if (s->n_aux > 65536 || s->n_states > 65536) return fail(nullptr, GWC_ERR_INVALID_ARG, "n_aux and n_states must be <= 65536");
   if ((long long)s->n_occ * (s->n_states - s->n_occ) > (1LL << 31) - 1)
     return fail(nullptr, GWC_ERR_INVALID_ARG, "n_occ * n_virt too large");
   if (!s->core_idx || !s->eps || !s->o_ov || !s->o_core) return fail(nullptr, GWC_ERR_INVALID_ARG, "NULL input pointer");
   for (int c = 0; c < s->n_core; ++c)
-    if (s->core_idx[c] < 0 || s->core_idx[c] >= s->n_occ)
-      return fail(nullptr, GWC_ERR_INVALID_ARG, "core_idx must index occupied states");
+    if (s->core_idx[c] < 0 || s->core_idx[c] >= s->n_states)
+      return fail(nullptr, GWC_ERR_INVALID_ARG, "core_idx must index states 0..n_states-1");
   if (s->memory != GWC_MEM_DEVICE && s->memory != GWC_MEM_HOST) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad memory kind");
   return GWC_OK;
 }
@@ -200,6 +201,17 @@ gwc_status validate_options(const gwc_options* o, int n_core) {
   if (o->qp_mode < 0 || o->qp_mode > 2) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad qp_mode");
   (void)n_core;
   return GWC_OK;
+}
+
+// Orbital energies in G (the poles of the Green's function) and the Fermi level of the residue
+// prefactors: the input energies unless gwc_set_g_energies replaced them. W always uses d_eps.
+const double* g_eps_dev(const gwc_ctx* c) { return c->g_set ? c->d_eps_g : c->d_eps; }
+const std::vector<double>& g_eps_host(const gwc_ctx* c) { return c->g_set ? c->h_eps_g : c->h_eps; }
+double g_eps_f(const gwc_ctx* c) { return c->g_set ? c->eps_f_g : c->eps_f; }
+
+gwc_status need_occupied_cores(gwc_ctx* ctx, const char* what) {
+  if (ctx->cores_occupied) return GWC_OK;
+  return fail(ctx, GWC_ERR_INVALID_ARG, std::string(what) + " needs every core_idx to be an occupied state");
 }
 
 struct Sizes {
@@ -270,6 +282,9 @@ gwc_status load_system(gwc_ctx* ctx, const gwc_system* s, cudaStream_t st) {
     if (!(ctx->h_eps[i] >= ctx->h_eps[i - 1])) return fail(ctx, GWC_ERR_INVALID_ARG, "eps must be ascending and finite");
   ctx->eps_f = std::isnan(s->eps_f) ? 0.5 * (ctx->h_eps[s->n_occ - 1] + ctx->h_eps[s->n_occ]) : s->eps_f;
   ctx->h_core.assign(s->core_idx, s->core_idx + s->n_core);
+  ctx->cores_occupied = true;
+  for (int c : ctx->h_core) ctx->cores_occupied = ctx->cores_occupied && c < s->n_occ;
+  ctx->g_set = false;  // G takes the (new) input energies
   TRY(upload(ctx, ctx->d_eps, s->eps, sizeof(double) * s->n_states, s->memory, st));
   TRY(upload(ctx, ctx->d_o_ov, s->o_ov, sizeof(double) * s->n_aux * n_ov, s->memory, st));
   TRY(upload(ctx, ctx->d_o_core, s->o_core, sizeof(double) * s->n_states * s->n_core * s->n_aux, s->memory, st));
@@ -698,7 +713,7 @@ void gwc_destroy(gwc_ctx* ctx) {
                   ctx->d_qp_rowmap, ctx->d_all_done, ctx->d_cw_a, ctx->d_cw_b, ctx->d_coef, ctx->d_tw,
                   ctx->d_pair_z, ctx->d_pair_rows, ctx->d_zim, ctx->d_req_wrel, ctx->d_req_z, ctx->d_req_rows,
                   ctx->d_req_pair_of, ctx->d_req_w, ctx->d_req_im, ctx->d_req_a, ctx->d_req_nu, ctx->d_req_eqp,
-                  ctx->d_req_dh, ctx->d_req_it};
+                  ctx->d_req_dh, ctx->d_req_it, ctx->d_eps_g, ctx->d_ev_sig, ctx->d_ev_diff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& r : ctx->ev_pending) {
@@ -789,13 +804,15 @@ gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double
   const int ns = ctx->n_states, nc = ctx->n_core;
   // plan: one residue pair per (w_j, m) with f_m(w_j) != 0 (Eq. cd_prefactors)
   auto th = [](double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); };
+  const std::vector<double>& eg = g_eps_host(ctx);  // poles of G
+  const double ef = g_eps_f(ctx);
   std::vector<int> pidx((size_t)n_omega * ns, -1);
   std::vector<int> pm;
   std::vector<double> pw;
   for (int j = 0; j < n_omega; ++j)
     for (int m = 0; m < ns; ++m) {
-      double em = ctx->h_eps[m], w = omega[j];
-      double f = -th(ctx->eps_f - em) * th(em - w) + th(em - ctx->eps_f) * th(w - em);
+      double em = eg[m], w = omega[j];
+      double f = -th(ef - em) * th(em - w) + th(em - ef) * th(w - em);
       if (f != 0.0) {
         pidx[(size_t)j * ns + m] = (int)pm.size();
         pm.push_back(m);
@@ -829,10 +846,10 @@ gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double
     CU(cudaMemcpyAsync(ctx->d_pair_m, pm.data(), sizeof(int) * n_pairs, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(ctx->d_pair_w, pw.data(), sizeof(double) * n_pairs, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(ctx->d_pair_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, st));
-    LAUNCH(launch_fill_z_pairs(ctx->d_eps, ctx->d_pair_m, ctx->d_pair_w, n_pairs, ctx->opt.eta, ctx->d_pair_z, st));
+    LAUNCH(launch_fill_z_pairs(g_eps_dev(ctx), ctx->d_pair_m, ctx->d_pair_w, n_pairs, ctx->opt.eta, ctx->d_pair_z, st));
     TRY(residue_batches(ctx, n_pairs, ctx->d_pair_z, ctx->d_pair_rows, nc, ctx->d_wres, nullptr, st));
   }
-  LAUNCH(launch_sigma_grid(ctx->d_eps, ns, nc, ctx->d_core_idx, ctx->d_grid_w, n_omega, ctx->eps_f, ctx->d_xi, ctx->d_wxi,
+  LAUNCH(launch_sigma_grid(g_eps_dev(ctx), ns, nc, ctx->d_core_idx, ctx->d_grid_w, n_omega, ef, ctx->d_xi, ctx->d_wxi,
                            ctx->opt.n_im, ctx->d_wim, ctx->d_pidx, ctx->d_wres, ctx->opt.dec, ctx->d_group, sigma_c,
                            im_sigma_dec, st));
   if (sigma_x) CU(cudaMemcpyAsync(sigma_x, ctx->d_sx, sizeof(double) * nc, cudaMemcpyDeviceToDevice, st));
@@ -841,9 +858,78 @@ gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double
   return check_stream_error(ctx);
 }
 
+gwc_status gwc_set_g_energies(gwc_ctx* ctx, const double* eps_g, double eps_f, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!eps_g) {
+    ctx->g_set = false;
+    return GWC_OK;
+  }
+  const int n = ctx->n_states;
+  for (int m = 0; m < n; ++m)
+    if (!std::isfinite(eps_g[m])) return fail(ctx, GWC_ERR_INVALID_ARG, "eps_g must be finite");
+  const double ef = std::isnan(eps_f) ? 0.5 * (eps_g[ctx->n_occ - 1] + eps_g[ctx->n_occ]) : eps_f;
+  for (int m = 0; m < n; ++m)
+    if ((m < ctx->n_occ) != (eps_g[m] < ef))
+      return fail(ctx, GWC_ERR_INVALID_ARG, "eps_g must keep the occupied states below eps_f and the virtual ones above");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx->d_eps_g) TRY(dalloc(ctx, &ctx->d_eps_g, n));
+  ctx->h_eps_g.assign(eps_g, eps_g + n);
+  CU(cudaMemcpyAsync(ctx->d_eps_g, ctx->h_eps_g.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));  // the host vector may change on the next call
+  ctx->eps_f_g = ef;
+  ctx->g_set = true;
+  return GWC_OK;
+}
+
+gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int* iters, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!eps_qp || !iters || !(tol > 0.0) || max_iter < 1 || max_iter > 1000)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "need eps_qp, iters, tol > 0 and 1 <= max_iter <= 1000");
+  const int n = ctx->n_states;
+  if (ctx->n_core != n) return fail(ctx, GWC_ERR_INVALID_ARG, "evGW0 needs every state as a core (n_core = n_states)");
+  for (int c = 0; c < n; ++c)
+    if (ctx->h_core[c] != c) return fail(ctx, GWC_ERR_INVALID_ARG, "evGW0 needs core_idx = 0..n_states-1");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx->d_ev_sig) TRY(dalloc(ctx, &ctx->d_ev_sig, (size_t)n * n * 2));
+  if (!ctx->d_ev_diff) TRY(dalloc(ctx, &ctx->d_ev_diff, 1));
+  struct GReset {  // later calls see the input energies in G again, on every return path
+    gwc_ctx* c;
+    ~GReset() { c->g_set = false; }
+  } g_reset{ctx};
+  std::vector<double> e(ctx->h_eps);
+  CU(cudaMemcpyAsync(eps_qp, ctx->d_eps, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  gwc_status res = GWC_ERR_NOT_CONVERGED;
+  int it = 0;
+  while (it < max_iter) {
+    ++it;
+    gwc_status r = gwc_set_g_energies(ctx, e.data(), NAN, stream);
+    if (r == GWC_OK) r = gwc_sigma_core(ctx, e.data(), n, ctx->d_ev_sig, nullptr, nullptr, stream);
+    if (r != GWC_OK) {
+      res = r;
+      break;
+    }
+    unsigned long long bits = 0;
+    CU(cudaMemsetAsync(ctx->d_ev_diff, 0, sizeof(unsigned long long), st));
+    LAUNCH(launch_evgw0_update(ctx->d_eps, ctx->d_sx, ctx->d_vxc_eff, ctx->d_ev_sig, n, eps_qp, ctx->d_ev_diff, st));
+    CU(cudaMemcpyAsync(e.data(), eps_qp, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&bits, ctx->d_ev_diff, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double diff;
+    std::memcpy(&diff, &bits, sizeof(diff));
+    if (diff < tol) {
+      res = GWC_OK;
+      break;
+    }
+  }
+  *iters = it;
+  if (res == GWC_ERR_NOT_CONVERGED) return fail(ctx, res, "evGW0 did not converge within max_iter");
+  return res;
+}
+
 gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
   if (!eps_qp || !dh || !iters) return fail(ctx, GWC_ERR_INVALID_ARG, "need eps_qp, dh, iters");
+  TRY(need_occupied_cores(ctx, "gwc_qp_solve"));
   cudaStream_t st = (cudaStream_t)stream;
   TRY(compute_wim(ctx, st));
   TRY(enqueue_qp(ctx, eps_qp, dh, iters, true, st));
@@ -874,6 +960,7 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
 
 gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
                               double* sigma_c, double* im_sigma_dec, void* stream) {
+  if (ctx) TRY(need_occupied_cores(ctx, "gwc_sigma_core_wac"));
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
   if (!omega || !sigma_c || n_omega < 1 || n_omega > (1 << 20) || n_core_ref < 0 || n_val_ref < 0 ||
       n_core_ref + n_val_ref > 4096)
@@ -987,6 +1074,7 @@ gwc_status gwc_gdh_spectrum(gwc_ctx* ctx, const double* omega, int n_omega, cons
 
 // ---- request mode ----------------------------------------------------------------------------------
 gwc_status gwc_request_plan(gwc_ctx* ctx, const double* omega_rel, int n_omega, void* stream) {
+  if (ctx) TRY(need_occupied_cores(ctx, "gwc_request_plan"));
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
   if (!omega_rel || n_omega < 1 || n_omega > 8192)
     return fail(ctx, GWC_ERR_INVALID_ARG, "need omega_rel and 1 <= n_omega <= 8192");

@@ -150,6 +150,8 @@ int launch_fill_z_pairs(const double* eps, const int* pair_m, const double* pair
                         cudaStream_t s);
 
 // Self-energy assembly on a grid: see sigma.cu
+int launch_evgw0_update(const double* eps, const double* sx, const double* vxc, const double* sigma, int n, double* e,
+                        unsigned long long* diff_bits, cudaStream_t s);
 int launch_sigma_grid(const double* eps, int n_states, int n_core, const int* core_idx, const double* omega, int n_w,
                       double eps_f, const double* xi, const double* wxi, int n_im, const double* wim,
                       const int* pidx /*[n_w][n_states] -> pair or -1*/, const double* wres /*[pair][n_core][2]*/,
@@ -305,6 +307,15 @@ struct gwc_ctx {
   double *d_req_a = nullptr, *d_req_nu = nullptr;
   double *d_req_eqp = nullptr, *d_req_dh = nullptr;
   int* d_req_it = nullptr;
+
+  // orbital energies in G (gwc_set_g_energies): the input energies unless set; W always uses d_eps
+  bool g_set = false;
+  std::vector<double> h_eps_g;
+  double* d_eps_g = nullptr;
+  double eps_f_g = 0.0;
+  bool cores_occupied = true;   // every core_idx < n_occ (needed by the QP, request and CD-WAC paths)
+  double* d_ev_sig = nullptr;   // evGW0: [n_states][n_states][2] self-energies at the current energies
+  unsigned long long* d_ev_diff = nullptr;  // evGW0: max |eps_new - eps| as the bits of a double
 
   // host staging
   int* h_pin_i = nullptr;

@@ -346,7 +346,29 @@ __global__ void sigma_grid_wac_kernel(const double* __restrict__ eps, int n_stat
   }
 }
 
+// ---- evGW0 update (Sec. "GW for core-levels: beyond G0W0") --------------------------------------
+// Every state at once: e_n <- eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n[G(e)](e_n), with
+// sigma [n][n][2] the self-energies of all states on the grid of the current energies (so the
+// diagonal holds Sigma^c_n(e_n)). The largest change |e_new - e| goes to *diff_bits as the bit
+// pattern of a non-negative double (ordered like the value, so atomicMax is the maximum).
+__global__ void evgw0_update_kernel(const double* __restrict__ eps, const double* __restrict__ sx,
+                                    const double* __restrict__ vxc, const double* __restrict__ sigma, int n,
+                                    double* __restrict__ e, unsigned long long* __restrict__ diff_bits) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const double e_new = eps[k] + sx[k] - vxc[k] + sigma[2 * ((size_t)k * n + k)];
+    const double d = fabs(e_new - e[k]);
+    e[k] = e_new;
+    atomicMax(diff_bits, (unsigned long long)__double_as_longlong(d));
+  }
+}
+
 }  // namespace
+
+int launch_evgw0_update(const double* eps, const double* sx, const double* vxc, const double* sigma, int n, double* e,
+                        unsigned long long* diff_bits, cudaStream_t s) {
+  evgw0_update_kernel<<<(n + 255) / 256, 256, 0, s>>>(eps, sx, vxc, sigma, n, e, diff_bits);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_thiele_fit(const double* wim, int n_states, int n_core, int n_im, const double* wref, int n_ref, int n_pairs,
                       const double* zref, double* coef, cudaStream_t s) {

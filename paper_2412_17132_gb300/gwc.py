@@ -102,6 +102,9 @@ _SIGS = {
     "gwc_screen": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_sigma_core": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_qp_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gwc_set_g_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "gwc_evgw0": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.c_void_p]),
     "gwc_cumulant_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
@@ -289,6 +292,24 @@ class Context:
             sig, dec, sx = out
         _check(lib().gwc_sigma_core(self._ctx, om.ctypes.data, n_w, _ptr(sig), _ptr(dec), _ptr(sx), _stream(stream)), self._ctx)
         return sig, dec, sx
+
+    def set_g_energies(self, eps_g=None, eps_f=math.nan, stream=None):
+        """Orbital energies in G for sigma_core (host array [n_states]); None returns to the input energies."""
+        if eps_g is None:
+            _check(lib().gwc_set_g_energies(self._ctx, None, math.nan, _stream(stream)), self._ctx)
+            return
+        e = np.ascontiguousarray(np.asarray(eps_g, dtype=np.float64))
+        _check(lib().gwc_set_g_energies(self._ctx, e.ctypes.data, float(eps_f), _stream(stream)), self._ctx)
+
+    def evgw0(self, tol=1e-8, max_iter=100, stream=None):
+        """evGW0 QP energies of every state (the context must list every state as a core): a CUDA
+        tensor [n_states] and the number of steps."""
+        import torch
+
+        e = torch.empty((self.n_states,), dtype=torch.float64, device="cuda")
+        it = ctypes.c_int(0)
+        _check(lib().gwc_evgw0(self._ctx, float(tol), int(max_iter), _ptr(e), ctypes.byref(it), _stream(stream)), self._ctx)
+        return e, it.value
 
     def qp_solve(self, stream=None, out=None):
         import torch

@@ -81,7 +81,7 @@ def test_workspace_bytes_host_only(libgwc):
 
 @pytest.mark.parametrize(
     "kw",
-    [dict(n_occ=0), dict(n_occ=20), dict(n_aux=0), dict(n_core=0), dict(n_core=5), dict(core=[7])],
+    [dict(n_occ=0), dict(n_occ=20), dict(n_aux=0), dict(n_core=0), dict(n_core=21), dict(core=[20]), dict(core=[-1])],
 )
 def test_create_rejects_bad_sizes_without_gpu(libgwc, kw):
     from paper_2412_17132_gb300 import gwc
