@@ -111,6 +111,9 @@ def test_null_context_calls_are_rejected(libgwc):
     assert libgwc.gwc_cumulant_spectrum(None, None, 0, None, None, None, None) == 1
     assert libgwc.gwc_build_chi0(None, None, 0, None, None) == 1
     assert libgwc.gwc_screen(None, None, 0, None, 0, None, None) == 1
+    assert libgwc.gwc_set_g_energies(None, None, 0.0, None) == 1
+    it = ctypes.c_int(0)
+    assert libgwc.gwc_evgw0(None, 1e-8, 10, None, ctypes.byref(it), None) == 1
 
 
 @pytest.mark.parametrize(
