@@ -461,7 +461,7 @@ def run_gpu(args):
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         qp_builds = int(sum(int(i) + 1 for i in out["qp"]["iters"])) * mol.n_occ
-        r = oracle_sample(mol, n_points=2, qp_builds=qp_builds)
+        r = oracle_sample(mol, n_points=6, qp_builds=qp_builds)  # ~10 s of CPU work on 16 host cores
         out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                                "sample": r["sample"], "measured_s": r["measured_s"]}
     if rank == 0:
