@@ -218,6 +218,27 @@ class System:
                 dec[c] = f * w[c].imag
         return sig, dec
 
+    def im_sigma_dec_group(self, omega: float, groups) -> np.ndarray:
+        """Decoupled Im Sigma with symmetry-equivalent cores (Sec. "Core-valence decoupling", Eq.
+        sigma_spectral_decoupled_symmetric, in the residue form of Eq. cd_sigma_imaginary_decoupled):
+        for core n the sum over the cores i of its group (groups[c] is the label of core c),
+            Im Sigma^dec_n(w) = sum_{i in group(n)} f_i Im W^c_{i n}(|eps_i - w| + i eta),
+        each member with its own prefactor f_i, its own residue frequency |eps_i - w| and the RI vector
+        o_{in} = O^.(i, n) (one solve per member). A group of one member is the DIAG form. Returns [n_core]."""
+        groups = [int(g) for g in groups]
+        out = np.zeros(self.n_core)
+        for c, n in enumerate(self.core_idx):
+            for c2, i in enumerate(self.core_idx):
+                if groups[c2] != groups[c]:
+                    continue
+                f = residue_prefactor(self.eps_g[i], omega, self.eps_f)
+                if f == 0.0:
+                    continue
+                pi = chi0(self.o_ov, self.delta, complex(abs(self.eps_g[i] - omega), self.eta))
+                w = screened_wc(pi, self.o_core[int(i), c][:, None])[0]
+                out[c] += f * w.imag
+        return out
+
     def sigma_c_grid(self, omegas: np.ndarray):
         """Sigma^c on a common absolute grid: complex [n_core][n_w] and decoupled Im [n_core][n_w]."""
         s = np.empty((self.n_core, omegas.size), dtype=np.complex128)

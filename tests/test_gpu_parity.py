@@ -234,6 +234,7 @@ def test_ragged_system_sigma_fp64(gwc):
 
 
 def test_group_decoupling_fp64(gwc):
+    """GROUP decoupling (Eq. sigma_spectral_decoupled_symmetric) against the oracle's group form."""
     mol = synth.small(n_states=30, n_occ=6, n_core=3, n_aux=40, seed=31, n_omega=15)
     groups = [0, 0, 1]
     ctx = gwc.Context.from_molecule(mol, prec="fp64", dec="group", groups=groups)
@@ -242,14 +243,27 @@ def test_group_decoupling_fp64(gwc):
     s = G.System.from_molecule(mol)
     dec = dec.cpu().numpy()
     for j, w in enumerate(mol.omega):
-        _, per_m = s.residue_term(float(w))
-        for c in range(3):
-            ref = 0.0
-            for c2 in range(3):
-                if groups[c2] == groups[c] and c2 in per_m:
-                    f, wv = per_m[c2]
-                    ref += f * wv[c].imag
-            assert abs(dec[c, j] - ref) < 1e-9
+        ref = s.im_sigma_dec_group(float(w), groups)
+        assert np.max(np.abs(dec[:, j] - ref)) < 1e-9, (j, dec[:, j], ref)
+
+
+def test_group_decoupling_mirrored_cores_fp64(gwc):
+    """Two symmetry-equivalent (degenerate, mirrored) cores and a third one in its own group."""
+    import test_oracle_pins as P
+
+    eps, n_occ, core_idx, o_ov, o_core, eta = P.mirrored_two_core_system()
+    groups = [0, 0, 1]
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda").contiguous()  # noqa: E731
+    ctx = gwc.Context(dev(eps), n_occ, core_idx, dev(o_ov), dev(o_core), eta=eta, n_im=8, prec="fp64", dec="group",
+                      groups=groups)
+    ws = np.linspace(eps[0] - 1.2, eps[0] + 0.02, 23)
+    _, dec, _ = ctx.sigma_core(ws)
+    ctx.sync()
+    s = G.System(eps, n_occ, core_idx, o_ov, o_core, eta, n_im=8)
+    dec = dec.cpu().numpy()
+    for j, w in enumerate(ws):
+        ref = s.im_sigma_dec_group(float(w), groups)
+        assert np.max(np.abs(dec[:, j] - ref)) < 1e-9 * max(1.0, np.max(np.abs(ref))), (j, dec[:, j], ref)
 
 
 def test_benzene_sampled_fp64(gwc):

@@ -142,3 +142,68 @@ def test_g_energies_ignored_in_the_residues(monkeypatch):
 
     monkeypatch.setattr(G.System, "residue_term", residue_term)
     _fails(P.test_evgw0_sigma_matches_sum_over_poles_with_qp_energies)
+
+
+def _group_variant(member_energy_of_n=False, diagonal_rhs=False, all_cores=False):
+    """im_sigma_dec_group with one planted mistake: the residue frequency of every member taken from
+    the core's own energy, the RI vector o_nn used for every member, or the sum over all cores."""
+
+    def fn(self, omega, groups):
+        out = np.zeros(self.n_core)
+        for c, n in enumerate(self.core_idx):
+            for c2, i in enumerate(self.core_idx):
+                if not all_cores and groups[c2] != groups[c]:
+                    continue
+                e = self.eps_g[n] if member_energy_of_n else self.eps_g[i]
+                f = G.residue_prefactor(e, omega, self.eps_f)
+                if f == 0.0:
+                    continue
+                pi = G.chi0(self.o_ov, self.delta, complex(abs(e - omega), self.eta))
+                rhs = self.o_core[int(n) if diagonal_rhs else int(i), c][:, None]
+                out[c] += f * G.screened_wc(pi, rhs)[0].imag
+        return out
+
+    return fn
+
+
+def test_group_members_at_the_cores_own_residue_frequency(monkeypatch):
+    monkeypatch.setattr(G.System, "im_sigma_dec_group", _group_variant(member_energy_of_n=True))
+    _fails(P.test_group_decoupling_uses_each_members_own_residue_frequency)
+
+
+def test_group_members_with_the_diagonal_ri_vector(monkeypatch):
+    monkeypatch.setattr(G.System, "im_sigma_dec_group", _group_variant(diagonal_rhs=True))
+    _fails(P.test_group_decoupling_equals_sum_over_symmetry_equivalent_poles)
+
+
+def test_group_sum_over_every_core(monkeypatch):
+    monkeypatch.setattr(G.System, "im_sigma_dec_group", _group_variant(all_cores=True))
+    _fails(P.test_group_decoupling_equals_sum_over_symmetry_equivalent_poles)
+
+
+def test_group_pins_pass_on_the_unmodified_variant(monkeypatch):
+    monkeypatch.setattr(G.System, "im_sigma_dec_group", _group_variant())
+    P.test_group_decoupling_equals_sum_over_symmetry_equivalent_poles()
+    P.test_group_decoupling_uses_each_members_own_residue_frequency()
+
+
+def test_wac_core_window_left_in_ev(monkeypatch):
+    orig = G.wac_reference_points
+
+    def ref(*a, **kw):  # 40 taken as Ha: the eV -> Ha conversion dropped
+        kw["wc_max_ev"] = 40.0 * 27.211386245988
+        return orig(*a, **kw)
+
+    monkeypatch.setattr(G, "wac_reference_points", ref)
+    _fails(P.test_wac_reference_points_follow_the_printed_parameters)
+
+
+def test_wac_valence_margins_swapped(monkeypatch):
+    orig = G.wac_reference_points
+
+    def ref(*a, **kw):  # 1 % below and 8 % above instead of 8 % below and 1 % above
+        kw.update(d_lower=0.01, d_upper=0.08)
+        return orig(*a, **kw)
+
+    monkeypatch.setattr(G, "wac_reference_points", ref)
+    _fails(P.test_wac_reference_points_follow_the_printed_parameters)

@@ -388,6 +388,78 @@ def test_correlation_satellites_appear_with_high_virtuals(tiny_mol):
     assert np.max(np.abs(full - dec)) > 1e-6
 
 
+def mirrored_two_core_system(seed=41, n_states=14, n_occ=4, n_aux=10, eta=2e-3):
+    """Two symmetry-equivalent 1s cores (states 0 and 1, degenerate) plus a third core (state 2).
+
+    A full RI tensor O^P_mn (symmetric in m, n) is made invariant under the mirror that swaps the
+    states 0 <-> 1 together with the auxiliary functions P <-> n_aux-1-P, so W^c_00 = W^c_11 and
+    W^c_10 = W^c_01 at every z, while W^c_10 != W^c_00."""
+    rng = np.random.default_rng(seed)
+    eps = np.sort(np.concatenate([[-10.4, -10.4, -10.3], rng.uniform(-1.0, -0.25, n_occ - 3),
+                                  rng.uniform(0.0, 3.0, n_states - n_occ - 2), [6.0, 25.0]]))
+    o = rng.normal(0.0, 0.05, (n_aux, n_states, n_states))
+    o = 0.5 * (o + o.transpose(0, 2, 1))
+    perm = np.arange(n_states)
+    perm[[0, 1]] = [1, 0]
+    o = 0.5 * (o + o[::-1][:, perm][:, :, perm])
+    o[:, :3, :] *= 3.0  # core-localised coefficients
+    o[:, :, :3] *= 3.0
+    o_ov = np.ascontiguousarray(o[:, :n_occ, n_occ:].reshape(n_aux, -1))
+    o_core = np.ascontiguousarray(o[:, :, :3].transpose(1, 2, 0))  # [m][core][P]
+    return eps, n_occ, np.array([0, 1, 2]), o_ov, o_core, eta
+
+
+def _group_sop_reference(s, omega, groups, c):
+    """sum over the group of core c and the RPA poles of rho_{i n}^2 eta / ((w - eps_i + Omega)^2 + eta^2)
+    (Eq. sigma_spectral_decoupled_symmetric with the pole at eps_i - Omega), and the bound
+    sum rho^2 eta / (|eps_i - w| + Omega)^2 on its difference from the residue form (the anti-resonant
+    term that the residue form keeps and the time-ordered sum drops)."""
+    om, xpy = S.casida_sop(s.o_ov, s.delta)
+    ref, bound = 0.0, 0.0
+    for c2, i in enumerate(s.core_idx):
+        if groups[c2] != groups[c]:
+            continue
+        rho = S.transition_moments(s.o_ov, xpy, s.o_core[int(i), c])
+        x = omega - s.eps[i]
+        ref += float(np.sum(rho**2 * s.eta / ((x + om) ** 2 + s.eta**2)))
+        bound += float(np.sum(rho**2 * s.eta / (abs(x) + om) ** 2))
+    return ref, bound
+
+
+def test_group_decoupling_equals_sum_over_symmetry_equivalent_poles():
+    # Eq. sigma_spectral_decoupled_symmetric: the group form is the RPA pole sum over the group's
+    # members, each with its own transition moments rho_{i n} and its own pole position eps_i - Omega
+    eps, n_occ, core_idx, o_ov, o_core, eta = mirrored_two_core_system()
+    s = G.System(eps, n_occ, core_idx, o_ov, o_core, eta, n_im=8)
+    groups = [0, 0, 1]
+    om, _ = S.casida_sop(s.o_ov, s.delta)
+    ws = [eps[0] - om[0] - 0.3 * eta, eps[0] - om[3], eps[0] - 0.37, eps[0] + 0.01, eps[2] - om[1]]
+    for w in ws:
+        got = s.im_sigma_dec_group(float(w), groups)
+        for c in range(3):
+            ref, bound = _group_sop_reference(s, float(w), groups, c)
+            assert abs(got[c] - ref) <= bound * (1.0 + 1e-9) + 1e-13, (w, c, got[c], ref, bound)
+        # the two mirror images see the same group sum; the off-diagonal member contributes
+        assert abs(got[0] - got[1]) <= 1e-12 * max(1e-12, abs(got[0]))
+        diag = s.sigma_c(float(w))[1]
+        assert abs(got[2] - diag[2]) <= 1e-14 * max(1.0, abs(diag[2]))  # a one-member group is DIAG
+
+
+def test_group_decoupling_uses_each_members_own_residue_frequency():
+    # non-degenerate members: the residue of member i sits at |eps_i - w| (checked against the pole sum)
+    m = synth.small(n_states=16, n_occ=5, n_core=3, n_aux=9, seed=44, n_high=2)
+    s = G.System.from_molecule(m, n_im=8)
+    groups = [0, 0, 0]
+    om, _ = S.casida_sop(s.o_ov, s.delta)
+    for w in (m.eps[0] - om[0], m.eps[2] - om[0], m.eps[1] - om[2]):
+        got = s.im_sigma_dec_group(float(w), groups)
+        for c in range(3):
+            ref, bound = _group_sop_reference(s, float(w), groups, c)
+            assert abs(got[c] - ref) <= bound * (1.0 + 1e-9) + 1e-13, (w, c, got[c], ref, bound)
+        # every member on its own resonance carries weight: the group sum is not the DIAG value
+        assert np.max(np.abs(got - s.sigma_c(float(w))[1])) > 1e-3 * np.max(np.abs(got))
+
+
 # ----------------------------------------------------------------------------------------
 # Exchange (Eq. sigma_x): brute force over (n i | i n) with (mn|kl) = sum_P O^P_mn O^P_kl
 # ----------------------------------------------------------------------------------------
@@ -467,6 +539,26 @@ def test_thiele_interpolates_and_reproduces_rational_functions():
     a = G.thiele_coefficients(zr, w(zr))
     zt = np.array([0.55 + 1e-3j, 2.7 + 1e-3j, 1.1j, 7.0 + 1e-3j])
     assert np.max(np.abs(G.thiele_eval(a, zr, zt) - w(zt))) < 1e-8 * np.max(np.abs(w(zt)))
+
+
+def test_wac_reference_points_follow_the_printed_parameters():
+    # Sec. "Computational Details": N_C = N_V = 100 real points; core region w_C in [0, 40] eV; valence
+    # region from 8 % below to 1 % above the range of |eps_m - w| of the residues of the non-core
+    # occupied states. Hand-built three-level case: core -10.4, valence -0.5, virtual 2.0 Ha,
+    # eps_F = 0.75; at w = -10.5 and -10.0 the valence residue sits at x = 10.0 and 9.5 Ha.
+    eps = np.array([-10.4, -0.5, 2.0])
+    x = G.wac_reference_points(eps, 2, [0], [-10.5, -10.0], 0.75)
+    assert x.size == 200
+    core, val = x[:100], x[100:]
+    assert core[0] == 0.0 and abs(core[-1] - 40.0 / 27.211386245988) < 1e-12  # 40 eV = 1.46998 Ha
+    assert np.allclose(np.diff(core), core[-1] / 99, rtol=0, atol=1e-14)
+    assert abs(val[0] - 9.5 * 0.92) < 1e-12 and abs(val[-1] - 10.0 * 1.01) < 1e-12
+    assert np.allclose(np.diff(val), (10.1 - 8.74) / 99, rtol=0, atol=1e-13)
+    # above the valence level no non-core occupied state has a residue: only the core region
+    assert G.wac_reference_points(eps, 2, [0], [0.1], 0.75).size == 100
+    # the core's own residue does not move the valence window
+    x2 = G.wac_reference_points(eps, 2, [0], [-10.5, -10.0, -10.4], 0.75)
+    assert np.array_equal(x2, x)
 
 
 def test_cdwac_equals_cd_when_w_has_few_poles():
