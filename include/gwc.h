@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define GWC_ABI_VERSION 1
+#define GWC_ABI_VERSION 2
 
 typedef enum {
   GWC_OK = 0,
@@ -99,6 +99,12 @@ typedef struct {
   int profile;           /* nonzero: time the chi0, factorisation and solve kernels with CUDA
                             events on the launching stream (accumulated in gwc_stats)          */
   int qp_mode;           /* gwc_qp_mode: how gwc_qp_solve and the request step get eps^QP     */
+  int wait_us;           /* bound of every device-side wait of the tensor-core kernels, in
+                            microseconds (0: one second). A wait that runs out stops its
+                            kernel's work on that tile or matrix, which drains the copies and
+                            MMAs it issued, frees its tensor memory and records
+                            GWC_ERR_TIMEOUT (reported by gwc_sync); the results of that call
+                            are undefined, and the context stays usable. 0..60000000          */
 } gwc_options;
 
 /* GWC_QP_SECANT: iterate the G_dH W0 QP equation (eq quasiparticle_equation with the shifted
@@ -128,7 +134,7 @@ typedef struct {
 typedef struct gwc_ctx gwc_ctx;
 
 /* Fills o with the defaults: eta 1e-3, n_im 32, xi0 1, BF16X3, DIAG, n_t 2^16, t_max 2000,
- * max_qp_iter 50, qp_tol 1e-7, batch 0, profile 0, qp_mode SECANT. */
+ * max_qp_iter 50, qp_tol 1e-7, batch 0, profile 0, qp_mode SECANT, wait_us 0 (one second). */
 gwc_status gwc_default_options(gwc_options* o);
 
 /* Device bytes a context of this shape allocates (resident copies + workspace + the
@@ -273,8 +279,13 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
  * that loads libgwc until the process exits); limits: n_core*n_t <= GWC_NOALLOC_MAX_WORK,
  * n_core*n_omega <= GWC_NOALLOC_MAX_COEF, n_t a power of two in 16..2^18, n_omega <= 8192.
  * Larger sizes return GWC_ERR_INVALID_ARG (message in gwc_last_error(NULL)) before any launch.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. All calls share the array: calls that
+ * Set-up: the first call in a device's context looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for that context (a context created after a device reset
+ * is looked up anew). With CUDA's lazy module loading that first call also loads the library's
+ * module on the device, which is when the array takes its device memory, and a call with
+ * n_omega > 3072 sets the cumulant kernel's shared-memory attribute. So make one warm-up call per
+ * device, with the largest n_omega you will use, before any stream capture and before a memory
+ * budget applies; later calls then allocate nothing. All calls share the array: calls that
  * overlap on the GPU (other streams, unsynchronised threads) race and must be serialised.
  * Every scratch element a call reads is written earlier in the same call, so stale contents
  * of a previous call never reach the output. */

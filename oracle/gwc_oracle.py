@@ -325,7 +325,11 @@ class System:
         return eqp, dh, iters
 
 
-def evgw0(system: "System", tol: float = 1e-8, max_iter: int = 100):
+class NotConverged(RuntimeError):
+    """An iteration stopped without meeting its tolerance (evgw0 with on_fail="raise")."""
+
+
+def evgw0(system: "System", tol: float = 1e-8, max_iter: int = 100, on_fail: str = "return"):
     """Eigenvalue self-consistency in G with W fixed (evGW0; Sec. "GW for core-levels: beyond
     G0W0", Eq. ev_sigma_spectral): the orbital energies in G are replaced by the current QP
     energies of EVERY state while W keeps the RPA excitations of the input energies, so the
@@ -336,19 +340,31 @@ def evgw0(system: "System", tol: float = 1e-8, max_iter: int = 100):
         eps^(k+1)_n = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n[G(eps^(k))](eps^(k)_n),
     so that the first step is eps_n + dH_n (the Hedin shift of Eq. hedin_shift is the first
     iteration of evGW0), with eps_F the midpoint of the current QP HOMO and LUMO, until
-    max_n |eps^(k+1)_n - eps^(k)_n| < tol. Returns (eps_qp [n_states], iterations)."""
+    max_n |eps^(k+1)_n - eps^(k)_n| < tol. The scheme stops without converging when max_iter steps
+    do not reach tol, or when an iterate moves a state across eps_F (an occupied QP energy at or above
+    the midpoint of the QP HOMO and LUMO, or a virtual one below it: the occupations of G would no
+    longer be the input's). Returns (eps_qp [n_states], iterations); on a stop without convergence it
+    returns the last iterate and max_iter (or the steps done before the crossing), or raises
+    NotConverged with on_fail="raise"."""
     n = system.n_states
     if system.n_core != n or np.any(system.core_idx != np.arange(n)):
         raise ValueError("evgw0 needs every state as a core (core_idx = 0..n_states-1)")
     sx, vxc = system.sigma_x(), system.v_xc()
     e = system.eps.copy()
     for it in range(1, max_iter + 1):
+        ef = fermi_level(e, system.n_occ)
+        if np.any(e[: system.n_occ] >= ef) or np.any(e[system.n_occ :] < ef):
+            if on_fail == "raise":
+                raise NotConverged(f"evGW0: QP energies crossed eps_F at iteration {it}")
+            return e, it - 1
         s = system.with_g_energies(e)
         new = np.array([system.eps[c] + sx[c] - vxc[c] + s.sigma_c(float(e[c]))[0][c].real for c in range(n)])
         done = np.max(np.abs(new - e)) < tol
         e = new
         if done:
             return e, it
+    if on_fail == "raise":
+        raise NotConverged(f"evGW0 did not reach tol {tol} in {max_iter} steps")
     return e, max_iter
 
 

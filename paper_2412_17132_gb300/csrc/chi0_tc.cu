@@ -23,7 +23,7 @@
 //     segment's part-0 MMAs run, so the tensor pipe does not wait for a whole fold. The last
 //     fold writes alpha * Pi + beta * I (eps = 1 - Pi for alpha = -1, beta = 1) to global memory.
 //
-// Every wait on an mbarrier is bounded (one second); on expiry the CTA records kStatTimeout,
+// Every wait on an mbarrier is bounded (one second unless the context sets another bound); on expiry the CTA records kStatTimeout,
 // stops issuing work, drains the copies and MMAs it issued and frees TMEM.
 #include <cuda.h>
 
@@ -80,6 +80,7 @@ struct TcParams {
   long long ldm, mat_stride;
   const int* active;
   unsigned* status;
+  unsigned long long wait_ns;  // bound of every mbarrier wait
 };
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 128.
@@ -189,12 +190,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int issued = 0;
       for (int kc = 0; kc < p.n_kc; ++kc) {
         const int s = kc % NB_ST, u = kc / NB_ST;
-        if (!mbar_wait(smem_u32(&b_empty[s]), (u & 1) ^ 1, abort_flag)) break;
+        if (!mbar_wait(smem_u32(&b_empty[s]), (u & 1) ^ 1, abort_flag, p.wait_ns)) break;
         mbar_expect_tx(smem_u32(&b_full[s]), b_bytes);
         uint8_t* bd = b_ring + s * 2 * TILE;
         tma_load_2d(smem_u32(bd), &tm_hi, kc * BK, Q0, smem_u32(&b_full[s]));
         if (p.split3) tma_load_2d(smem_u32(bd + TILE), &tm_lo, kc * BK, Q0, smem_u32(&b_full[s]));
-        if (!mbar_wait(smem_u32(&r_empty[s]), (u & 1) ^ 1, abort_flag)) {
+        if (!mbar_wait(smem_u32(&r_empty[s]), (u & 1) ^ 1, abort_flag, p.wait_ns)) {
           issued = kc + 1;  // the B copy of this chunk is in flight
           break;
         }
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool split3 = p.split3 != 0;
       for (int kc = 0; kc < p.n_kc && ok; ++kc) {
         const int s = kc % NB_ST, u = kc / NB_ST;
-        if (!mbar_wait(smem_u32(&b_full[s]), u & 1, abort_flag)) {
+        if (!mbar_wait(smem_u32(&b_full[s]), u & 1, abort_flag, p.wait_ns)) {
           ok = false;
           break;
         }
@@ -234,11 +235,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int part = 0; part < n_parts; ++part, ++a) {
           const int t = a % NA_ST, ua = a / NA_ST;
           // a new segment overwrites this part's fresh accumulator: its previous fold must be done
-          if (seg_start && kc > 0 && !mbar_wait(smem_u32(&fold_done[part]), (kc / kSeg - 1) & 1, abort_flag)) {
+          if (seg_start && kc > 0 && !mbar_wait(smem_u32(&fold_done[part]), (kc / kSeg - 1) & 1, abort_flag, p.wait_ns)) {
             ok = false;
             break;
           }
-          if (!mbar_wait(smem_u32(&a_full[t]), ua & 1, abort_flag)) {
+          if (!mbar_wait(smem_u32(&a_full[t]), ua & 1, abort_flag, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int a = 0;
     for (int kc = 0; kc < p.n_kc; ++kc) {
       const int s = kc % NB_ST, u = kc / NB_ST;
-      if (!mbar_wait(smem_u32(&r_full[s]), u & 1, abort_flag)) break;
+      if (!mbar_wait(smem_u32(&r_full[s]), u & 1, abort_flag, p.wait_ns)) break;
       float raw[32];
       const uint8_t* rrow = r_ring + s * RAW + h * (RAW / 2) + r * 128;
 #pragma unroll
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int part = 0; part < n_parts; ++part, ++a) {
         const int t = a % NA_ST, ua = a / NA_ST;
-        if (!mbar_wait(smem_u32(&a_empty[t]), (ua & 1) ^ 1, abort_flag)) {
+        if (!mbar_wait(smem_u32(&a_empty[t]), (ua & 1) ^ 1, abort_flag, p.wait_ns)) {
           ok = false;
           break;
         }
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool last = seg == n_seg - 1;
       if (!last) {
         for (int part = 0; part < n_parts; ++part) {
-          ok = mbar_wait(smem_u32(&seg_full[part]), seg & 1, abort_flag);
+          ok = mbar_wait(smem_u32(&seg_full[part]), seg & 1, abort_flag, p.wait_ns);
           ok = __all_sync(0xffffffffu, ok);
           if (!ok) break;
           tc_fence_after();
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       } else {
         for (int part = 0; part < n_parts && ok; ++part) {
-          ok = mbar_wait(smem_u32(&seg_full[part]), seg & 1, abort_flag);
+          ok = mbar_wait(smem_u32(&seg_full[part]), seg & 1, abort_flag, p.wait_ns);
           ok = __all_sync(0xffffffffu, ok);
         }
         if (!ok) break;
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32, int ld_pad,
                    int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F, bool complex_out,
                    double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
-                   unsigned* status, cudaStream_t s) {
+                   unsigned* status, unsigned long long wait_ns, cudaStream_t s) {
   if (!tc_supported()) return -2;
   if (n_aux_pad % BM || n_ov_pad % BK || ld_pad != n_ov_pad || ld_dtab % BK) return -2;
   // TMA: 16-B aligned bases, row strides multiples of 16 B, x coordinates multiples of 64 / 32
@@ -484,6 +485,7 @@ int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* 
   p.mat_stride = mat_stride;
   p.active = active;
   p.status = status;
+  p.wait_ns = wait_ns;
   const int nt = n_aux_pad / BM;
   dim3 grid(nt * (nt + 1) / 2, (F + p.fpc - 1) / p.fpc);
   static bool attr_c = false, attr_r = false;

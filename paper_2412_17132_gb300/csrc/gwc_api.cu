@@ -199,6 +199,7 @@ gwc_status validate_options(const gwc_options* o, int n_core) {
   if (!(o->qp_tol > 0.0)) return fail(nullptr, GWC_ERR_INVALID_ARG, "qp_tol must be > 0");
   if (o->batch < 0 || o->batch > 4096) return fail(nullptr, GWC_ERR_INVALID_ARG, "batch must be in 0..4096");
   if (o->qp_mode < 0 || o->qp_mode > 2) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad qp_mode");
+  if (o->wait_us < 0 || o->wait_us > 60000000) return fail(nullptr, GWC_ERR_INVALID_ARG, "wait_us must be in 0..6e7");
   (void)n_core;
   return GWC_OK;
 }
@@ -321,7 +322,7 @@ gwc_status run_chi0_any(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, 
   } else {
     int n = launch_chi0_tc(prec == GWC_PREC_BF16X3, ctx->d_o_hi, ctx->d_o_lo, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux,
                            ctx->n_aux_pad, ctx->n_ov_pad, (const float*)ctx->d_dtab, ctx->ld_dtab, F, complex_z, alpha,
-                           beta, out, ctx->ldm, stride, active, ctx->d_status, st);
+                           beta, out, ctx->ldm, stride, active, ctx->d_status, ctx->wait_ns, st);
     if (n == -2) return fail(ctx, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for this shape/device");
     LAUNCH(n);
     if (full) {
@@ -330,8 +331,10 @@ gwc_status run_chi0_any(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, 
     }
   }
   ev_end(ctx, kClsChi0, ev, st);
-  ctx->stats.chi0_builds += F;
-  ctx->stats.chi0_flop += (double)F * (complex_z ? 2.0 : 1.0) * (double)ctx->n_aux * (ctx->n_aux + 1.0) * (double)ctx->n_ov;
+  if (!active) {  // masked launches (QP rounds) are counted on the device: only the builds they do
+    ctx->stats.chi0_builds += F;
+    ctx->stats.chi0_flop += (double)F * (complex_z ? 2.0 : 1.0) * (double)ctx->n_aux * (ctx->n_aux + 1.0) * (double)ctx->n_ov;
+  }
   return GWC_OK;
 }
 
@@ -340,7 +343,7 @@ int launch_factor(gwc_ctx* ctx, MatKind kind, void* mats, int n, int nrow, long 
                   cudaStream_t st) {
   const bool mixed = ctx->opt.prec == GWC_PREC_BF16 || ctx->opt.prec == GWC_PREC_BF16X3;
   if (kind == MatKind::CplxF32 && mixed && ctx->factor_tc) {
-    const int r = launch_ldlt_tc(mats, n, nrow, ctx->ldm, stride, F, act, ctx->d_status, st);
+    const int r = launch_ldlt_tc(mats, n, nrow, ctx->ldm, stride, F, act, ctx->d_status, ctx->wait_ns, st);
     if (r != -2) return r;
   }
   return launch_ldlt(kind, mats, n, nrow, ctx->ldm, stride, F, act, ctx->d_status, st);
@@ -447,10 +450,25 @@ gwc_status residue_batches_buf(gwc_ctx* ctx, int n_pairs, const double* z_dev, c
                                  (long long)r * 2, act, st));
       ev_end(ctx, kClsSolve, evs, st);
     }
-    ctx->stats.factorizations += nb;
-    ctx->stats.factor_flop += factor_flop(ctx->n_aux, true, nb);
+    if (!act) {
+      ctx->stats.factorizations += nb;
+      ctx->stats.factor_flop += factor_flop(ctx->n_aux, true, nb);
+    }
   }
   return GWC_OK;
+}
+
+// Folds the builds that masked launches really did (counted by the QP pair kernel) into the stats.
+void fold_active_builds(gwc_ctx* ctx) {
+  if (!ctx->d_active_builds) return;
+  unsigned long long n = 0;
+  if (cudaMemcpy(&n, ctx->d_active_builds, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess) return;
+  const unsigned long long add = n - ctx->active_folded;
+  ctx->active_folded = n;
+  ctx->stats.chi0_builds += (long long)add;
+  ctx->stats.chi0_flop += (double)add * 2.0 * (double)ctx->n_aux * (ctx->n_aux + 1.0) * (double)ctx->n_ov;
+  ctx->stats.factorizations += (long long)add;
+  ctx->stats.factor_flop += (double)add * factor_flop(ctx->n_aux, true, 1);
 }
 
 gwc_status residue_batches(gwc_ctx* ctx, int n_pairs, const double* z_dev, const int* rows_dev, int r, double* w_out,
@@ -469,7 +487,7 @@ gwc_status enqueue_qp(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, bool
   const int rounds = hedin ? 1 : ctx->opt.max_qp_iter + 2;
   for (int r = 0; r < rounds; ++r) {
     LAUNCH(launch_qp_pairs(ctx->d_eps, ctx->d_core_idx, nc, no, ctx->eps_f, ctx->opt.eta, ctx->d_qp, ctx->d_qp_z,
-                           ctx->d_qp_active, ctx->d_qp_fac, ctx->d_all_done, st));
+                           ctx->d_qp_active, ctx->d_qp_fac, ctx->d_all_done, ctx->d_active_builds, st));
     TRY(residue_batches(ctx, np, ctx->d_qp_z, ctx->d_qp_rowmap, 1, ctx->d_qp_w, ctx->d_qp_active, st));
     LAUNCH(launch_qp_assemble_update(ctx->d_eps, ctx->n_states, no, nc, ctx->d_core_idx, ctx->eps_f, ctx->d_xi,
                                      ctx->d_wxi, ctx->opt.n_im, ctx->d_wim, ctx->d_qp_w, ctx->d_qp_fac, ctx->d_sx,
@@ -537,6 +555,7 @@ gwc_status gwc_default_options(gwc_options* o) {
   o->batch = 0;
   o->profile = 0;
   o->qp_mode = GWC_QP_SECANT;
+  o->wait_us = 0;
   return GWC_OK;
 }
 
@@ -576,6 +595,7 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   ctx->n_core = s->n_core;
   ctx->n_ov = s->n_occ * ctx->n_virt;
   ctx->opt = *o;
+  ctx->wait_ns = o->wait_us > 0 ? 1000ull * (unsigned long long)o->wait_us : 1000000000ull;
   if (o->group_of_core) ctx->h_group.assign(o->group_of_core, o->group_of_core + s->n_core);
   ctx->opt.group_of_core = nullptr;
   Sizes z = sizes_of(s, o);
@@ -604,6 +624,9 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   CTRY(dalloc(ctx, &ctx->d_vxc_eff, s->n_core));
   CTRY(dalloc(ctx, &ctx->d_status, 4));
   CTRY(dalloc(ctx, &ctx->d_all_done, 1));
+  CTRY(dalloc(ctx, &ctx->d_active_builds, 1));
+  if (cudaMemset(ctx->d_active_builds, 0, sizeof(unsigned long long)) != cudaSuccess)
+    return bail(fail(ctx, GWC_ERR_CUDA, "counter reset failed"));
   if (!ctx->h_group.empty()) {
     CTRY(dalloc(ctx, &ctx->d_group, s->n_core));
     if (cudaMemcpy(ctx->d_group, ctx->h_group.data(), sizeof(int) * s->n_core, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -713,7 +736,8 @@ void gwc_destroy(gwc_ctx* ctx) {
                   ctx->d_qp_rowmap, ctx->d_all_done, ctx->d_cw_a, ctx->d_cw_b, ctx->d_coef, ctx->d_tw,
                   ctx->d_pair_z, ctx->d_pair_rows, ctx->d_zim, ctx->d_req_wrel, ctx->d_req_z, ctx->d_req_rows,
                   ctx->d_req_pair_of, ctx->d_req_w, ctx->d_req_im, ctx->d_req_a, ctx->d_req_nu, ctx->d_req_eqp,
-                  ctx->d_req_dh, ctx->d_req_it, ctx->d_eps_g, ctx->d_ev_sig, ctx->d_ev_diff};
+                  ctx->d_req_dh, ctx->d_req_it, ctx->d_eps_g, ctx->d_ev_sig, ctx->d_ev_diff, ctx->d_active_builds,
+                  ctx->d_ev_pidx, ctx->d_ev_pm, ctx->d_ev_pw, ctx->d_ev_z, ctx->d_ev_rows, ctx->d_ev_wres, ctx->d_ev_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& r : ctx->ev_pending) {
@@ -881,6 +905,53 @@ gwc_status gwc_set_g_energies(gwc_ctx* ctx, const double* eps_g, double eps_f, v
   return GWC_OK;
 }
 
+// Sigma^c_j(e_j) of every state j at its own current energy e_j, the only values evGW0 uses: one residue
+// pair per (j, m) with f_m(e_j) != 0, each with the single right-hand side o_mj (not all n cores), then
+// the diagonal assembly. Uses the G energies set by gwc_set_g_energies; synchronises `st`.
+static gwc_status evgw0_sigma_diag(gwc_ctx* ctx, const std::vector<double>& e, cudaStream_t st) {
+  const int n = ctx->n_states;
+  auto th = [](double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); };
+  const std::vector<double>& eg = g_eps_host(ctx);
+  const double ef = g_eps_f(ctx);
+  std::vector<int> pidx((size_t)n * n, -1), rows, pm;
+  std::vector<double> pw;
+  for (int j = 0; j < n; ++j)
+    for (int m = 0; m < n; ++m) {
+      const double f = -th(ef - eg[m]) * th(eg[m] - e[j]) + th(eg[m] - ef) * th(e[j] - eg[m]);
+      if (f == 0.0) continue;
+      if (pm.size() >= (size_t)std::numeric_limits<int>::max())
+        return fail(ctx, GWC_ERR_INVALID_ARG, "evGW0: too many residue pairs");
+      pidx[(size_t)j * n + m] = (int)pm.size();
+      pm.push_back(m);
+      pw.push_back(e[j]);
+      rows.push_back(m * n + j);  // o_core row (m, core j) = O^.(m, j)
+    }
+  const size_t np = pm.size();
+  if (np > ctx->ev_pair_cap) {
+    TRY(dalloc(ctx, &ctx->d_ev_pm, np));
+    TRY(dalloc(ctx, &ctx->d_ev_pw, np));
+    TRY(dalloc(ctx, &ctx->d_ev_z, 2 * np));
+    TRY(dalloc(ctx, &ctx->d_ev_rows, np));
+    TRY(dalloc(ctx, &ctx->d_ev_wres, 2 * np));
+    ctx->ev_pair_cap = np;
+  }
+  if (!ctx->d_ev_pidx) TRY(dalloc(ctx, &ctx->d_ev_pidx, (size_t)n * n));
+  if (!ctx->d_ev_w) TRY(dalloc(ctx, &ctx->d_ev_w, n));
+  CU(cudaMemcpyAsync(ctx->d_ev_pidx, pidx.data(), sizeof(int) * pidx.size(), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(ctx->d_ev_w, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if (np > 0) {
+    CU(cudaMemcpyAsync(ctx->d_ev_pm, pm.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(ctx->d_ev_pw, pw.data(), sizeof(double) * np, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(ctx->d_ev_rows, rows.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+    LAUNCH(launch_fill_z_pairs(g_eps_dev(ctx), ctx->d_ev_pm, ctx->d_ev_pw, (int)np, ctx->opt.eta, ctx->d_ev_z, st));
+    TRY(residue_batches(ctx, (int)np, ctx->d_ev_z, ctx->d_ev_rows, 1, ctx->d_ev_wres, nullptr, st));
+  }
+  LAUNCH(launch_sigma_diag(g_eps_dev(ctx), n, n, ctx->d_ev_w, ef, ctx->d_xi, ctx->d_wxi, ctx->opt.n_im, ctx->d_wim,
+                           ctx->d_ev_pidx, ctx->d_ev_wres, ctx->d_ev_sig, st));
+  CU(cudaStreamSynchronize(st));  // the host vectors above are read by the async copies
+  return GWC_OK;
+}
+
 gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int* iters, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
   if (!eps_qp || !iters || !(tol > 0.0) || max_iter < 1 || max_iter > 1000)
@@ -890,24 +961,28 @@ gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int
   for (int c = 0; c < n; ++c)
     if (ctx->h_core[c] != c) return fail(ctx, GWC_ERR_INVALID_ARG, "evGW0 needs core_idx = 0..n_states-1");
   cudaStream_t st = (cudaStream_t)stream;
-  if (!ctx->d_ev_sig) TRY(dalloc(ctx, &ctx->d_ev_sig, (size_t)n * n * 2));
+  if (!ctx->d_ev_sig) TRY(dalloc(ctx, &ctx->d_ev_sig, (size_t)n * 2));
   if (!ctx->d_ev_diff) TRY(dalloc(ctx, &ctx->d_ev_diff, 1));
   struct GReset {  // later calls see the input energies in G again, on every return path
     gwc_ctx* c;
     ~GReset() { c->g_set = false; }
   } g_reset{ctx};
+  TRY(compute_wim(ctx, st));
   std::vector<double> e(ctx->h_eps);
   CU(cudaMemcpyAsync(eps_qp, ctx->d_eps, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   gwc_status res = GWC_ERR_NOT_CONVERGED;
+  std::string why = "evGW0 did not converge within max_iter";
   int it = 0;
   while (it < max_iter) {
     ++it;
-    gwc_status r = gwc_set_g_energies(ctx, e.data(), NAN, stream);
-    if (r == GWC_OK) r = gwc_sigma_core(ctx, e.data(), n, ctx->d_ev_sig, nullptr, nullptr, stream);
-    if (r != GWC_OK) {
-      res = r;
+    if (gwc_set_g_energies(ctx, e.data(), NAN, stream) != GWC_OK) {
+      // an iterate moved a QP energy across the Fermi level: the occupations of G are no longer
+      // those of the input, and the scheme stops there
+      why = "evGW0: QP energies crossed eps_F at iteration " + std::to_string(it);
+      --it;
       break;
     }
+    TRY(evgw0_sigma_diag(ctx, e, st));
     unsigned long long bits = 0;
     CU(cudaMemsetAsync(ctx->d_ev_diff, 0, sizeof(unsigned long long), st));
     LAUNCH(launch_evgw0_update(ctx->d_eps, ctx->d_sx, ctx->d_vxc_eff, ctx->d_ev_sig, n, eps_qp, ctx->d_ev_diff, st));
@@ -922,8 +997,8 @@ gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int
     }
   }
   *iters = it;
-  if (res == GWC_ERR_NOT_CONVERGED) return fail(ctx, res, "evGW0 did not converge within max_iter");
-  return res;
+  if (res == GWC_ERR_NOT_CONVERGED) return fail(ctx, res, why);
+  return check_stream_error(ctx);
 }
 
 gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, void* stream) {
@@ -1371,6 +1446,7 @@ gwc_status gwc_sync(gwc_ctx* ctx, void* stream) {
 gwc_status gwc_get_stats(gwc_ctx* ctx, gwc_stats* out) {
   if (!ctx || !out) return GWC_ERR_INVALID_ARG;
   ev_flush(ctx);
+  fold_active_builds(ctx);
   *out = ctx->stats;
   return GWC_OK;
 }
@@ -1378,6 +1454,7 @@ gwc_status gwc_get_stats(gwc_ctx* ctx, gwc_stats* out) {
 gwc_status gwc_reset_stats(gwc_ctx* ctx) {
   if (!ctx) return GWC_ERR_INVALID_ARG;
   ev_flush(ctx);
+  fold_active_builds(ctx);
   ctx->stats = gwc_stats{};
   return GWC_OK;
 }

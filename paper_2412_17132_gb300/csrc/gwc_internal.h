@@ -115,7 +115,7 @@ int launch_chi0_simt(MatKind kind, const void* o_ov /*double or float [n_aux][ld
 int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32, int ld_pad,
                    int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F, bool complex_out,
                    double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
-                   unsigned* status, cudaStream_t s);
+                   unsigned* status, unsigned long long wait_ns, cudaStream_t s);
 
 // Batched in-place LDL^T of F matrices [nrow][ldm]: the first n columns are factored (W = L D below
 // the diagonal, d on it, L^T above it); rows n..nrow-1 are appended right-hand sides that the row
@@ -125,7 +125,7 @@ int launch_ldlt(MatKind kind, void* mats, int n, int nrow, long long ldm, long l
 // Same contract for complex FP32 matrices, trailing updates on the tensor cores (3xTF32).
 // Returns -2 if the device has no tcgen05.
 int launch_ldlt_tc(void* mats, int n, int nrow, long long ldm, long long mat_stride, int F, const int* active,
-                   unsigned* status, cudaStream_t s);
+                   unsigned* status, unsigned long long wait_ns, cudaStream_t s);
 // Appended rows: row n+q of matrix f = o_core row row_of[f*r+q]; bnorm2 = |b|^2.
 int launch_border_rows(MatKind kind, void* mats, int n, long long ldm, long long stride, const double* src,
                        long long src_row_stride, const int* row_of, int F, int r, double* bnorm2, cudaStream_t s);
@@ -150,6 +150,11 @@ int launch_fill_z_pairs(const double* eps, const int* pair_m, const double* pair
                         cudaStream_t s);
 
 // Self-energy assembly on a grid: see sigma.cu
+// sigma [n_core][2] = Sigma^c_j(omega_j) of core j at its own frequency; wres1 [pair][2] (one RHS per pair)
+int launch_sigma_diag(const double* eps, int n_states, int n_core, const double* omega, double eps_f, const double* xi,
+                      const double* wxi, int n_im, const double* wim, const int* pidx, const double* wres1, double* sigma,
+                      cudaStream_t s);
+// e[k] = eps_k + sx_k - vxc_k + Re sigma[k] (sigma [n][2]); diff_bits = max |change| as double bits
 int launch_evgw0_update(const double* eps, const double* sx, const double* vxc, const double* sigma, int n, double* e,
                         unsigned long long* diff_bits, cudaStream_t s);
 int launch_sigma_grid(const double* eps, int n_states, int n_core, const int* core_idx, const double* omega, int n_w,
@@ -167,7 +172,8 @@ struct QpState {
 };
 int launch_qp_init(const double* eps, const int* core_idx, int n_core, QpState* st, cudaStream_t s);
 int launch_qp_pairs(const double* eps, const int* core_idx, int n_core, int n_occ, double eps_f, double eta,
-                    const QpState* st, double* z, int* active, double* fac, int* all_done, cudaStream_t s);
+                    const QpState* st, double* z, int* active, double* fac, int* all_done,
+                    unsigned long long* active_count /*+= active pairs, or null*/, cudaStream_t s);
 int launch_qp_assemble_update(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx,
                               double eps_f, const double* xi, const double* wxi, int n_im, const double* wim,
                               const double* wpair /*[n_core*n_occ][2]*/, const double* fac, const double* sx,
@@ -229,6 +235,7 @@ struct gwc_ctx {
   int n_states = 0, n_occ = 0, n_virt = 0, n_aux = 0, n_core = 0, n_ov = 0;
   int n_aux_pad = 0, n_ov_pad = 0;
   gwc_options opt{};
+  unsigned long long wait_ns = 1000000000ull;  // bound of the tensor-core kernels' device waits
   double eps_f = 0.0;
   bool vxc_given = false;
   std::vector<double> h_eps;
@@ -287,6 +294,10 @@ struct gwc_ctx {
   double* d_qp_w = nullptr;     // [n_core*n_occ][2]
   int* d_qp_rowmap = nullptr;   // [n_core*n_occ]
   int* d_all_done = nullptr;
+  // builds of masked launches (QP rounds) that are not skipped: counted on the device, folded into
+  // the stats by gwc_get_stats / gwc_reset_stats
+  unsigned long long* d_active_builds = nullptr;
+  unsigned long long active_folded = 0;
 
   // cumulant
   double *d_cw_a = nullptr, *d_cw_b = nullptr, *d_coef = nullptr, *d_tw = nullptr;
@@ -314,8 +325,17 @@ struct gwc_ctx {
   double* d_eps_g = nullptr;
   double eps_f_g = 0.0;
   bool cores_occupied = true;   // every core_idx < n_occ (needed by the QP, request and CD-WAC paths)
-  double* d_ev_sig = nullptr;   // evGW0: [n_states][n_states][2] self-energies at the current energies
+  double* d_ev_sig = nullptr;   // evGW0: [n_states][2] Sigma^c_j(eps_j) at the current energies
   unsigned long long* d_ev_diff = nullptr;  // evGW0: max |eps_new - eps| as the bits of a double
+  // evGW0 diagonal residue plan: pair (j, m) with one right-hand side o_mj
+  int* d_ev_pidx = nullptr;      // [n_states][n_states] -> pair or -1
+  int* d_ev_pm = nullptr;        // [pairs] residue state m
+  double* d_ev_pw = nullptr;     // [pairs] frequency e_j
+  double* d_ev_z = nullptr;      // [pairs][2]
+  int* d_ev_rows = nullptr;      // [pairs] o_core row m * n_core + j
+  double* d_ev_wres = nullptr;   // [pairs][2]
+  double* d_ev_w = nullptr;      // [n_states] current energies
+  size_t ev_pair_cap = 0;
 
   // host staging
   int* h_pin_i = nullptr;

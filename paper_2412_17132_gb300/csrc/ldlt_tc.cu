@@ -295,6 +295,7 @@ struct TcSmem {
   uint32_t* tmem_slot;
   volatile int* abort_flag;
   int* sing;
+  unsigned long long wait_ns;  // bound of every mbarrier wait
 };
 
 // Iterates the (row tile, column tile, half) stages of one panel in issue order.
@@ -345,7 +346,7 @@ __device__ void transform_role(const TcSmem& sm, const float2* A, int n, int nro
   bool ok = true;
   for (int tI = 0; tI < n_ti && ok; ++tI, ++rt) {
     // A operand of row tile tI: W[i0 + row][k0 .. k0 + 64), four threads per row (64 bytes each)
-    if (!mbar_wait(smem_u32(sm.a_empty), (rt & 1) ^ 1, sm.abort_flag)) break;
+    if (!mbar_wait(smem_u32(sm.a_empty), (rt & 1) ^ 1, sm.abort_flag, sm.wait_ns)) break;
     {
       const int rq = tt & 3, rr = tt >> 2;
       const int i0 = R0 + TM * tI;
@@ -388,7 +389,7 @@ __device__ void transform_role(const TcSmem& sm, const float2* A, int n, int nro
     const int nc = tile_cols(R0, n, tI);
     for (int q = 0; q < 2 * nc; ++q, ++seq) {
       const int s = seq & 1, us = seq >> 1;
-      if (!mbar_wait(smem_u32(&sm.b_empty[s]), (us & 1) ^ 1, sm.abort_flag)) {
+      if (!mbar_wait(smem_u32(&sm.b_empty[s]), (us & 1) ^ 1, sm.abort_flag, sm.wait_ns)) {
         ok = false;
         break;
       }
@@ -425,12 +426,12 @@ __device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, in
   bool ok = true;
   const uint32_t abase = smem_u32(sm.base);
   for (int tI = 0; tI < n_ti && ok; ++tI, ++rt) {
-    if (!mbar_wait(smem_u32(sm.a_full), rt & 1, sm.abort_flag)) break;
+    if (!mbar_wait(smem_u32(sm.a_full), rt & 1, sm.abort_flag, sm.wait_ns)) break;
     tc_fence_after();
     const int nc = tile_cols(R0, n, tI);
     for (int tJ = 0; tJ < nc && ok; ++tJ, ++tcount) {
       const int b = tcount & 1, ub = tcount >> 1;
-      if (!mbar_wait(smem_u32(&sm.tempty[b]), (ub & 1) ^ 1, sm.abort_flag)) {
+      if (!mbar_wait(smem_u32(&sm.tempty[b]), (ub & 1) ^ 1, sm.abort_flag, sm.wait_ns)) {
         ok = false;
         break;
       }
@@ -438,7 +439,7 @@ __device__ void mma_role(const TcSmem& sm, uint32_t tmem_base, int n, int R0, in
       const uint32_t dp = tmem_base + (uint32_t)(b * 256), dq = dp + 128;  // P and Q accumulators
       for (int h = 0; h < 2; ++h, ++seq) {
         const int s = seq & 1, us = seq >> 1;
-        if (!mbar_wait(smem_u32(&sm.b_full[s]), us & 1, sm.abort_flag)) {
+        if (!mbar_wait(smem_u32(&sm.b_full[s]), us & 1, sm.abort_flag, sm.wait_ns)) {
           ok = false;
           break;
         }
@@ -542,7 +543,7 @@ __device__ void epilogue_role(const TcSmem& sm, uint32_t tmem_base, float2* __re
     const int nc = tile_cols(R0, n, tI);
     for (int tJ = 0; tJ < nc; ++tJ, ++tcount) {
       const int b = tcount & 1, ub = tcount >> 1;
-      ok = mbar_wait(smem_u32(&sm.tfull[b]), ub & 1, sm.abort_flag);
+      ok = mbar_wait(smem_u32(&sm.tfull[b]), ub & 1, sm.abort_flag, sm.wait_ns);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
@@ -608,7 +609,7 @@ __device__ void epilogue_role(const TcSmem& sm, uint32_t tmem_base, float2* __re
 
 __global__ void __launch_bounds__(NT_TC, 1)
     ldlt_tc_kernel(float2* __restrict__ mats, int n, int nrow, long long ldm, long long stride,
-                   const int* __restrict__ active, unsigned* __restrict__ status) {
+                   const int* __restrict__ active, unsigned* __restrict__ status, unsigned long long wait_ns) {
   const int f = blockIdx.x;
   if (active && !active[f]) return;  // uniform across the CTA, before any barrier or TMEM use
   float2* A = mats + f * stride;
@@ -626,6 +627,7 @@ __global__ void __launch_bounds__(NT_TC, 1)
   sm.tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
   sm.abort_flag = reinterpret_cast<volatile int*>(sm.tmem_slot + 1);
   sm.sing = reinterpret_cast<int*>(sm.tmem_slot + 2);
+  sm.wait_ns = wait_ns;
   const PanelInv ps(sm.base);  // aliases the operand buffers (the phases alternate)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -704,7 +706,7 @@ __global__ void __launch_bounds__(NT_TC, 1)
 
 // Returns 1 (launches), -1 on a launch error or bad layout, -2 if the device has no tcgen05.
 int launch_ldlt_tc(void* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active,
-                   unsigned* status, cudaStream_t s) {
+                   unsigned* status, unsigned long long wait_ns, cudaStream_t s) {
   if (!tc_supported()) return -2;
   // 16-byte loads and stores: ldm and the matrix stride multiples of 4 complex values (32 B)
   if ((ldm % 4) || (stride % 4) || (reinterpret_cast<uintptr_t>(mats) & 15) || nrow < n || n < 1) return -1;
@@ -714,7 +716,8 @@ int launch_ldlt_tc(void* mats, int n, int nrow, long long ldm, long long stride,
       return -1;
     attr = true;
   }
-  ldlt_tc_kernel<<<F, NT_TC, SMEM_TC, s>>>(reinterpret_cast<float2*>(mats), n, nrow, ldm, stride, active, status);
+  ldlt_tc_kernel<<<F, NT_TC, SMEM_TC, s>>>(reinterpret_cast<float2*>(mats), n, nrow, ldm, stride, active, status,
+                                                wait_ns);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -12,7 +12,11 @@
 // 10.5 MB) until the process exits. All calls share it and it keeps the last call's contents;
 // every element a call reads is first written by that same call, so nothing is cleared. Calls
 // that overlap on the GPU (different streams, or threads that do not serialise) race on it.
+#include <cuda.h>
+
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "gwc_internal.h"
 
@@ -28,21 +32,54 @@ static_assert(GWC_NOALLOC_MAX_COEF == kMaxCoef, "header limit");
 
 __device__ __align__(256) double2 g_noalloc_scratch[kScratch2];
 
-std::mutex g_addr_mutex;
-double2* g_addr[128] = {nullptr};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
 
-// Device address of the scratch array on the current device (looked up once per device;
-// in host code the symbol itself is only a host-side stand-in, not a device address).
+// Unique id of the context current on this thread (cuCtxGetId: never reused within the process, so
+// a context created after a device reset gets a new id); false if the driver gives none.
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  CUcontext c = nullptr;
+  if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
+
+std::mutex g_addr_mutex;
+std::vector<std::pair<unsigned long long, double2*>> g_addr;  // (context id, device address)
+
+// Device address of the scratch array in the current device's context, looked up once per context
+// (in host code the symbol itself is only a host-side stand-in, not a device address). Without a
+// context id from the driver the address is looked up on every call.
 gwc_status scratch_address(double2** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return GWC_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return GWC_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_addr_mutex);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GWC_ERR_CUDA;
-    g_addr[dev] = static_cast<double2*>(p);
-  }
-  *out = g_addr[dev];
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
+  if (have_id)
+    for (const auto& e : g_addr)
+      if (e.first == id) {
+        *out = e.second;
+        return GWC_OK;
+      }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GWC_ERR_CUDA;
+  if (!have_id) have_id = current_context_id(&id);  // the lookup made the primary context current
+  if (have_id) g_addr.emplace_back(id, static_cast<double2*>(p));
+  *out = static_cast<double2*>(p);
   return GWC_OK;
 }
 

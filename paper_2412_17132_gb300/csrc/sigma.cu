@@ -105,7 +105,8 @@ __global__ void qp_init_kernel(const double* __restrict__ eps, const int* __rest
 
 __global__ void qp_pairs_kernel(const double* __restrict__ eps, const int* __restrict__ core_idx, int n_core, int n_occ,
                                 double eps_f, double eta, const QpState* __restrict__ st, double* __restrict__ z,
-                                int* __restrict__ active, double* __restrict__ fac, int* __restrict__ all_done) {
+                                int* __restrict__ active, double* __restrict__ fac, int* __restrict__ all_done,
+                                unsigned long long* __restrict__ active_count) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) {
     int d = 1;
@@ -118,6 +119,7 @@ __global__ void qp_pairs_kernel(const double* __restrict__ eps, const int* __res
   double f = st[c].done ? 0.0 : prefactor(eps[m], w, eps_f);
   fac[t] = f;
   active[t] = f != 0.0;
+  if (f != 0.0 && active_count) atomicAdd(active_count, 1ull);  // builds this round really does
   z[2 * t] = fabs(eps[m] - w);
   z[2 * t + 1] = eta;
 }
@@ -351,11 +353,44 @@ __global__ void sigma_grid_wac_kernel(const double* __restrict__ eps, int n_stat
 // sigma [n][n][2] the self-energies of all states on the grid of the current energies (so the
 // diagonal holds Sigma^c_n(e_n)). The largest change |e_new - e| goes to *diff_bits as the bit
 // pattern of a non-negative double (ordered like the value, so atomicMax is the maximum).
+// Sigma^c_j(w_j) of core j at its own frequency w_j only (evGW0: every state is a core, evaluated at
+// its own current energy). The residue pairs (w_j, m) carry the one right-hand side o_mj each, so
+// wres1 is [pair][2]; otherwise the terms of sigma_grid_kernel.
+__global__ void sigma_diag_kernel(const double* __restrict__ eps, int n_states, int n_core, const double* __restrict__ omega,
+                                  double eps_f, const double* __restrict__ xi, const double* __restrict__ wxi, int n_im,
+                                  const double* __restrict__ wim, const int* __restrict__ pidx,
+                                  const double* __restrict__ wres1, double* __restrict__ sigma) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= n_core) return;
+  const double w = omega[j];
+  double si = 0.0, rr = 0.0, ri = 0.0;
+  for (int m = lane; m < n_states; m += 32) {
+    const double em = eps[m];
+    si += imag_term(w - em, m, j, n_states, n_core, xi, wxi, n_im, wim);
+    const double f = prefactor(em, w, eps_f);
+    if (f != 0.0) {
+      const int p = pidx[(size_t)j * n_states + m];
+      rr += f * wres1[2 * (size_t)p];
+      ri += f * wres1[2 * (size_t)p + 1];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    si += __shfl_down_sync(0xffffffffu, si, o);
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+    ri += __shfl_down_sync(0xffffffffu, ri, o);
+  }
+  if (lane == 0) {
+    sigma[2 * (size_t)j] = -si + rr;
+    sigma[2 * (size_t)j + 1] = ri;
+  }
+}
+
 __global__ void evgw0_update_kernel(const double* __restrict__ eps, const double* __restrict__ sx,
                                     const double* __restrict__ vxc, const double* __restrict__ sigma, int n,
                                     double* __restrict__ e, unsigned long long* __restrict__ diff_bits) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const double e_new = eps[k] + sx[k] - vxc[k] + sigma[2 * ((size_t)k * n + k)];
+    const double e_new = eps[k] + sx[k] - vxc[k] + sigma[2 * (size_t)k];
     const double d = fabs(e_new - e[k]);
     e[k] = e_new;
     atomicMax(diff_bits, (unsigned long long)__double_as_longlong(d));
@@ -363,6 +398,15 @@ __global__ void evgw0_update_kernel(const double* __restrict__ eps, const double
 }
 
 }  // namespace
+
+int launch_sigma_diag(const double* eps, int n_states, int n_core, const double* omega, double eps_f, const double* xi,
+                      const double* wxi, int n_im, const double* wim, const int* pidx, const double* wres1, double* sigma,
+                      cudaStream_t s) {
+  const long long threads = 32LL * n_core;
+  sigma_diag_kernel<<<(int)((threads + 255) / 256), 256, 0, s>>>(eps, n_states, n_core, omega, eps_f, xi, wxi, n_im, wim,
+                                                                  pidx, wres1, sigma);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_evgw0_update(const double* eps, const double* sx, const double* vxc, const double* sigma, int n, double* e,
                         unsigned long long* diff_bits, cudaStream_t s) {
@@ -478,9 +522,11 @@ int launch_qp_init(const double* eps, const int* core_idx, int n_core, QpState* 
 }
 
 int launch_qp_pairs(const double* eps, const int* core_idx, int n_core, int n_occ, double eps_f, double eta,
-                    const QpState* st, double* z, int* active, double* fac, int* all_done, cudaStream_t s) {
+                    const QpState* st, double* z, int* active, double* fac, int* all_done,
+                    unsigned long long* active_count, cudaStream_t s) {
   int n = n_core * n_occ;
-  qp_pairs_kernel<<<(n + 127) / 128, 128, 0, s>>>(eps, core_idx, n_core, n_occ, eps_f, eta, st, z, active, fac, all_done);
+  qp_pairs_kernel<<<(n + 127) / 128, 128, 0, s>>>(eps, core_idx, n_core, n_occ, eps_f, eta, st, z, active, fac, all_done,
+                                                  active_count);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -12,7 +12,7 @@
 namespace gwc {
 namespace {
 
-constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s bound per wait
+constexpr unsigned long long kWaitNs = 1000000000ull;  // default bound per wait: 1 s (gwc_options.wait_us = 0)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -48,16 +48,43 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// try_wait whose suspension is capped at hint_ns (the instruction's suspend-time hint)
+__device__ __forceinline__ bool mbar_try_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait: false (and the CTA abort flag raised) if the phase does not complete within
-// kWaitNs, or if another role aborted already.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// limit_ns (the context's wait bound), or if another role aborted already.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   unsigned long long t0 = gtime();
+  if (limit_ns < kWaitNs) {
+    // a bound shorter than the default: each try suspends at most a quarter of it and the clock is
+    // read after every try, so the bound holds whatever the hardware's own suspension limit is
+    const uint32_t hint = (uint32_t)(limit_ns / 4 + 1);
+    for (;;) {
+      if (mbar_try_hint(bar, parity, hint)) return true;
+      if (*abort_flag) return false;
+      if (gtime() - t0 > limit_ns) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 255u) == 255u) {
       if (*abort_flag) return false;
-      if (gtime() - t0 > kWaitNs) {
+      if (gtime() - t0 > limit_ns) {
         *abort_flag = 1;
         return false;
       }

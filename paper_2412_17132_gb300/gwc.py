@@ -69,6 +69,7 @@ class Options(ctypes.Structure):
         ("batch", ctypes.c_int),
         ("profile", ctypes.c_int),
         ("qp_mode", ctypes.c_int),
+        ("wait_us", ctypes.c_int),
     ]
 
 
@@ -217,7 +218,7 @@ class Context:
 
     def __init__(self, eps, n_occ, core_idx, o_ov, o_core, *, vxc=None, eps_f=math.nan, eta=1e-3, n_im=32, xi0=1.0,
                  prec="bf16x3", dec="diag", groups=None, n_t=1 << 16, t_max=2000.0, max_qp_iter=50, qp_tol=1e-7,
-                 batch=0, profile=False, qp_mode="secant", stream=None):
+                 batch=0, profile=False, qp_mode="secant", wait_us=0, stream=None):
         self._ctx = ctypes.c_void_p()
         host = isinstance(eps, np.ndarray)
         self._keep = []
@@ -239,6 +240,7 @@ class Context:
         opt.max_qp_iter, opt.qp_tol, opt.batch = int(max_qp_iter), float(qp_tol), int(batch)
         opt.profile = 1 if profile else 0
         opt.qp_mode = QP[qp_mode]
+        opt.wait_us = int(wait_us)
         self.opt = opt
         self.prec = prec
         _check(lib().gwc_create(ctypes.byref(self._ctx), ctypes.byref(sysd), ctypes.byref(opt), _stream(stream)), None)
@@ -301,12 +303,13 @@ class Context:
         e = np.ascontiguousarray(np.asarray(eps_g, dtype=np.float64))
         _check(lib().gwc_set_g_energies(self._ctx, e.ctypes.data, float(eps_f), _stream(stream)), self._ctx)
 
-    def evgw0(self, tol=1e-8, max_iter=100, stream=None):
+    def evgw0(self, tol=1e-8, max_iter=100, stream=None, out=None):
         """evGW0 QP energies of every state (the context must list every state as a core): a CUDA
-        tensor [n_states] and the number of steps."""
+        tensor [n_states] and the number of steps. With `out` given, the last iterate is there even
+        when the call raises (GWC_ERR_NOT_CONVERGED)."""
         import torch
 
-        e = torch.empty((self.n_states,), dtype=torch.float64, device="cuda")
+        e = torch.empty((self.n_states,), dtype=torch.float64, device="cuda") if out is None else out
         it = ctypes.c_int(0)
         _check(lib().gwc_evgw0(self._ctx, float(tol), int(max_iter), _ptr(e), ctypes.byref(it), _stream(stream)), self._ctx)
         return e, it.value

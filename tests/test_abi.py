@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(libgwc):
 
 
 def test_abi_version_and_strings(libgwc):
-    assert libgwc.gwc_abi_version() == 1
+    assert libgwc.gwc_abi_version() == 2
     assert libgwc.gwc_status_string(4) == b"singular dielectric matrix"
 
 

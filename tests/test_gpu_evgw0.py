@@ -71,3 +71,20 @@ def test_virtual_cores_rejected_where_occupied_cores_are_needed(gwc):
         c.qp_solve()
     assert err.value.status == 1
     c.close()
+
+
+def test_evgw0_stop_without_convergence_matches_oracle(gwc):
+    """Two steps cannot reach 1e-14 Ha: the oracle raises, the library reports GWC_ERR_NOT_CONVERGED, and
+    the last iterate is the oracle's second iterate."""
+    s = _all_state_system()
+    with pytest.raises(G.NotConverged):
+        G.evgw0(s, tol=1e-14, max_iter=2, on_fail="raise")
+    ref, it_ref = G.evgw0(s, tol=1e-14, max_iter=2)
+    assert it_ref == 2
+    c = _ctx(gwc, s, "fp64")
+    e = torch.empty(s.n_states, dtype=torch.float64, device="cuda")
+    with pytest.raises(gwc.GwcError) as err:
+        c.evgw0(tol=1e-14, max_iter=2, out=e)
+    assert err.value.status == 5
+    assert np.max(np.abs(e.cpu().numpy() - ref)) < 1e-8
+    c.close()

@@ -70,6 +70,24 @@ def test_noalloc_matches_context_path_twice(gwc):
         assert float((a.sum(dim=1) * dnu - 1.0).abs().max()) < 1e-9
 
 
+def test_noalloc_at_the_size_limit_and_without_bins(gwc):
+    # n_core * n_t = 2^18 (the whole ping-pong buffers and twiddle table), n_omega = 4096 (the
+    # cumulant kernel above 48 KB of shared memory), then nu_out = NULL; both against the context path
+    n_core, n_w, n_t, t_max, eta = 4, 4096, 1 << 16, 2000.0, 1e-3
+    w, im = _inputs(n_core, n_w, 9)
+    a_ref, nu_ref = _with_context(n_core, n_t, t_max, eta, w, im)
+    peak = float(a_ref.abs().max())
+    for with_nu in (True, False):
+        a = torch.full((n_core, n_t), float("nan"), dtype=torch.float64, device="cuda")
+        nu = torch.empty((n_t,), dtype=torch.float64, device="cuda") if with_nu else None
+        gwc.cumulant_spectrum_noalloc(w, im, n_t, t_max, eta, a, nu)
+        torch.cuda.synchronize()
+        assert torch.isfinite(a).all()
+        assert float((a - a_ref).abs().max()) <= 1e-10 * peak
+        if with_nu:
+            assert float((nu - nu_ref).abs().max()) <= 1e-12
+
+
 def test_noalloc_rejects_sizes_beyond_the_static_scratch(gwc):
     lib = gwc.lib()
     w, im = _inputs(1, 10, 1)
