@@ -1,13 +1,21 @@
 #!/usr/bin/env python
 """Throughput of the GW+C core-level hot path on GB300: Sigma_c(w) points/s + chi0 TFLOP/s.
 
-One step = one pass of the whole path over the benzene-sized synthetic molecule
-(300 states, 21 occupied incl. six 1s cores, 1100 auxiliary functions, 800 real frequencies):
-residency of the inputs (precision copies of O), the imaginary-axis W table, every residue
-chi0 build / dielectric factorisation / contraction, the self-energy of all cores on the grid,
-the device QP iteration, and one cumulant spectrum per core (n_t = 2^16).
+Default workload: the pentacene-sized synthetic molecule (1300 states, 73 occupied incl. twenty-two
+1s cores, 4500 auxiliary functions, N_ov = 89 571) in the precision form (split-BF16 chi0 on the
+tensor cores, FP32-accurate 3xTF32 factorisation of eps; FP64 residues, assembly, QP and cumulant).
+One step is one pass of the whole path over a fixed, stated subset of that workload:
+  - residency: the inputs reloaded into the resident context (precision copies of O, Sigma^x);
+  - the imaginary-axis W table (33 real builds, factorisations and 28 600 contractions);
+  - the decoupled Im Sigma of all 22 cores on the 800-point relative grid (one residue build per
+    grid point with a residue, shared by the cores) and the cumulant spectrum of every core;
+  - the G_dH W0 QP energies (Hedin shift) of cores 0, 11 and 21;
+  - the full contour-deformation Sigma^c (-I + R) of all 22 cores at 4 of the 800 grid points.
+Points per step = the (core, w) self-energy values the step produces (decoupled Im Sigma points,
+full Sigma^c points, one Sigma^c(eps_n) per QP core), broken down in the JSON line.
+--workload benzene runs the whole benzene-sized job per step (all cores on the full grid).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|fp32|fp64|bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|bf16x3f64|fp32|fp64|bf16]
   python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample, same metric
 
 Under torchrun every rank runs an independent replica on its own GPU (the path needs no
@@ -39,8 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gwc", choices=["gwc", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16", "fp32", "fp64"])
-    ap.add_argument("--workload", default="benzene", choices=["benzene", "tiny", "pentacene", "batch", "serve"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16x3f64", "bf16", "fp32", "fp64"])
+    ap.add_argument("--workload", default="pentacene",
+                    choices=["pentacene", "benzene", "tiny", "pentacene-forms", "batch", "serve"])
+    ap.add_argument("--no-fp64-path", action="store_true", help="pentacene: skip the FP64 GPU path sample")
     ap.add_argument("--molecules", type=int, default=48, help="batched form: molecules in the graph")
     ap.add_argument("--omega-points", type=int, default=800, help="batched/serving/pentacene: grid points")
     ap.add_argument("--requests", type=int, default=2000, help="serving form: requests in the stream")
@@ -191,6 +201,9 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "pentacene":
+        print(json.dumps(run_reference_pentacene(args)), flush=True)
+        return 0
     mol = make_workload(args.workload)
     for _ in range(args.warmup):
         oracle_sample(mol, n_points=1)
@@ -302,10 +315,10 @@ def run_gpu(args):
         ctx.sigma_core(mol.omega, out=(sig, dec, sx))
         ctx.qp_solve(out=(eqp, dh, its))
         ctx.cumulant_spectrum(w_rel, dec, out=(a, nu))
-        if host:
-            sig_h.copy_(sig, non_blocking=True)
-            eqp_h.copy_(eqp, non_blocking=True)
-            a_h.copy_(a, non_blocking=True)
+        if host:  # results back through the C ABI (gwc_copy_out)
+            ctx.copy_out(sig_h, sig)
+            ctx.copy_out(eqp_h, eqp)
+            ctx.copy_out(a_h, a)
 
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
@@ -473,6 +486,364 @@ def run_gpu(args):
 
 
 # ------------------------------------------------------------------------------------------
+# Default workload: the pentacene-sized precision form, a fixed subset of the job per step
+# ------------------------------------------------------------------------------------------
+PENT_SIGMA_IDX = [100, 300, 500, 700]  # grid points of the full Sigma^c (100 and 700 are in the oracle file)
+PENT_QP_CORES = [0, 11, 21]  # cores whose QP energy the step computes (the oracle file's)
+PENT_N_OMEGA = 800
+
+
+def pent_grid_rel():
+    import numpy as np
+
+    return np.linspace(-25.0 / HARTREE_EV, 5.0 / HARTREE_EV, PENT_N_OMEGA)
+
+
+def pentacene_mol(device):
+    from paper_2412_17132_gb300 import synth
+
+    return synth.pentacene_device() if device else synth.pentacene()
+
+
+def pent_step_builds(eps, n_occ, core_idx, omega):
+    """Residue builds one pentacene step does, by phase (bookkeeping for the extrapolations of the
+    FP64 GPU path and the CPU oracle): a build per residue pair with a nonzero prefactor f_m, Theta(0) = 1/2."""
+    import numpy as np
+
+    ef = 0.5 * (eps[n_occ - 1] + eps[n_occ])
+
+    def nz(m, w):
+        th = lambda x: 1.0 if x > 0 else (0.0 if x < 0 else 0.5)  # noqa: E731
+        return -th(ef - eps[m]) * th(eps[m] - w) + th(eps[m] - ef) * th(w - eps[m]) != 0.0
+
+    dec = int(np.sum(pent_grid_rel() <= 0.0))  # occupied cores: a residue for w - eps_c <= 0
+    qp = sum(1 for c in PENT_QP_CORES for m in range(eps.size) if nz(m, float(eps[core_idx[c]])))
+    sig = sum(1 for j in PENT_SIGMA_IDX for m in range(eps.size) if nz(m, float(omega[j])))
+    return {"table": 33, "decoupled": dec, "qp": qp, "sigma": sig}
+
+
+def pent_points(n_core):
+    full = n_core * len(PENT_SIGMA_IDX)
+    return {"decoupled_im_sigma": n_core * PENT_N_OMEGA, "full_sigma": full, "qp_sigma": len(PENT_QP_CORES),
+            "total": n_core * PENT_N_OMEGA + full + len(PENT_QP_CORES)}
+
+
+def pent_oracle_sample(mol_host, builds, t_node=None):
+    """FP64 oracle on the pentacene-sized system: one residue build (chi0 at x + i eta, LU solve with the
+    22 core right-hand sides) and, unless t_node is given, one imaginary-axis node (real chi0, LU solve
+    with all 28 600 right-hand sides of the W table), timed; the step extrapolated as
+    33 T_node + residue builds x T_build."""
+    from oracle import gwc_oracle as G
+
+    s = G.System.from_molecule(mol_host)
+    t0 = time.perf_counter()
+    s.w_residue(30, abs(float(mol_host.eps[30]) - float(mol_host.omega[PENT_SIGMA_IDX[0]])))
+    t_build = time.perf_counter() - t0
+    measured = t_build
+    if t_node is None:
+        rhs = s.o_core.reshape(s.n_states * s.n_core, -1).T
+        t1 = time.perf_counter()
+        G.screened_wc(G.chi0(s.o_ov, s.delta, 1j * float(s.xi[0])).real, rhs)
+        t_node = time.perf_counter() - t1
+        measured += t_node
+    n_res = builds["decoupled"] + builds["qp"] + builds["sigma"]
+    t_step = builds["table"] * t_node + n_res * t_build
+    pts = pent_points(mol_host.n_core)["total"]
+    return {"value": pts / t_step, "t_step_s": t_step, "t_build_s": t_build, "t_node_s": t_node,
+            "measured_s": measured,
+            "sample": (f"FP64 oracle on the pentacene-sized system: one residue build (chi0 + LU, 22 right-hand sides) "
+                       f"and one imaginary-axis node (chi0 + LU, {s.n_states * s.n_core} right-hand sides) timed; the step "
+                       f"extrapolated as {builds['table']} nodes + {n_res} residue builds")}
+
+
+def host_copy(mol):
+    """The device-generated molecule with its arrays on the host (numpy), for the CPU oracle."""
+    import copy
+
+    h = copy.copy(mol)
+    h.o_ov = mol.o_ov.cpu().numpy()
+    h.o_core = mol.o_core.cpu().numpy()
+    return h
+
+
+def run_reference_pentacene(args):
+    import torch
+
+    dev = torch.cuda.is_available()
+    mol = pentacene_mol(dev)
+    mh = host_copy(mol) if dev else mol
+    del mol
+    builds = pent_step_builds(mh.eps, mh.n_occ, mh.core_idx, mh.omega)
+    # the imaginary-axis node once (in the first warm-up step), then one residue build per step
+    t_node = pent_oracle_sample(mh, builds)["t_node_s"]
+    for _ in range(max(0, args.warmup - 1)):
+        pent_oracle_sample(mh, builds, t_node)
+    vals, times = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = pent_oracle_sample(mh, builds, t_node)
+        times.append(time.perf_counter() - t0)
+        vals.append(r["value"])
+    value = statistics.mean(vals)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe_pent(mh), "implementation": "FP64 CPU oracle (numpy/LAPACK), bounded sample per step",
+                   "step": pent_step_text(), "residue_builds_per_step": builds},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": r["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def describe_pent(mol):
+    return (f"pentacene-sized synthetic molecule: N_states={mol.n_states}, N_occ={mol.n_occ}, N_core={mol.n_core}, "
+            f"N_aux={mol.n_aux}, N_ov={mol.n_occ * mol.n_virt}, {PENT_N_OMEGA} real omega over 30 eV, {mol.n_im} imaginary "
+            f"nodes, eta={mol.eta} Ha, cumulant n_t={mol.n_t}, t_max={mol.t_max}")
+
+
+def pent_step_text():
+    return ("reload of the inputs; imaginary-axis W table; decoupled Im Sigma of all cores on the 800-point relative grid "
+            "and their cumulant spectra; G_dH W0 QP (Hedin shift) of cores " + ", ".join(map(str, PENT_QP_CORES)) +
+            "; full CD Sigma^c of all cores at grid points " + ", ".join(map(str, PENT_SIGMA_IDX)))
+
+
+def run_pentacene_headline(args):
+    import numpy as np
+    import torch
+
+    from paper_2412_17132_gb300 import gwc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    dev = torch.device("cuda", local)
+    mol = pentacene_mol(True)
+    nc, nt = mol.n_core, mol.n_t
+    eps_d = torch.as_tensor(mol.eps, device=dev)
+    oov_d, ocore_d = mol.o_ov, mol.o_core
+    grid_rel = pent_grid_rel()
+    pts = mol.omega[PENT_SIGMA_IDX]
+    builds = pent_step_builds(mol.eps, mol.n_occ, mol.core_idx, mol.omega)
+    npts = pent_points(nc)
+    ctx = gwc.Context(eps_d, mol.n_occ, mol.core_idx, oov_d, ocore_d, prec=args.prec, qp_mode="hedin", eta=mol.eta,
+                      n_im=mol.n_im, xi0=mol.xi0, n_t=nt, t_max=mol.t_max, batch=args.batch, profile=True)
+    ctx.request_plan(grid_rel)
+    ctx.set_qp_cores(PENT_QP_CORES)
+    sig = torch.empty((nc, len(pts), 2), dtype=torch.float64, device=dev)
+    sx = torch.empty((nc,), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > L2 (129 MB)
+    # e2e buffers: inputs and results in pinned host memory
+    eps_h = torch.as_tensor(mol.eps).pin_memory()
+    oov_h = torch.empty(oov_d.shape, dtype=torch.float64).pin_memory()
+    ocore_h = torch.empty(ocore_d.shape, dtype=torch.float64).pin_memory()
+    oov_h.copy_(oov_d)
+    ocore_h.copy_(ocore_d)
+    res_h = [torch.empty(nc, dtype=torch.float64).pin_memory(), torch.empty(nc, dtype=torch.float64).pin_memory(),
+             torch.empty(nc, dtype=torch.int32).pin_memory(),
+             torch.empty((nc, PENT_N_OMEGA), dtype=torch.float64).pin_memory(),
+             torch.empty((nc, nt), dtype=torch.float64).pin_memory(), torch.empty(nt, dtype=torch.float64).pin_memory()]
+    sig_h = torch.empty(sig.shape, dtype=torch.float64).pin_memory()
+
+    def step(host=False):
+        if host:
+            ctx.load(eps_h.numpy(), oov_h.numpy(), ocore_h.numpy(), core_idx=mol.core_idx)
+        else:
+            ctx.load(eps_d, oov_d, ocore_d, core_idx=mol.core_idx)
+        ctx.request_step()  # table, QP of the selected cores, decoupled residues, spectra
+        ctx.sigma_core(pts, want_dec=False, out=(sig, None, sx))  # full Sigma^c (the table is reused)
+        if host:  # results back through the C ABI
+            ctx.request_results(out=res_h)
+            ctx.copy_out(sig_h, sig)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        step()
+    ctx.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+
+    ctx.reset_stats()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clk = clocks.stop()
+    ctx.sync()
+    st = ctx.stats()
+    total_ms, units, value = job_throughput(sum(times), npts["total"] * args.steps, pg, dev)
+    res_d = ctx.request_results()  # device copies of the last step's results
+    eqp, dh = res_d[0].cpu().numpy(), res_d[1].cpu().numpy()
+    im_dec = res_d[3]
+    a_spec = res_d[4]
+    sig_last = sig.cpu().numpy()
+
+    e2e = None
+    if not args.no_e2e:
+        k = min(2, args.steps)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            step(host=True)
+        e1.record(stream)
+        e1.synchronize()
+        _, _, e2e_value = job_throughput(e0.elapsed_time(e1), npts["total"] * k, pg, dev)
+        h2d = mol.eps.nbytes + oov_h.numel() * 8 + ocore_h.numel() * 8
+        d2h = sum(t.numel() * t.element_size() for t in res_h) + sig_h.numel() * 8
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": k, "path": "gwc_load from pinned host memory, gwc_request_copy_results and gwc_copy_out to pinned host"}
+
+    out = None
+    if rank == 0:
+        peaks, src = load_peaks()
+        chi0_t, fac_t = st["chi0_ms"] * 1e-3, st["factor_ms"] * 1e-3
+        chi0_alg = st["chi0_flop"] / chi0_t if chi0_t > 0 else 0.0
+        n_aux_pad = -(-mol.n_aux // 128) * 128
+        n_ov = mol.n_occ * mol.n_virt
+        n_ov_pad = -(-n_ov // 64) * 64
+        ntl = n_aux_pad // 128
+        tile_ratio = (ntl * (ntl + 1) / 2 * 128 * 128 * 2 * n_ov_pad) / (mol.n_aux * (mol.n_aux + 1.0) * n_ov)
+        mma_mult = {"bf16x3": 3.0, "bf16x3f64": 3.0, "bf16": 1.0}.get(args.prec, 0.0) * tile_ratio
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"kernel": f"chi0_tc_kernel (tcgen05 {args.prec})", "bound": "tensor", "achieved": chi0_alg / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "frac": chi0_alg / 1e12 / peak,
+                "traffic": load_traffic("chi0_tc_kernel", "pentacene", 1.0),
+                "traffic_unit": "DRAM bytes per frequency (complex z) from the committed ncu capture",
+                "mma_frac": mma_mult * chi0_alg / 1e12 / peak,
+                "peak_source": f"{src} bf16 sustained (kernel timed inside a long step)",
+                "share_of_step": chi0_t / (total_ms * 1e-3),
+                "work": "algorithmic flop of the builds done: N_aux(N_aux+1) N_ov per real part, 2 parts at complex z"}
+        lat = sorted(times)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"bf16x3": "bf16x3+f32+f64", "bf16x3f64": "bf16x3+f64", "bf16": "bf16+f32+f64", "fp32": "f32+f64",
+                      "fp64": "f64"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": describe_pent(mol), "precision": args.prec,
+                       "factorisation": {"bf16x3": "FP32-accurate (tcgen05 3xTF32 trailing updates, FP32 panels)",
+                                         "bf16": "FP32-accurate (tcgen05 3xTF32)", "bf16x3f64": "FP64 (SIMT)",
+                                         "fp32": "FP32 (SIMT)", "fp64": "FP64 (SIMT)"}[args.prec],
+                       "step": pent_step_text(), "points_per_step": npts, "residue_builds_per_step": builds,
+                       "parallelism": f"replicas x{ws}", "l2": "256 MB written between timed steps (L2 flushed)",
+                       "qp": "G_dH W0, eps_n + dH_n (exact fixed point of the QP equation)"},
+            "roofline": roof,
+            "chi0_tflops": {"algorithmic": chi0_alg / 1e12, "gemm_equivalent": 2 * chi0_alg / 1e12,
+                            "mma_executed": mma_mult * chi0_alg / 1e12 if mma_mult else None},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                           "per_step": times},
+            "kernel_time_share": {"chi0": st["chi0_ms"] / total_ms, "factor": st["factor_ms"] / total_ms,
+                                  "solve": st["solve_ms"] / total_ms},
+            "builds_done": st["chi0_builds"] / args.steps,
+            "gpu_launches": int(st["kernel_launches"]),
+            "clocks": clk,
+            "e2e": e2e,
+            "spectra_per_s": nc / (total_ms * 1e-3 / args.steps),
+            "qp": {"cores": PENT_QP_CORES, "eps_qp_Ha": [float(eqp[c]) for c in PENT_QP_CORES],
+                   "dH_Ha": [float(dh[c]) for c in PENT_QP_CORES]},
+        }
+        out["vs_oracle"] = pent_vs_oracle(dh, sig_last, im_dec.cpu().numpy(), grid_rel)
+    ctx.close()
+    del flush
+
+    if rank == 0 and not args.no_fp64_path and args.prec != "fp64":
+        out["fp64_path"] = pent_fp64_path(gwc, mol, eps_d, builds, npts, dev)
+        if out["fp64_path"].get("value"):
+            out["mixed_over_fp64_path"] = value / out["fp64_path"]["value"]
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r = pent_oracle_sample(host_copy(mol), builds)
+        out["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                               "sample": r["sample"], "measured_s": r["measured_s"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def pent_vs_oracle(dh, sig, im_dec, grid_rel):
+    """Errors against the FP64 oracle values in tests/golden/pentacene_oracle.json, per core."""
+    import numpy as np
+
+    p = os.path.join(ROOT, "tests", "golden", "pentacene_oracle.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        gold = json.load(f)
+    out = {"dH_err_eV": {}, "sigma_err_Ha": {}, "im_sigma_dec_err_Ha": {}}
+    for k, c in enumerate(gold["cores"]):
+        if c in PENT_QP_CORES:
+            out["dH_err_eV"][str(c)] = float((dh[c] - gold["dH"][k]) * HARTREE_EV)
+    for j, gi in enumerate(PENT_SIGMA_IDX):
+        if gi in gold.get("omega_idx", []):
+            ref = np.array([complex(*v) for v in gold["points"][gold["omega_idx"].index(gi)]["sigma_c"]])
+            got = sig[:, j, 0] + 1j * sig[:, j, 1]
+            out["sigma_err_Ha"][str(gi)] = {"max_abs": float(np.max(np.abs(got - ref))),
+                                            "max_rel": float(np.max(np.abs(got - ref) / np.abs(ref)))}
+    d = gold.get("dec_rel")
+    if d:
+        for k, c in enumerate(d["cores"][: len(d["values"])]):
+            got = im_dec[c, d["nu_idx"]]
+            out["im_sigma_dec_err_Ha"][str(c)] = float(np.max(np.abs(got - np.array(d["values"][k]))))
+    return out
+
+
+def pent_fp64_path(gwc, mol, eps_d, builds, npts, dev):
+    """The plain FP64 GPU path (FP64 chi0, FP64 LDL^T) on a measured sample: its imaginary-axis W table and
+    one factorisation wave of 8 residue builds (22 right-hand sides each); the step's time extrapolated as
+    T_table + residue builds x T_chi0 + factorisation waves x T_wave (waves of `batch` matrices per phase)."""
+    import numpy as np
+    import torch
+
+    batch = 73  # FP64 complex 4500 x 4500 matrices fitting the 24 GB workspace
+    c64 = gwc.Context(eps_d, mol.n_occ, mol.core_idx, mol.o_ov, mol.o_core, prec="fp64", eta=mol.eta, n_im=mol.n_im,
+                      xi0=mol.xi0, n_t=mol.n_t, t_max=mol.t_max, batch=batch, profile=True)
+    ef = 0.5 * (mol.eps[mol.n_occ - 1] + mol.eps[mol.n_occ])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c64.sigma_core(np.array([ef]), want_dec=False)  # between HOMO and LUMO: no residues, the table alone
+    c64.sync()
+    t_table = time.perf_counter() - t0
+    z = torch.tensor([[abs(mol.eps[30] - mol.omega[PENT_SIGMA_IDX[0]]) + 0.01 * k, mol.eta] for k in range(8)],
+                     dtype=torch.float64, device=dev)
+    rhs = mol.o_core[30].unsqueeze(0).expand(8, -1, -1).contiguous()
+    c64.reset_stats()
+    w64 = c64.screen(z, rhs)
+    c64.sync()
+    st = c64.stats()
+    c64.close()
+    t_chi0 = st["chi0_ms"] * 1e-3 / 8
+    t_wave = st["factor_ms"] * 1e-3
+    waves = sum(-(-builds[k] // batch) for k in ("decoupled", "qp", "sigma"))
+    n_res = builds["decoupled"] + builds["qp"] + builds["sigma"]
+    t_step = t_table + n_res * t_chi0 + waves * t_wave
+    return {"value": npts["total"] / t_step, "unit": UNIT, "t_step_s": t_step, "t_table_s": t_table,
+            "t_chi0_per_build_s": t_chi0, "t_factor_wave_s": t_wave, "waves": waves,
+            "sample": ("FP64 GPU path measured: its imaginary-axis W table, and 8 residue builds (FP64 chi0, one "
+                       "FP64 LDL^T wave, 22 right-hand sides); the same step extrapolated from these"),
+            "w_fp64_sample": w64.cpu().numpy().tolist()}
+
+
+# ------------------------------------------------------------------------------------------
 # Precision form at the pentacene size, batched form, serving form
 # ------------------------------------------------------------------------------------------
 def _events():
@@ -637,6 +1008,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "pentacene":
+        return run_pentacene_headline(args)
+    if args.workload == "pentacene-forms":
         return run_pentacene(args)
     if args.workload == "batch":
         return run_batch(args)

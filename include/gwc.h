@@ -48,12 +48,20 @@ typedef enum {
 
 /* Arithmetic of the polarizability build chi0 and of the dielectric factorisation.
  * All modes keep the self-energy assembly, the QP iteration and the cumulant in FP64.
- *   FP64   : chi0 FP64 (SIMT), factorisation and solves FP64           (plain FP64 path)
- *   FP32   : chi0 FP32 (SIMT), factorisation and solves FP32
- *   BF16   : chi0 on tcgen05 tensor cores, BF16 operands, FP32 accumulate; factor FP32
- *   BF16X3 : chi0 on tcgen05, split-BF16 operands (hi*hi + hi*lo + lo*hi), FP32
- *            accumulate; factor FP32                                      (mixed path)   */
-typedef enum { GWC_PREC_FP64 = 0, GWC_PREC_BF16 = 1, GWC_PREC_BF16X3 = 2, GWC_PREC_FP32 = 3 } gwc_precision;
+ *   FP64       : chi0 FP64 (SIMT), factorisation and solves FP64        (plain FP64 path)
+ *   FP32       : chi0 FP32 (SIMT), factorisation and solves FP32
+ *   BF16       : chi0 on tcgen05 tensor cores, BF16 operands, FP32 accumulate; factor FP32
+ *   BF16X3     : chi0 on tcgen05, split-BF16 operands (hi*hi + hi*lo + lo*hi), FP32
+ *                accumulate; factor FP32-accurate (3xTF32 tensor-core updates)  (mixed path)
+ *   BF16X3_F64 : chi0 as BF16X3, widened to FP64; factorisation of eps, the imaginary-axis solves
+ *                and the residue contractions y_k^2/d_k in FP64 (SIMT)                           */
+typedef enum {
+  GWC_PREC_FP64 = 0,
+  GWC_PREC_BF16 = 1,
+  GWC_PREC_BF16X3 = 2,
+  GWC_PREC_FP32 = 3,
+  GWC_PREC_BF16X3_F64 = 4
+} gwc_precision;
 
 /* Form of Im Sigma handed to the cumulant (Sec. "Core-valence decoupling", Eqs.
  * sigma_spectral_decoupled, sigma_spectral_decoupled_symmetric, cd_sigma_imaginary_decoupled):
@@ -215,6 +223,16 @@ gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int
  * A core that does not converge in max_qp_iter keeps its last iterate and sets
  * GWC_ERR_NOT_CONVERGED (reported by gwc_sync). */
 gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, void* stream);
+
+/* Cores whose QP energies gwc_qp_solve and the request step compute: cores = HOST list of core indices
+ * (0..n_core-1), n of them; NULL restores the default (every core). The other cores cost no dielectric
+ * build and get NaN in eps_qp and dh and 0 iterations. Synchronises `stream`. */
+gwc_status gwc_set_qp_cores(gwc_ctx* ctx, const int* cores, int n, void* stream);
+
+/* Copies `bytes` of a result from device memory (src) to dst (host, pinned or pageable, or device),
+ * enqueued on `stream` (an asynchronous copy for pinned host memory): the library's output path for
+ * callers that hold results in device buffers and want them on the host through this interface. */
+gwc_status gwc_copy_out(gwc_ctx* ctx, void* dst, const void* src, size_t bytes, void* stream);
 
 /* Sigma^c of every core on an absolute grid by CD-WAC (Sec. "Self-energy evaluation", eq
  * pade_approximation): the imaginary-axis term as in gwc_sigma_core; W^c_mn for each occupied residue

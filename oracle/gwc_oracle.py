@@ -218,16 +218,18 @@ class System:
                 dec[c] = f * w[c].imag
         return sig, dec
 
-    def im_sigma_dec_group(self, omega: float, groups) -> np.ndarray:
+    def im_sigma_dec_group(self, omega: float, groups, cores=None) -> np.ndarray:
         """Decoupled Im Sigma with symmetry-equivalent cores (Sec. "Core-valence decoupling", Eq.
         sigma_spectral_decoupled_symmetric, in the residue form of Eq. cd_sigma_imaginary_decoupled):
         for core n the sum over the cores i of its group (groups[c] is the label of core c),
             Im Sigma^dec_n(w) = sum_{i in group(n)} f_i Im W^c_{i n}(|eps_i - w| + i eta),
         each member with its own prefactor f_i, its own residue frequency |eps_i - w| and the RI vector
-        o_{in} = O^.(i, n) (one solve per member). A group of one member is the DIAG form. Returns [n_core]."""
+        o_{in} = O^.(i, n) (one solve per member). A group of one member is the DIAG form. Returns [n_core];
+        with `cores` (core indices) given, only those entries are computed and the others are 0."""
         groups = [int(g) for g in groups]
         out = np.zeros(self.n_core)
-        for c, n in enumerate(self.core_idx):
+        todo = range(self.n_core) if cores is None else [int(c) for c in cores]
+        for c in todo:
             for c2, i in enumerate(self.core_idx):
                 if groups[c2] != groups[c]:
                     continue

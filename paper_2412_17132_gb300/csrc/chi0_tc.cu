@@ -75,6 +75,7 @@ struct TcParams {
   int ppf;                // parts per frequency (1 real, 2 complex)
   int fpc;                // frequencies per CTA (kParts / ppf)
   int split3;
+  int out64;              // matrices in FP64 (double / double2) instead of FP32
   float alpha, beta;
   void* out;
   long long ldm, mat_stride;
@@ -411,7 +412,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               v[0][i] = p.alpha * v[0][i] + dg;
               if (CPLX) v[CPLX ? 1 : 0][i] = p.alpha * v[CPLX ? 1 : 0][i];
             }
-            if (CPLX) {
+            if (p.out64) {  // FP64 matrices (FP64 factorisation): the FP32 sums widened exactly
+              if (CPLX) {
+                double2* o = reinterpret_cast<double2*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + qb;
+                for (int i = 0; i < 16; ++i)
+                  if (full || (qb + i < p.n_aux && qb + i <= P))
+                    o[i] = make_double2((double)v[0][i], (double)v[CPLX ? 1 : 0][i]);
+              } else {
+                double* o = reinterpret_cast<double*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + qb;
+                for (int i = 0; i < 16; ++i)
+                  if (full || (qb + i < p.n_aux && qb + i <= P)) o[i] = (double)v[0][i];
+              }
+            } else if (CPLX) {
               float2* o = reinterpret_cast<float2*>(p.out) + f * p.mat_stride + (long long)P * p.ldm + qb;
               if (full) {
 #pragma unroll
@@ -457,7 +469,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32, int ld_pad,
                    int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F, bool complex_out,
                    double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
-                   unsigned* status, unsigned long long wait_ns, cudaStream_t s) {
+                   unsigned* status, unsigned long long wait_ns, bool out64, cudaStream_t s) {
   if (!tc_supported()) return -2;
   if (n_aux_pad % BM || n_ov_pad % BK || ld_pad != n_ov_pad || ld_dtab % BK) return -2;
   // TMA: 16-B aligned bases, row strides multiples of 16 B, x coordinates multiples of 64 / 32
@@ -478,6 +490,7 @@ int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* 
   p.ppf = complex_out ? 2 : 1;
   p.fpc = kParts / p.ppf;
   p.split3 = split3 ? 1 : 0;
+  p.out64 = out64 ? 1 : 0;
   p.alpha = (float)alpha;
   p.beta = (float)beta;
   p.out = out;

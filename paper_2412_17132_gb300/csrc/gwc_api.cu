@@ -144,8 +144,10 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   if (n % 2 == 1) x[n / 2] = 0.0;
 }
 
-MatKind real_kind(const gwc_ctx* c) { return c->opt.prec == GWC_PREC_FP64 ? MatKind::RealF64 : MatKind::RealF32; }
-MatKind cplx_kind(const gwc_ctx* c) { return c->opt.prec == GWC_PREC_FP64 ? MatKind::CplxF64 : MatKind::CplxF32; }
+// Modes whose dielectric matrices (factorisation, solves, residue contractions) are FP64.
+bool factor64(int prec) { return prec == GWC_PREC_FP64 || prec == GWC_PREC_BF16X3_F64; }
+MatKind real_kind(const gwc_ctx* c) { return factor64(c->opt.prec) ? MatKind::RealF64 : MatKind::RealF32; }
+MatKind cplx_kind(const gwc_ctx* c) { return factor64(c->opt.prec) ? MatKind::CplxF64 : MatKind::CplxF32; }
 
 template <typename T>
 gwc_status dalloc(gwc_ctx* ctx, T** p, size_t count) {
@@ -190,7 +192,7 @@ gwc_status validate_options(const gwc_options* o, int n_core) {
   if (!(o->eta > 0.0) || !std::isfinite(o->eta)) return fail(nullptr, GWC_ERR_INVALID_ARG, "eta must be > 0");
   if (o->n_im < 1 || o->n_im > 1024) return fail(nullptr, GWC_ERR_INVALID_ARG, "n_im must be in 1..1024");
   if (!(o->xi0 > 0.0)) return fail(nullptr, GWC_ERR_INVALID_ARG, "xi0 must be > 0");
-  if (o->prec < 0 || o->prec > 3) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad precision");
+  if (o->prec < 0 || o->prec > 4) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad precision");
   if (o->dec < 0 || o->dec > 2) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad decoupling mode");
   if (o->n_t < 16 || o->n_t > (1 << 22) || (o->n_t & (o->n_t - 1)))
     return fail(nullptr, GWC_ERR_INVALID_ARG, "n_t must be a power of two in 16..2^22");
@@ -228,8 +230,8 @@ Sizes sizes_of(const gwc_system* s, const gwc_options* o) {
   z.n_ov_pad = (int)round_up(n_ov, 64);
   z.ld_dtab = z.n_ov_pad;
   z.ldm = round_up(s->n_aux, 4);
-  z.elem_c = o->prec == GWC_PREC_FP64 ? 16 : 8;
-  z.elem_r = o->prec == GWC_PREC_FP64 ? 8 : 4;
+  z.elem_c = factor64(o->prec) ? 16 : 8;
+  z.elem_r = factor64(o->prec) ? 8 : 4;
   return z;
 }
 
@@ -320,9 +322,9 @@ gwc_status run_chi0_any(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, 
     LAUNCH(launch_chi0_simt(kind, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux, ctx->n_ov_pad, ctx->d_dtab, ctx->ld_dtab, F,
                             alpha, beta, out, ctx->ldm, stride, full, active, st));
   } else {
-    int n = launch_chi0_tc(prec == GWC_PREC_BF16X3, ctx->d_o_hi, ctx->d_o_lo, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux,
+    int n = launch_chi0_tc(prec != GWC_PREC_BF16, ctx->d_o_hi, ctx->d_o_lo, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux,
                            ctx->n_aux_pad, ctx->n_ov_pad, (const float*)ctx->d_dtab, ctx->ld_dtab, F, complex_z, alpha,
-                           beta, out, ctx->ldm, stride, active, ctx->d_status, ctx->wait_ns, st);
+                           beta, out, ctx->ldm, stride, active, ctx->d_status, ctx->wait_ns, factor64(prec), st);
     if (n == -2) return fail(ctx, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for this shape/device");
     LAUNCH(n);
     if (full) {
@@ -483,7 +485,7 @@ gwc_status enqueue_qp(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, bool
   const int nc = ctx->n_core, no = ctx->n_occ;
   const int np = nc * no;
   const bool hedin = ctx->opt.qp_mode == GWC_QP_HEDIN;
-  LAUNCH(launch_qp_init(ctx->d_eps, ctx->d_core_idx, nc, ctx->d_qp, st));
+  LAUNCH(launch_qp_init(ctx->d_eps, ctx->d_core_idx, nc, ctx->qp_mask_set ? ctx->d_qp_mask : nullptr, ctx->d_qp, st));
   const int rounds = hedin ? 1 : ctx->opt.max_qp_iter + 2;
   for (int r = 0; r < rounds; ++r) {
     LAUNCH(launch_qp_pairs(ctx->d_eps, ctx->d_core_idx, nc, no, ctx->eps_f, ctx->opt.eta, ctx->d_qp, ctx->d_qp_z,
@@ -737,7 +739,8 @@ void gwc_destroy(gwc_ctx* ctx) {
                   ctx->d_pair_z, ctx->d_pair_rows, ctx->d_zim, ctx->d_req_wrel, ctx->d_req_z, ctx->d_req_rows,
                   ctx->d_req_pair_of, ctx->d_req_w, ctx->d_req_im, ctx->d_req_a, ctx->d_req_nu, ctx->d_req_eqp,
                   ctx->d_req_dh, ctx->d_req_it, ctx->d_eps_g, ctx->d_ev_sig, ctx->d_ev_diff, ctx->d_active_builds,
-                  ctx->d_ev_pidx, ctx->d_ev_pm, ctx->d_ev_pw, ctx->d_ev_z, ctx->d_ev_rows, ctx->d_ev_wres, ctx->d_ev_w};
+                  ctx->d_ev_pidx, ctx->d_ev_pm, ctx->d_ev_pw, ctx->d_ev_z, ctx->d_ev_rows, ctx->d_ev_wres, ctx->d_ev_w,
+                  ctx->d_qp_mask};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& r : ctx->ev_pending) {
@@ -798,15 +801,20 @@ gwc_status gwc_screen(gwc_ctx* ctx, const double* z, int F, const double* rhs, i
     }
     res = run_chi0(ctx, true, nb, z + 2 * (size_t)f0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st);
     if (res != GWC_OK) break;
+    cudaEvent_t evf = ev_begin(ctx, st);
     int n1 = launch_factor(ctx, ck, ctx->d_mats, ctx->n_aux, ctx->n_aux, stride, nb, nullptr, st);
+    ev_end(ctx, kClsFactor, evf, st);
     int n2 = launch_rhs_gather(ck, rhs, ctx->n_aux, d_rows, nb, n_rhs, ctx->n_aux, d_r, ctx->ldm,
                                (long long)n_rhs * ctx->ldm, d_bn, st);
+    cudaEvent_t evs = ev_begin(ctx, st);
     int n3 = launch_ldlt_solve_w(ck, ctx->d_mats, ctx->n_aux, ctx->ldm, stride, d_r, n_rhs, ctx->ldm,
                                  (long long)n_rhs * ctx->ldm, d_bn, nb, w + (size_t)f0 * n_rhs * 2, (long long)n_rhs * 2,
                                  nullptr, st);
+    ev_end(ctx, kClsSolve, evs, st);
     if (n1 < 0 || n2 < 0 || n3 < 0) res = fail(ctx, GWC_ERR_CUDA, "screen launch failed");
     ctx->stats.kernel_launches += std::max(n1, 0) + std::max(n2, 0) + std::max(n3, 0);
     ctx->stats.factorizations += nb;
+    ctx->stats.factor_flop += factor_flop(ctx->n_aux, true, nb);
   }
   cudaStreamSynchronize(st);
   cudaFree(d_r);
@@ -1009,6 +1017,33 @@ gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, vo
   TRY(compute_wim(ctx, st));
   TRY(enqueue_qp(ctx, eps_qp, dh, iters, true, st));
   return check_stream_error(ctx);
+}
+
+gwc_status gwc_set_qp_cores(gwc_ctx* ctx, const int* cores, int n, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0 || (n > 0 && !cores)) return fail(ctx, GWC_ERR_INVALID_ARG, "need cores for n > 0");
+  if (!cores) {
+    ctx->qp_mask_set = false;
+    return GWC_OK;
+  }
+  std::vector<int> mask(ctx->n_core, 0);
+  for (int k = 0; k < n; ++k) {
+    if (cores[k] < 0 || cores[k] >= ctx->n_core) return fail(ctx, GWC_ERR_INVALID_ARG, "core index out of range");
+    mask[cores[k]] = 1;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!ctx->d_qp_mask) TRY(dalloc(ctx, &ctx->d_qp_mask, ctx->n_core));
+  CU(cudaMemcpyAsync(ctx->d_qp_mask, mask.data(), sizeof(int) * ctx->n_core, cudaMemcpyHostToDevice, st));
+  CU(cudaStreamSynchronize(st));  // the host vector goes out of scope
+  ctx->qp_mask_set = true;
+  return GWC_OK;
+}
+
+gwc_status gwc_copy_out(gwc_ctx* ctx, void* dst, const void* src, size_t bytes, void* stream) {
+  if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!dst || !src) return fail(ctx, GWC_ERR_INVALID_ARG, "need dst and src");
+  CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, (cudaStream_t)stream));
+  return GWC_OK;
 }
 
 gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_omega, const double* im_sigma,

@@ -115,7 +115,7 @@ int launch_chi0_simt(MatKind kind, const void* o_ov /*double or float [n_aux][ld
 int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32, int ld_pad,
                    int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F, bool complex_out,
                    double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
-                   unsigned* status, unsigned long long wait_ns, cudaStream_t s);
+                   unsigned* status, unsigned long long wait_ns, bool out64 /*FP64 matrices*/, cudaStream_t s);
 
 // Batched in-place LDL^T of F matrices [nrow][ldm]: the first n columns are factored (W = L D below
 // the diagonal, d on it, L^T above it); rows n..nrow-1 are appended right-hand sides that the row
@@ -170,7 +170,8 @@ struct QpState {
   double x0, g0, x1, g1, dh, w_eval;
   int phase, it, done, pad;
 };
-int launch_qp_init(const double* eps, const int* core_idx, int n_core, QpState* st, cudaStream_t s);
+// mask [n_core] (or null: every core): cores with mask 0 are not solved (NaN results, 0 iterations)
+int launch_qp_init(const double* eps, const int* core_idx, int n_core, const int* mask, QpState* st, cudaStream_t s);
 int launch_qp_pairs(const double* eps, const int* core_idx, int n_core, int n_occ, double eps_f, double eta,
                     const QpState* st, double* z, int* active, double* fac, int* all_done,
                     unsigned long long* active_count /*+= active pairs, or null*/, cudaStream_t s);
@@ -294,6 +295,8 @@ struct gwc_ctx {
   double* d_qp_w = nullptr;     // [n_core*n_occ][2]
   int* d_qp_rowmap = nullptr;   // [n_core*n_occ]
   int* d_all_done = nullptr;
+  int* d_qp_mask = nullptr;     // [n_core] cores whose QP energies are computed (gwc_set_qp_cores)
+  bool qp_mask_set = false;
   // builds of masked launches (QP rounds) that are not skipped: counted on the device, folded into
   // the stats by gwc_get_stats / gwc_reset_stats
   unsigned long long* d_active_builds = nullptr;

@@ -91,15 +91,16 @@ __global__ void sigma_grid_kernel(const double* __restrict__ eps, int n_states, 
 // phase-0 evaluation at eps_n already is g(x0) = dH_n, so phase 1 is skipped.
 // ---------------------------------------------------------------------------------------------
 
+// done: 0 iterating, 1 converged, 2 stopped at max_iter, 3 not requested (mask[c] == 0)
 __global__ void qp_init_kernel(const double* __restrict__ eps, const int* __restrict__ core_idx, int n_core,
-                               QpState* __restrict__ st) {
+                               const int* __restrict__ mask, QpState* __restrict__ st) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_core) return;
   QpState s{};
   s.w_eval = eps[core_idx[c]];
   s.phase = 0;
   s.it = 0;
-  s.done = 0;
+  s.done = (mask && !mask[c]) ? 3 : 0;
   st[c] = s;
 }
 
@@ -110,7 +111,7 @@ __global__ void qp_pairs_kernel(const double* __restrict__ eps, const int* __res
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) {
     int d = 1;
-    for (int c = 0; c < n_core; ++c) d &= st[c].done;
+    for (int c = 0; c < n_core; ++c) d &= st[c].done != 0;
     *all_done = d;
   }
   if (t >= n_core * n_occ) return;
@@ -209,6 +210,11 @@ __global__ void qp_finish_kernel(const QpState* __restrict__ st, int n_core, dou
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_core) return;
   QpState s = st[c];
+  if (s.done == 3) {  // not requested
+    eps_qp[c] = dh[c] = __longlong_as_double(0x7ff8000000000000ll);
+    iters[c] = 0;
+    return;
+  }
   eps_qp[c] = s.x1;
   dh[c] = s.dh;
   iters[c] = s.it;
@@ -223,6 +229,11 @@ __global__ void qp_finish_hedin_kernel(const QpState* __restrict__ st, const dou
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_core) return;
   const QpState s = st[c];
+  if (s.done == 3) {  // not requested
+    eps_qp[c] = dh[c] = __longlong_as_double(0x7ff8000000000000ll);
+    iters[c] = 0;
+    return;
+  }
   eps_qp[c] = eps[core_idx[c]] + s.dh;
   dh[c] = s.dh;
   iters[c] = 1;
@@ -516,8 +527,8 @@ int launch_sigma_grid(const double* eps, int n_states, int n_core, const int* co
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_qp_init(const double* eps, const int* core_idx, int n_core, QpState* st, cudaStream_t s) {
-  qp_init_kernel<<<(n_core + 63) / 64, 64, 0, s>>>(eps, core_idx, n_core, st);
+int launch_qp_init(const double* eps, const int* core_idx, int n_core, const int* mask, QpState* st, cudaStream_t s) {
+  qp_init_kernel<<<(n_core + 63) / 64, 64, 0, s>>>(eps, core_idx, n_core, mask, st);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

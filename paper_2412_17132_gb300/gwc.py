@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgwc.so")
 
-PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "fp32": 3}
+PREC = {"fp64": 0, "bf16": 1, "bf16x3": 2, "fp32": 3, "bf16x3f64": 4}
 DEC = {"none": 0, "diag": 1, "group": 2}
 QP = {"secant": 0, "hedin": 1, "g0w0": 2}
 STATUS = {
@@ -125,6 +125,8 @@ _SIGS = {
                                         ctypes.c_void_p]),
     "gwc_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_batch_destroy": (None, [ctypes.c_void_p]),
+    "gwc_set_qp_cores": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "gwc_copy_out": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "gwc_cumulant_spectrum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                       ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                                       ctypes.c_void_p]),
@@ -393,6 +395,21 @@ class Context:
                    torch.empty((nc, nt), dtype=torch.float64, device="cuda"), torch.empty(nt, dtype=torch.float64, device="cuda"))
         _check(lib().gwc_request_copy_results(self._ctx, *[_ptr(t) for t in out], _stream(stream)), self._ctx)
         return out
+
+    def set_qp_cores(self, cores=None, stream=None):
+        """Cores (indices 0..n_core-1) whose QP energies qp_solve and the request step compute; None: all."""
+        if cores is None:
+            _check(lib().gwc_set_qp_cores(self._ctx, None, 0, _stream(stream)), self._ctx)
+            return
+        c = np.ascontiguousarray(np.asarray(cores, dtype=np.int32))
+        _check(lib().gwc_set_qp_cores(self._ctx, c.ctypes.data, int(c.size), _stream(stream)), self._ctx)
+
+    def copy_out(self, dst, src, stream=None):
+        """gwc_copy_out: copies the device tensor src into dst (a pinned host tensor or a device tensor)."""
+        nbytes = src.numel() * src.element_size()
+        assert dst.numel() * dst.element_size() == nbytes
+        _check(lib().gwc_copy_out(self._ctx, _ptr(dst), _ptr(src), nbytes, _stream(stream)), self._ctx)
+        return dst
 
     def autotune(self, stream=None) -> int:
         c = ctypes.c_int()

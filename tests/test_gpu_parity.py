@@ -52,7 +52,8 @@ def _cplx(t):
 ZS = [complex(0.0, 0.7), complex(0.0, 0.0), complex(0.31, 1e-3), complex(9.9, 1e-3), complex(10.45, 1e-3)]
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5), ("bf16x3", 2e-5), ("bf16", 5e-3)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5), ("bf16x3", 2e-5), ("bf16x3f64", 2e-5),
+                                      ("bf16", 5e-3)])
 def test_chi0_matches_oracle(gwc, tiny, prec, tol):
     ctx = gwc.Context.from_molecule(tiny, prec=prec)
     z = torch.tensor([[v.real, v.imag] for v in ZS], dtype=torch.float64, device="cuda")
@@ -93,7 +94,7 @@ def test_chi0_ragged_shapes_bf16x3(gwc, n_aux, n_states, n_occ):
         assert np.max(np.abs(out[f] - ref)) <= 2e-5 * max(1e-300, np.max(np.abs(ref)))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-4), ("bf16x3", 2e-3)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-4), ("bf16x3", 2e-3), ("bf16x3f64", 2e-3)])
 def test_screen_matches_oracle(gwc, tiny, prec, tol):
     ctx = gwc.Context.from_molecule(tiny, prec=prec)
     z = torch.tensor([[v.real, v.imag] for v in ZS], dtype=torch.float64, device="cuda")
@@ -111,10 +112,10 @@ def test_screen_matches_oracle(gwc, tiny, prec, tol):
 # Sigma tolerance: fp64 absolute; reduced precision relative to |Sigma| with the condition
 # number kappa ~ ||Pi(i0)||/eta = 2e3 of eps near the RPA poles times the chi0 error
 # (fp32 ~1e-7, bf16x3 ~3e-6), plus an absolute floor for small |Sigma|.
-SIG_TOL = {"fp64": (0.0, 1e-8), "fp32": (3e-3, 2e-4), "bf16x3": (2e-2, 2e-3)}
+SIG_TOL = {"fp64": (0.0, 1e-8), "fp32": (3e-3, 2e-4), "bf16x3": (2e-2, 2e-3), "bf16x3f64": (2e-2, 2e-3)}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16x3f64"])
 def test_sigma_grid_tiny_full(gwc, tiny, tiny_oracle, prec):
     """Every point of the 400-point grid of the tiny molecule, real and imaginary parts."""
     rel, ab = SIG_TOL[prec]
@@ -128,7 +129,7 @@ def test_sigma_grid_tiny_full(gwc, tiny, tiny_oracle, prec):
     assert abs(float(sx[0]) - tiny_oracle.sigma_x()[0]) < 1e-10 * abs(tiny_oracle.sigma_x()[0])
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x3f64"])
 def test_gates_tiny_reduced_precision(gwc, tiny, tiny_oracle, prec):
     """The accuracy gates: QP |dE| <= 1e-3 eV, A(w) max-abs <= 1e-3 of the peak, satellite
     positions <= 0.01 eV, each against the FP64 oracle."""
@@ -162,7 +163,7 @@ def test_bf16_alone_misses_the_qp_gate_and_is_reported(gwc, tiny, tiny_oracle):
     assert 1e-5 < err < 0.1
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16x3f64"])
 def test_qp_matches_oracle(gwc, tiny, tiny_oracle, prec):
     ctx = gwc.Context.from_molecule(tiny, prec=prec)
     e, dh, it = ctx.qp_solve()
@@ -351,3 +352,28 @@ def test_cdwac_hedin_shift_matches_oracle_tiny(gwc, tiny, tiny_oracle):
     ref = G.sigma_c_wac(tiny_oracle, w, xref)
     assert np.max(np.abs(_cplx(wac) - ref)) < 1e-6
     assert abs(_cplx(wac)[0, 0].real - tiny_oracle.sigma_c_core(0, float(tiny.eps[0])).real) * EV < 1e-3
+
+
+def test_fp64_factorisation_of_the_same_chi0(gwc):
+    """BF16X3_F64 factors the same split-BF16 chi0 in FP64: its W differs from the FP32-factor mode's only
+    by the FP32 factorisation error (far below the chi0 error), and both lie within the chi0-error
+    budget of the oracle's FP64 W."""
+    mol = synth.small(n_states=50, n_occ=7, n_core=2, n_aux=257, seed=29)
+    z = torch.tensor([[0.0, 0.4], [0.45, 1e-3], [9.95, 1e-3]], dtype=torch.float64, device="cuda")
+    rhs_np = np.stack([mol.o_core[[0, 5, 20], 0, :] for _ in range(3)])
+    rhs = torch.as_tensor(rhs_np, device="cuda")
+    w = {}
+    for prec in ("bf16x3", "bf16x3f64"):
+        ctx = gwc.Context.from_molecule(mol, prec=prec)
+        w[prec] = _cplx(ctx.screen(z, rhs))
+        ctx.sync()
+        ctx.close()
+    delta = G.transition_energies(mol.eps, mol.n_occ)
+    for f in range(3):
+        zz = complex(float(z[f, 0]), float(z[f, 1]))
+        ref = G.screened_wc(G.chi0(mol.o_ov, delta, zz), rhs_np[f].T)
+        scale = max(1e-6, np.max(np.abs(ref)))
+        e32 = np.max(np.abs(w["bf16x3"][f] - ref)) / scale
+        e64 = np.max(np.abs(w["bf16x3f64"][f] - ref)) / scale
+        assert e64 < 2e-3 and e32 < 2e-3, (f, e32, e64)
+        assert np.max(np.abs(w["bf16x3f64"][f] - w["bf16x3"][f])) / scale < 1e-4
