@@ -761,11 +761,16 @@ def run_pentacene_headline(args):
                    "dH_Ha": [float(dh[c]) for c in PENT_QP_CORES]},
         }
         out["vs_oracle"] = pent_vs_oracle(dh, sig_last, im_dec.cpu().numpy(), grid_rel)
+    # residue contractions at 8 frequencies, compared with the FP64 GPU path below
+    z8, rhs8 = pent_fp64_sample_inputs(mol, dev)
+    w_mixed = ctx.screen(z8, rhs8).cpu().numpy()
+    ctx.sync()
     ctx.close()
     del flush
 
     if rank == 0 and not args.no_fp64_path and args.prec != "fp64":
-        out["fp64_path"] = pent_fp64_path(gwc, mol, eps_d, builds, npts, dev)
+        out["fp64_path"], w64 = pent_fp64_path(gwc, mol, eps_d, builds, npts, dev)
+        out["fp64_path"]["w_mixed_vs_fp64_max_rel"] = float(np.max(np.abs(w_mixed - w64)) / np.max(np.abs(w64)))
         if out["fp64_path"].get("value"):
             out["mixed_over_fp64_path"] = value / out["fp64_path"]["value"]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -815,6 +820,7 @@ def pent_fp64_path(gwc, mol, eps_d, builds, npts, dev):
     import torch
 
     batch = 73  # FP64 complex 4500 x 4500 matrices fitting the 24 GB workspace
+    z, rhs = pent_fp64_sample_inputs(mol, dev)
     c64 = gwc.Context(eps_d, mol.n_occ, mol.core_idx, mol.o_ov, mol.o_core, prec="fp64", eta=mol.eta, n_im=mol.n_im,
                       xi0=mol.xi0, n_t=mol.n_t, t_max=mol.t_max, batch=batch, profile=True)
     ef = 0.5 * (mol.eps[mol.n_occ - 1] + mol.eps[mol.n_occ])
@@ -823,9 +829,6 @@ def pent_fp64_path(gwc, mol, eps_d, builds, npts, dev):
     c64.sigma_core(np.array([ef]), want_dec=False)  # between HOMO and LUMO: no residues, the table alone
     c64.sync()
     t_table = time.perf_counter() - t0
-    z = torch.tensor([[abs(mol.eps[30] - mol.omega[PENT_SIGMA_IDX[0]]) + 0.01 * k, mol.eta] for k in range(8)],
-                     dtype=torch.float64, device=dev)
-    rhs = mol.o_core[30].unsqueeze(0).expand(8, -1, -1).contiguous()
     c64.reset_stats()
     w64 = c64.screen(z, rhs)
     c64.sync()
@@ -836,11 +839,19 @@ def pent_fp64_path(gwc, mol, eps_d, builds, npts, dev):
     waves = sum(-(-builds[k] // batch) for k in ("decoupled", "qp", "sigma"))
     n_res = builds["decoupled"] + builds["qp"] + builds["sigma"]
     t_step = t_table + n_res * t_chi0 + waves * t_wave
-    return {"value": npts["total"] / t_step, "unit": UNIT, "t_step_s": t_step, "t_table_s": t_table,
-            "t_chi0_per_build_s": t_chi0, "t_factor_wave_s": t_wave, "waves": waves,
+    return {"value": npts["total"] / t_step, "unit": UNIT, "extrapolated": True, "t_step_s": t_step,
+            "t_table_s": t_table, "t_chi0_per_build_s": t_chi0, "t_factor_wave_s": t_wave, "waves": waves,
             "sample": ("FP64 GPU path measured: its imaginary-axis W table, and 8 residue builds (FP64 chi0, one "
-                       "FP64 LDL^T wave, 22 right-hand sides); the same step extrapolated from these"),
-            "w_fp64_sample": w64.cpu().numpy().tolist()}
+                       "FP64 LDL^T wave, 22 right-hand sides); the same step extrapolated from these")}, w64.cpu().numpy()
+
+
+def pent_fp64_sample_inputs(mol, dev):
+    """8 residue frequencies near the valence residue of grid point 100 and the 22 core right-hand sides."""
+    import torch
+
+    z = torch.tensor([[abs(mol.eps[30] - mol.omega[PENT_SIGMA_IDX[0]]) + 0.01 * k, mol.eta] for k in range(8)],
+                     dtype=torch.float64, device=dev)
+    return z, mol.o_core[30].unsqueeze(0).expand(8, -1, -1).contiguous()
 
 
 # ------------------------------------------------------------------------------------------

@@ -153,13 +153,19 @@ gwc_status gwc_workspace_bytes(const gwc_system* sys, const gwc_options* opt, in
  * (host->device if memory == GWC_MEM_HOST), builds the resident precision copies of
  * O_ov (BF16 hi/lo and FP32), and computes the imaginary-axis grid. Enqueued on
  * `stream`; gwc_create synchronises that stream once before returning.
+ * With core_idx, eps, o_ov and o_core all NULL the system gives sizes only: the context is
+ * allocated with that capacity and holds no system until gwc_load (serving slots sized for the
+ * largest request of a class); the other entry points return GWC_ERR_INVALID_ARG until then.
  * In the BF16 and BF16X3 modes the complex dielectric matrices are factored by the tensor-core
  * kernel (3xTF32 trailing updates, FP32-accurate); the environment variable GWC_FACTOR=simt,
  * read here, keeps them on the FP32 SIMT kernel instead (for comparisons). */
 gwc_status gwc_create(gwc_ctx** ctx, const gwc_system* sys, const gwc_options* opt, void* stream);
 
-/* Replaces the system of an existing context by another of the SAME sizes (serving
- * slots); no allocation. Synchronises `stream` once. */
+/* Replaces the system of an existing context (serving slots): no device allocation. The new system
+ * may be smaller than the one the context was created with, as long as every buffer sized by the
+ * system fits the allocation made at creation (orbitals, cores, occupied-virtual pairs, RI sizes and
+ * their products, the dielectric workspace); otherwise GWC_ERR_INVALID_ARG and the context keeps its
+ * system. A change of sizes drops the request plan and the QP core selection. Synchronises `stream`. */
 gwc_status gwc_load(gwc_ctx* ctx, const gwc_system* sys, void* stream);
 
 /* RI polarizability (Sec. "Self-energy evaluation"; RI form of Ren et al. 2012, which the

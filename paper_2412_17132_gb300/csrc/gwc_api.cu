@@ -164,6 +164,15 @@ gwc_status dalloc(gwc_ctx* ctx, T** p, size_t count) {
   return GWC_OK;
 }
 
+// (Re)allocates *p only when `count` exceeds the capacity *cap (grow-only buffers).
+template <typename T>
+gwc_status grow(gwc_ctx* ctx, T** p, size_t* cap, size_t count) {
+  if (*p && count <= *cap) return GWC_OK;
+  gwc_status r = dalloc(ctx, p, count);
+  *cap = r == GWC_OK ? std::max<size_t>(count, 1) : 0;
+  return r;
+}
+
 #define TRY(x)                     \
   do {                             \
     gwc_status s_ = (x);           \
@@ -179,6 +188,7 @@ gwc_status validate_system(const gwc_system* s) {
   if (s->n_aux > 65536 || s->n_states > 65536) return fail(nullptr, GWC_ERR_INVALID_ARG, "n_aux and n_states must be <= 65536");
   if ((long long)s->n_occ * (s->n_states - s->n_occ) > (1LL << 31) - 1)
     return fail(nullptr, GWC_ERR_INVALID_ARG, "n_occ * n_virt too large");
+  if (!s->core_idx && !s->eps && !s->o_ov && !s->o_core) return GWC_OK;  // sizes only (a capacity for gwc_create)
   if (!s->core_idx || !s->eps || !s->o_ov || !s->o_core) return fail(nullptr, GWC_ERR_INVALID_ARG, "NULL input pointer");
   for (int c = 0; c < s->n_core; ++c)
     if (s->core_idx[c] < 0 || s->core_idx[c] >= s->n_states)
@@ -714,18 +724,92 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
     if (cudaMemcpy(ctx->d_qp_rowmap, rows.data(), sizeof(int) * np, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(ctx, GWC_ERR_CUDA, "qp rowmap upload failed"));
   }
-  CTRY(load_system(ctx, s, st));
+  {
+    gwc_ctx::Caps& c = ctx->cap;
+    c.n_states = s->n_states;
+    c.n_core = s->n_core;
+    c.n_ov = n_ov;
+    c.o_ov = (size_t)s->n_aux * n_ov;
+    c.o_core = (size_t)s->n_states * s->n_core * s->n_aux;
+    c.o_pad = o->prec != GWC_PREC_FP64 ? (size_t)z.n_aux_pad * z.n_ov_pad : 0;
+    c.plane = plane;
+    c.qp_np = (size_t)s->n_core * s->n_occ;
+    c.mats_bytes = ctx->mats_bytes;
+    c.dtab = (size_t)ctx->batch * 2 * z.ld_dtab;
+    c.rhs_bytes = ctx->rhs_bytes;
+    c.rhs_im_bytes = (size_t)ctx->wim_group * plane * z.ldm * z.elem_r;
+    c.bnorm = std::max(wim_rows, (size_t)ctx->batch * s->n_core);
+    c.batch = ctx->batch;
+  }
+  if (s->eps) {
+    CTRY(load_system(ctx, s, st));
+    ctx->loaded = true;
+  }
 #undef CTRY
   *out = ctx;
+  return GWC_OK;
+}
+
+// Sets the context's sizes to those of `s` inside the capacity it was created with: no allocation.
+gwc_status reshape(gwc_ctx* ctx, const gwc_system* s) {
+  const gwc_ctx::Caps& c = ctx->cap;
+  if (!ctx->h_group.empty() && s->n_core != ctx->n_core)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "a context with core groups keeps its number of cores");
+  const Sizes z = sizes_of(s, &ctx->opt);
+  const size_t n_ov = (size_t)s->n_occ * (s->n_states - s->n_occ);
+  const size_t plane = (size_t)s->n_states * s->n_core;
+  const bool fits = (size_t)s->n_states <= c.n_states && (size_t)s->n_core <= c.n_core && n_ov <= c.n_ov &&
+                    (size_t)s->n_aux * n_ov <= c.o_ov && plane * s->n_aux <= c.o_core &&
+                    (ctx->opt.prec == GWC_PREC_FP64 || (size_t)z.n_aux_pad * z.n_ov_pad <= c.o_pad) && plane <= c.plane &&
+                    (size_t)s->n_core * s->n_occ <= c.qp_np;
+  if (!fits) return fail(ctx, GWC_ERR_INVALID_ARG, "system larger than the capacity of this context (create a larger one)");
+  const int border = std::min(s->n_core, 64);
+  const size_t per_mat = (size_t)(s->n_aux + border) * z.ldm * z.elem_c;
+  long long b = std::min<long long>(c.batch, (long long)(c.mats_bytes / per_mat));
+  b = std::min<long long>(b, (long long)(c.dtab / (2 * (size_t)z.ld_dtab)));
+  b = std::min<long long>(b, (long long)(c.rhs_bytes / ((size_t)s->n_core * z.ldm * z.elem_c)));
+  b = std::min<long long>(b, (long long)(c.bnorm / s->n_core));
+  if (b >= ctx->n_sm) b -= b % ctx->n_sm;
+  const size_t per_node = plane * z.ldm * z.elem_r;
+  const long long wg = std::min<long long>({(long long)(c.rhs_im_bytes / per_node), b, (long long)ctx->opt.n_im + 1,
+                                            (long long)(c.bnorm / plane)});
+  if (b < 1 || wg < 1) return fail(ctx, GWC_ERR_INVALID_ARG, "system does not fit the context's workspace");
+  std::vector<int> ident(plane);
+  for (size_t i = 0; i < plane; ++i) ident[i] = (int)i;
+  CU(cudaMemcpy(ctx->d_rowmap, ident.data(), sizeof(int) * plane, cudaMemcpyHostToDevice));
+  std::vector<int> rows((size_t)s->n_core * s->n_occ);
+  for (int cc = 0; cc < s->n_core; ++cc)
+    for (int m = 0; m < s->n_occ; ++m) rows[(size_t)cc * s->n_occ + m] = m * s->n_core + cc;
+  CU(cudaMemcpy(ctx->d_qp_rowmap, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice));
+  ctx->n_states = s->n_states;
+  ctx->n_occ = s->n_occ;
+  ctx->n_virt = s->n_states - s->n_occ;
+  ctx->n_aux = s->n_aux;
+  ctx->n_core = s->n_core;
+  ctx->n_ov = (int)n_ov;
+  ctx->n_aux_pad = z.n_aux_pad;
+  ctx->n_ov_pad = z.n_ov_pad;
+  ctx->ld_dtab = z.ld_dtab;
+  ctx->ldm = z.ldm;
+  ctx->batch = (int)b;
+  ctx->border_max = border;
+  ctx->wim_group = (int)wg;
+  ctx->req_n_omega = 0;       // a request plan belongs to the previous system
+  ctx->req_n_pairs = 0;
+  ctx->qp_mask_set = false;   // so does a QP core selection
   return GWC_OK;
 }
 
 gwc_status gwc_load(gwc_ctx* ctx, const gwc_system* s, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
   if (validate_system(s) != GWC_OK) return fail(ctx, GWC_ERR_INVALID_ARG, g_create_error);
+  if (!s->eps) return fail(ctx, GWC_ERR_INVALID_ARG, "gwc_load needs the system's arrays");
   if (s->n_states != ctx->n_states || s->n_occ != ctx->n_occ || s->n_aux != ctx->n_aux || s->n_core != ctx->n_core)
-    return fail(ctx, GWC_ERR_INVALID_ARG, "gwc_load needs a system of the same sizes as the context");
-  return load_system(ctx, s, (cudaStream_t)stream);
+    TRY(reshape(ctx, s));
+  ctx->loaded = false;
+  TRY(load_system(ctx, s, (cudaStream_t)stream));
+  ctx->loaded = true;
+  return GWC_OK;
 }
 
 void gwc_destroy(gwc_ctx* ctx) {
@@ -755,6 +839,7 @@ void gwc_destroy(gwc_ctx* ctx) {
 
 gwc_status gwc_build_chi0(gwc_ctx* ctx, const double* z, int F, double* chi0, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (!z || !chi0 || F < 1 || F > 4096) return fail(ctx, GWC_ERR_INVALID_ARG, "need z, chi0 and 1 <= F <= 4096");
   cudaStream_t st = (cudaStream_t)stream;
   MatKind ck = cplx_kind(ctx);
@@ -770,6 +855,7 @@ gwc_status gwc_build_chi0(gwc_ctx* ctx, const double* z, int F, double* chi0, vo
 
 gwc_status gwc_screen(gwc_ctx* ctx, const double* z, int F, const double* rhs, int n_rhs, double* w, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (!z || !rhs || !w || F < 1 || F > 4096 || n_rhs < 1 || n_rhs > (1 << 20))
     return fail(ctx, GWC_ERR_INVALID_ARG, "need z, rhs, w, 1 <= F <= 4096, 1 <= n_rhs <= 2^20");
   cudaStream_t st = (cudaStream_t)stream;
@@ -827,6 +913,7 @@ gwc_status gwc_screen(gwc_ctx* ctx, const double* z, int F, const double* rhs, i
 gwc_status gwc_sigma_core(gwc_ctx* ctx, const double* omega, int n_omega, double* sigma_c, double* im_sigma_dec,
                           double* sigma_x, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (!omega || !sigma_c || n_omega < 1 || n_omega > (1 << 20))
     return fail(ctx, GWC_ERR_INVALID_ARG, "need omega, sigma_c and 1 <= n_omega <= 2^20");
   for (int j = 0; j < n_omega; ++j)
@@ -904,7 +991,7 @@ gwc_status gwc_set_g_energies(gwc_ctx* ctx, const double* eps_g, double eps_f, v
     if ((m < ctx->n_occ) != (eps_g[m] < ef))
       return fail(ctx, GWC_ERR_INVALID_ARG, "eps_g must keep the occupied states below eps_f and the virtual ones above");
   cudaStream_t st = (cudaStream_t)stream;
-  if (!ctx->d_eps_g) TRY(dalloc(ctx, &ctx->d_eps_g, n));
+  if (!ctx->d_eps_g) TRY(dalloc(ctx, &ctx->d_eps_g, ctx->cap.n_states));
   ctx->h_eps_g.assign(eps_g, eps_g + n);
   CU(cudaMemcpyAsync(ctx->d_eps_g, ctx->h_eps_g.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
   CU(cudaStreamSynchronize(st));  // the host vector may change on the next call
@@ -943,8 +1030,8 @@ static gwc_status evgw0_sigma_diag(gwc_ctx* ctx, const std::vector<double>& e, c
     TRY(dalloc(ctx, &ctx->d_ev_wres, 2 * np));
     ctx->ev_pair_cap = np;
   }
-  if (!ctx->d_ev_pidx) TRY(dalloc(ctx, &ctx->d_ev_pidx, (size_t)n * n));
-  if (!ctx->d_ev_w) TRY(dalloc(ctx, &ctx->d_ev_w, n));
+  if (!ctx->d_ev_pidx) TRY(dalloc(ctx, &ctx->d_ev_pidx, ctx->cap.n_states * ctx->cap.n_states));
+  if (!ctx->d_ev_w) TRY(dalloc(ctx, &ctx->d_ev_w, ctx->cap.n_states));
   CU(cudaMemcpyAsync(ctx->d_ev_pidx, pidx.data(), sizeof(int) * pidx.size(), cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(ctx->d_ev_w, e.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
   if (np > 0) {
@@ -962,6 +1049,7 @@ static gwc_status evgw0_sigma_diag(gwc_ctx* ctx, const std::vector<double>& e, c
 
 gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int* iters, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (!eps_qp || !iters || !(tol > 0.0) || max_iter < 1 || max_iter > 1000)
     return fail(ctx, GWC_ERR_INVALID_ARG, "need eps_qp, iters, tol > 0 and 1 <= max_iter <= 1000");
   const int n = ctx->n_states;
@@ -969,7 +1057,7 @@ gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int
   for (int c = 0; c < n; ++c)
     if (ctx->h_core[c] != c) return fail(ctx, GWC_ERR_INVALID_ARG, "evGW0 needs core_idx = 0..n_states-1");
   cudaStream_t st = (cudaStream_t)stream;
-  if (!ctx->d_ev_sig) TRY(dalloc(ctx, &ctx->d_ev_sig, (size_t)n * 2));
+  if (!ctx->d_ev_sig) TRY(dalloc(ctx, &ctx->d_ev_sig, ctx->cap.n_states * 2));
   if (!ctx->d_ev_diff) TRY(dalloc(ctx, &ctx->d_ev_diff, 1));
   struct GReset {  // later calls see the input energies in G again, on every return path
     gwc_ctx* c;
@@ -1011,6 +1099,7 @@ gwc_status gwc_evgw0(gwc_ctx* ctx, double tol, int max_iter, double* eps_qp, int
 
 gwc_status gwc_qp_solve(gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (!eps_qp || !dh || !iters) return fail(ctx, GWC_ERR_INVALID_ARG, "need eps_qp, dh, iters");
   TRY(need_occupied_cores(ctx, "gwc_qp_solve"));
   cudaStream_t st = (cudaStream_t)stream;
@@ -1032,7 +1121,7 @@ gwc_status gwc_set_qp_cores(gwc_ctx* ctx, const int* cores, int n, void* stream)
     mask[cores[k]] = 1;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  if (!ctx->d_qp_mask) TRY(dalloc(ctx, &ctx->d_qp_mask, ctx->n_core));
+  if (!ctx->d_qp_mask) TRY(dalloc(ctx, &ctx->d_qp_mask, ctx->cap.n_core));
   CU(cudaMemcpyAsync(ctx->d_qp_mask, mask.data(), sizeof(int) * ctx->n_core, cudaMemcpyHostToDevice, st));
   CU(cudaStreamSynchronize(st));  // the host vector goes out of scope
   ctx->qp_mask_set = true;
@@ -1049,6 +1138,7 @@ gwc_status gwc_copy_out(gwc_ctx* ctx, void* dst, const void* src, size_t bytes, 
 gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_omega, const double* im_sigma,
                                  double* a_out, double* nu_out, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (!omega_rel || !im_sigma || !a_out || n_omega < 1 || n_omega > 8192)
     return fail(ctx, GWC_ERR_INVALID_ARG, "need omega_rel, im_sigma, a_out and 1 <= n_omega <= 8192");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1070,8 +1160,9 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
 
 gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
                               double* sigma_c, double* im_sigma_dec, void* stream) {
-  if (ctx) TRY(need_occupied_cores(ctx, "gwc_sigma_core_wac"));
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
+  TRY(need_occupied_cores(ctx, "gwc_sigma_core_wac"));
   if (!omega || !sigma_c || n_omega < 1 || n_omega > (1 << 20) || n_core_ref < 0 || n_val_ref < 0 ||
       n_core_ref + n_val_ref > 4096)
     return fail(ctx, GWC_ERR_INVALID_ARG, "need omega, sigma_c, 1 <= n_omega <= 2^20, reference counts in 0..4096");
@@ -1175,6 +1266,7 @@ gwc_status gwc_g0w0_solutions(gwc_ctx* ctx, const double* omega, int n_omega, co
 gwc_status gwc_gdh_spectrum(gwc_ctx* ctx, const double* omega, int n_omega, const double* sigma_c, const double* dh,
                             double* a_out, double* omega_out, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (!omega || !sigma_c || !dh || !a_out || n_omega < 1)
     return fail(ctx, GWC_ERR_INVALID_ARG, "need omega, sigma_c, dh, a_out and n_omega >= 1");
   LAUNCH(launch_gdh_spectrum(ctx->d_eps, ctx->d_core_idx, ctx->n_core, omega, n_omega, sigma_c, dh, ctx->d_sx,
@@ -1186,6 +1278,7 @@ gwc_status gwc_gdh_spectrum(gwc_ctx* ctx, const double* omega, int n_omega, cons
 gwc_status gwc_request_plan(gwc_ctx* ctx, const double* omega_rel, int n_omega, void* stream) {
   if (ctx) TRY(need_occupied_cores(ctx, "gwc_request_plan"));
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (!omega_rel || n_omega < 1 || n_omega > 8192)
     return fail(ctx, GWC_ERR_INVALID_ARG, "need omega_rel and 1 <= n_omega <= 8192");
   if (ctx->opt.dec != GWC_DECOUPLE_DIAG)
@@ -1218,17 +1311,22 @@ gwc_status gwc_request_plan(gwc_ctx* ctx, const double* omega_rel, int n_omega, 
   for (int c = 0; c < nc; ++c)
     for (int j = 0; j < n_omega; ++j) wrel[(size_t)c * n_omega + j] = omega_rel[j];
   const size_t nt = ctx->opt.n_t;
-  TRY(dalloc(ctx, &ctx->d_req_wrel, wrel.size()));
-  TRY(dalloc(ctx, &ctx->d_req_z, std::max<size_t>(2, z.size())));
-  TRY(dalloc(ctx, &ctx->d_req_rows, std::max<size_t>(1, rows.size())));
-  TRY(dalloc(ctx, &ctx->d_req_pair_of, n_omega));
-  TRY(dalloc(ctx, &ctx->d_req_w, std::max<size_t>(1, (size_t)np) * nc * 2));
-  TRY(dalloc(ctx, &ctx->d_req_im, (size_t)nc * n_omega));
-  TRY(dalloc(ctx, &ctx->d_req_a, (size_t)nc * nt));
-  TRY(dalloc(ctx, &ctx->d_req_nu, nt));
-  TRY(dalloc(ctx, &ctx->d_req_eqp, nc));
-  TRY(dalloc(ctx, &ctx->d_req_dh, nc));
-  TRY(dalloc(ctx, &ctx->d_req_it, nc));
+  // grow-only: a context reused for requests of other sizes (serving) allocates only to grow
+  TRY(grow(ctx, &ctx->d_req_wrel, &ctx->req_cap_wrel, wrel.size()));
+  TRY(grow(ctx, &ctx->d_req_z, &ctx->req_cap_z, std::max<size_t>(2, z.size())));
+  TRY(grow(ctx, &ctx->d_req_rows, &ctx->req_cap_rows, std::max<size_t>(1, rows.size())));
+  TRY(grow(ctx, &ctx->d_req_pair_of, &ctx->req_cap_pair, n_omega));
+  TRY(grow(ctx, &ctx->d_req_w, &ctx->req_cap_w, std::max<size_t>(1, (size_t)np) * nc * 2));
+  TRY(grow(ctx, &ctx->d_req_im, &ctx->req_cap_im, (size_t)nc * n_omega));
+  TRY(grow(ctx, &ctx->d_req_a, &ctx->req_cap_a, (size_t)nc * nt));
+  TRY(grow(ctx, &ctx->d_req_nu, &ctx->req_cap_nu, nt));
+  size_t cap_core = ctx->req_cap_core;
+  TRY(grow(ctx, &ctx->d_req_eqp, &cap_core, nc));
+  cap_core = ctx->req_cap_core;
+  TRY(grow(ctx, &ctx->d_req_dh, &cap_core, nc));
+  cap_core = ctx->req_cap_core;
+  TRY(grow(ctx, &ctx->d_req_it, &cap_core, nc));
+  ctx->req_cap_core = cap_core;
   if (nc * nt * 2 > ctx->cw_cap) {
     TRY(dalloc(ctx, &ctx->d_cw_a, nc * nt * 2));
     TRY(dalloc(ctx, &ctx->d_cw_b, nc * nt * 2));
@@ -1253,6 +1351,7 @@ gwc_status gwc_request_plan(gwc_ctx* ctx, const double* omega_rel, int n_omega, 
 
 gwc_status gwc_request_step(gwc_ctx* ctx, void* stream) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   if (ctx->req_n_omega <= 0) return fail(ctx, GWC_ERR_INVALID_ARG, "no request plan (call gwc_request_plan first)");
   cudaStream_t st = (cudaStream_t)stream;
   const int nc = ctx->n_core;

@@ -236,6 +236,7 @@ struct gwc_ctx {
   int n_states = 0, n_occ = 0, n_virt = 0, n_aux = 0, n_core = 0, n_ov = 0;
   int n_aux_pad = 0, n_ov_pad = 0;
   gwc_options opt{};
+  bool loaded = false;  // a system's arrays are resident (gwc_create with arrays, or gwc_load)
   unsigned long long wait_ns = 1000000000ull;  // bound of the tensor-core kernels' device waits
   double eps_f = 0.0;
   bool vxc_given = false;
@@ -339,6 +340,17 @@ struct gwc_ctx {
   double* d_ev_wres = nullptr;   // [pairs][2]
   double* d_ev_w = nullptr;      // [n_states] current energies
   size_t ev_pair_cap = 0;
+
+  // element counts (bytes where named so) the shape-sized buffers were allocated with, at creation; a
+  // smaller system may be loaded into the context as long as every count fits (gwc_load)
+  struct Caps {
+    size_t n_states = 0, n_core = 0, n_ov = 0, o_ov = 0, o_core = 0, o_pad = 0, plane = 0, qp_np = 0;
+    size_t mats_bytes = 0, dtab = 0, rhs_bytes = 0, rhs_im_bytes = 0, bnorm = 0;
+    int batch = 0;
+  } cap;
+  // grow-only request-mode buffers: element counts allocated
+  size_t req_cap_wrel = 0, req_cap_z = 0, req_cap_rows = 0, req_cap_pair = 0, req_cap_w = 0, req_cap_im = 0,
+         req_cap_a = 0, req_cap_nu = 0, req_cap_core = 0;
 
   // host staging
   int* h_pin_i = nullptr;

@@ -248,6 +248,29 @@ class Context:
         _check(lib().gwc_create(ctypes.byref(self._ctx), ctypes.byref(sysd), ctypes.byref(opt), _stream(stream)), None)
 
     @classmethod
+    def with_capacity(cls, n_states, n_occ, n_aux, n_core, **kw):
+        """A context allocated for a system of these sizes that holds no system yet: gwc_load (``load``) puts
+        one in, of these sizes or smaller (serving slots)."""
+        self = cls.__new__(cls)
+        self._ctx = ctypes.c_void_p()
+        self._keep = []
+        self.n_states, self.n_occ, self.n_aux, self.n_core = int(n_states), int(n_occ), int(n_aux), int(n_core)
+        self.capacity = (self.n_states, self.n_occ, self.n_aux, self.n_core)
+        sysd = System(self.n_states, self.n_occ, self.n_aux, self.n_core, None, None, None, None, None, math.nan, 0)
+        opt = default_options()
+        for k, v in kw.items():
+            if k in ("prec", "dec", "qp_mode"):
+                v = {"prec": PREC, "dec": DEC, "qp_mode": QP}[k][v]
+            if k == "stream":
+                continue
+            setattr(opt, k, v)
+        self.opt = opt
+        self.prec = kw.get("prec", "bf16x3")
+        _check(lib().gwc_create(ctypes.byref(self._ctx), ctypes.byref(sysd), ctypes.byref(opt), _stream(kw.get("stream"))),
+               None)
+        return self
+
+    @classmethod
     def from_molecule(cls, mol, device="cuda", host=False, **kw):
         import torch
 
@@ -259,12 +282,17 @@ class Context:
         return cls(dev(mol.eps), mol.n_occ, mol.core_idx, dev(mol.o_ov), dev(mol.o_core), **args)
 
     # -- entry points ---------------------------------------------------------------------
-    def load(self, eps, o_ov, o_core, vxc=None, eps_f=math.nan, core_idx=None, stream=None):
+    def load(self, eps, o_ov, o_core, vxc=None, eps_f=math.nan, core_idx=None, n_occ=None, stream=None):
+        """gwc_load: a system of the context's sizes, or a smaller one within its capacity (then give n_occ
+        and core_idx; the sizes follow from the arrays)."""
         host = isinstance(eps, np.ndarray)
+        n_states, n_aux = int(eps.shape[0]), int(o_ov.shape[0])
+        n_occ = self.n_occ if n_occ is None else int(n_occ)
         core = np.ascontiguousarray(np.asarray(core_idx if core_idx is not None else range(self.n_core), dtype=np.int32))
-        sysd = System(self.n_states, self.n_occ, self.n_aux, self.n_core, core.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        sysd = System(n_states, n_occ, n_aux, int(core.shape[0]), core.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                       _ptr(eps), _ptr(o_ov), _ptr(o_core), _ptr(vxc), float(eps_f), 1 if host else 0)
         _check(lib().gwc_load(self._ctx, ctypes.byref(sysd), _stream(stream)), self._ctx)
+        self.n_states, self.n_occ, self.n_aux, self.n_core = n_states, n_occ, n_aux, int(core.shape[0])
 
     def build_chi0(self, z, stream=None):
         import torch

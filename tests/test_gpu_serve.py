@@ -71,3 +71,53 @@ def test_admission_respects_the_memory_budget(serve):
     spans = sorted((d.admitted, d.finished) for d in done)
     assert len(done) == 3
     assert all(spans[i + 1][0] >= spans[i][1] for i in range(2))  # strictly one at a time
+
+
+def test_capacity_context_reloads_smaller_systems(serve):
+    """A context created with sizes only (the capacity of a size class) runs requests of smaller molecules
+    loaded with gwc_load, one after another, with the results of a context made for each molecule."""
+    from paper_2412_17132_gb300 import gwc
+
+    n_cap, n_occ_cap, n_aux_cap, n_core_cap = serve.recipe_sizes(150)
+    cap = gwc.Context.with_capacity(n_cap, n_occ_cap, n_aux_cap, n_core_cap, prec="bf16x3", qp_mode="hedin", n_t=1 << 14)
+    with pytest.raises(gwc.GwcError):
+        cap.request_plan(GRID)  # no system loaded yet
+    for rid, n in enumerate((120, 90, 150)):
+        n_s, n_occ, n_aux, n_core = serve.recipe_sizes(n)
+        mol = synth.molecule_device(f"c{rid}", n_s, n_occ, n_core, n_aux, seed=900 + rid, n_t=1 << 14)
+        eps = torch.as_tensor(mol.eps, device="cuda")
+        cap.load(eps, mol.o_ov, mol.o_core, core_idx=mol.core_idx, n_occ=mol.n_occ)
+        cap.request_plan(GRID)
+        cap.request_step()
+        got = [t.cpu().numpy() for t in cap.request_results()]
+        cap.sync()
+        ref_ctx = gwc.Context(eps, mol.n_occ, mol.core_idx, mol.o_ov, mol.o_core, prec="bf16x3", qp_mode="hedin",
+                              n_t=1 << 14)
+        ref_ctx.request_plan(GRID)
+        ref_ctx.request_step()
+        ref = [t.cpu().numpy() for t in ref_ctx.request_results()]
+        ref_ctx.sync()
+        ref_ctx.close()
+        for g, r in zip(got, ref):
+            np.testing.assert_allclose(g, r, rtol=0, atol=1e-12 * max(1.0, float(np.max(np.abs(r)))))
+    big = serve.recipe_sizes(200)
+    mol = synth.molecule_device("big", big[0], big[1], big[3], big[2], seed=1, n_t=1 << 14)
+    with pytest.raises(gwc.GwcError) as err:
+        cap.load(torch.as_tensor(mol.eps, device="cuda"), mol.o_ov, mol.o_core, core_idx=mol.core_idx, n_occ=mol.n_occ)
+    assert err.value.status == 1
+    cap.close()
+
+
+def test_server_reuses_resident_contexts(serve):
+    sizes = [100, 130, 110, 140, 95, 120]
+    srv = serve.SpectrumServer(GRID, budget_bytes=1 << 40, slots=2, n_t=1 << 14)
+    reqs = []
+    for rid, n in enumerate(sizes):
+        n_s, n_occ, n_aux, n_core = serve.recipe_sizes(n)
+        reqs.append(serve.Request(rid=rid, arrival=0.0, n_states=n,
+                                  make=lambda rid=rid, n_s=n_s, n_occ=n_occ, n_aux=n_aux, n_core=n_core:
+                                  synth.molecule_device(f"s{rid}", n_s, n_occ, n_core, n_aux, seed=700 + rid, n_t=1 << 14)))
+    done = srv.run(reqs)
+    assert len(done) == len(sizes) and all(d.status == 0 for d in done)
+    assert srv.created <= 2 and srv.reused >= len(sizes) - 2  # one class, at most one context per slot
+    srv.close()

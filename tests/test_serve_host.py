@@ -27,23 +27,45 @@ class _Ctx:
 
 
 class _FakeServer(serve.SpectrumServer):
-    """The loop of SpectrumServer.run with the GPU start replaced: a request 'runs' for
-    `work[rid]` seconds; every admission records the bytes and slots in use at that moment."""
+    """The loop of SpectrumServer.run with the GPU parts replaced: every request gets its own resident
+    "context" of its footprint (no reuse), admitted while the busy footprints fit the budget or nothing
+    else runs; a request 'runs' for `work[rid]` seconds; every admission records the bytes and slots in
+    use at that moment."""
 
     def __init__(self, budget, slots, work):
         self.budget, self.slots, self.keep = budget, [None] * slots, False
-        self.work, self.log, self.inflight = work, [], {}
+        self.work, self.log, self.inflight, self.pool = work, [], {}, []
 
-    def _start(self, req, stream, now):
+    def _acquire(self, req, input_bytes):
+        busy = sum(e["bytes"] for e in self.pool if e["busy"])
+        if busy + req.footprint > self.budget and any(e["busy"] for e in self.pool):
+            return None
+        self.pool = [e for e in self.pool if e["busy"]]  # idle ones released
+        e = {"busy": True, "ctx": _Ctx(), "bytes": req.footprint, "cls": 0}
+        self.pool.append(e)
+        return e
+
+    def _start(self, req, entry, stream, now):
         req.admitted = now
         live = [r for r in self.inflight.values() if not (r.finished == r.finished)]  # not finished yet
         self.log.append((req.rid, now, sum(r.footprint for r in live) + req.footprint, len(live) + 1))
         self.inflight[req.rid] = req
-        return _Ctx(), (), _Ev(time.perf_counter() + self.work[req.rid])
+        return (), _Ev(time.perf_counter() + self.work[req.rid])
 
 
 def _reqs(sizes, arrivals):
-    return [serve.Request(rid=i, arrival=a, make=None, n_states=0, footprint=f) for i, (f, a) in enumerate(zip(sizes, arrivals))]
+    return [serve.Request(rid=i, arrival=a, make=None, n_states=100, footprint=f) for i, (f, a) in enumerate(zip(sizes, arrivals))]
+
+
+def test_size_classes_and_recipe():
+    assert serve.size_class(100) == 150 and serve.size_class(151) == 225 and serve.size_class(1500) == 1500
+    for n in (100, 149, 150, 700, 1499):
+        c = serve.size_class(n)
+        a, b = serve.recipe_sizes(n), serve.recipe_sizes(c)
+        # every size of the request fits the class's capacity (the context's buffers grow with each)
+        assert all(x <= y for x, y in zip(a, b))
+        n_ov = lambda s: s[1] * (s[0] - s[1])  # noqa: E731
+        assert n_ov(a) <= n_ov(b) and a[2] * n_ov(a) <= b[2] * n_ov(b)
 
 
 def test_admission_respects_budget_and_slots():
