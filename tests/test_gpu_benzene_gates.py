@@ -23,12 +23,15 @@ EV = synth.HARTREE_EV
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "benzene_oracle.json")
 
 # Split-BF16 chi0 has a relative error u ~ 2e-6 (three BF16 products of 8-bit-mantissa parts, FP32
-# accumulation in segments of 512 terms). W^c = b^T (eps^-1 - 1) b moves by about kappa u |W| with the
-# condition number kappa of eps = 1 - Pi. Measured at this size: max |dSigma| / |Sigma| = 6e-5 over the
-# 16 full points and max |d Im Sigma_dec| = 4e-6 Ha on the grid; the bounds below are 4x those.
-SIG_REL = 2.5e-4
-SIG_ABS = 2e-6
-DEC_ABS = 1.6e-5
+# accumulation in segments of 512 terms); W^c = b^T (eps^-1 - 1) b moves by about kappa u |W| with the
+# condition number kappa of eps = 1 - Pi, largest near the RPA poles (the bottom of the window). Measured
+# on a GB300 at this size: max |dSigma| / |Sigma| = 2.4e-4 (grid point 0, 25 eV below the cores; 1.5e-6
+# at the points above the valence residues), an absolute floor of 3.6e-6 Ha there, and max
+# |d Im Sigma_dec| = 1.7e-4 Ha against a peak |Im Sigma_dec| of 1.9 Ha. The bounds are 4x those: a
+# kernel error above 0.1 % of Sigma anywhere on the grid fails them.
+SIG_REL = 1e-3
+SIG_ABS = 1.5e-5
+DEC_ABS = 7e-4
 
 
 @pytest.fixture(scope="module")
