@@ -942,15 +942,16 @@ def run_batch(args):
     from paper_2412_17132_gb300 import gwc, synth
 
     grid = np.linspace(-25.0 / HARTREE_EV, 5.0 / HARTREE_EV, args.omega_points)
-    ctxs, sizes, tuned = [], [], []
+    ctxs, sizes, tuned, ctas_chosen = [], [], [], []
     t_setup = time.perf_counter()
     for j in range(args.molecules):
         mol = synth.batch_member_device(j)
         c = gwc.Context(torch.as_tensor(mol.eps, device="cuda"), mol.n_occ, mol.core_idx, mol.o_ov, mol.o_core,
-                        prec=args.prec, qp_mode="hedin", batch=args.batch or 64, eta=mol.eta, n_im=mol.n_im)
+                        prec=args.prec, qp_mode="hedin", batch=args.batch or 32, eta=mol.eta, n_im=mol.n_im)
         del mol
         c.request_plan(grid)
         tuned.append(c.autotune())
+        ctas_chosen.append(c.chi0_ctas())
         ctxs.append(c)
         sizes.append((c.n_states, c.n_aux, c.n_core))
         torch.cuda.empty_cache()
@@ -959,6 +960,9 @@ def run_batch(args):
     batch = gwc.Batch(ctxs)
     t_cap = time.perf_counter() - t_cap
     times = []
+    clocks = ClockSampler(0)
+    torch.cuda.synchronize()
+    clocks.start()
     for _ in range(args.steps):
         e0, e1 = _events()
         e0.record()
@@ -966,15 +970,20 @@ def run_batch(args):
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
+    clk = clocks.stop()
     points = sum(nc for _, _, nc in sizes) * args.omega_points
     out = {"metric": "batched form: decoupled Sigma points/s (+ Hedin QP + spectra) in one graph launch", "unit": UNIT,
            "value": points / statistics.mean(times), "n_gpus": 1, "steps": args.steps, "data": "synthetic",
            "ms_per_step": 1e3 * statistics.mean(times), "dtype": args.prec,
            "config": {"workload": f"{args.molecules} molecules, N_states ~ U{{100..1300}} (seed 1000+j), N_aux = 3.5 N, "
                                   f"{args.omega_points}-point relative grid, cores = round(0.3 N_occ), QP = eps_n + dH_n",
-                      "sizes_states_aux_cores": sizes, "autotuned_batch": tuned},
+                      "sizes_states_aux_cores": sizes, "autotuned_batch": tuned,
+                      "autotuned_chi0_ctas": ctas_chosen,
+                      "form": ("grouped: per phase one persistent grouped chi0 launch and one grouped LDL^T launch "
+                               "over all molecules, in one CUDA graph") if batch.grouped else "graph of per-molecule steps"},
            "spectra_per_s": sum(nc for _, _, nc in sizes) / statistics.mean(times),
-           "setup_s": t_setup, "capture_s": t_cap}
+           "setup_s": t_setup, "capture_s": t_cap, "clocks": clk,
+           "latency_ms": {"per_launch": [1e3 * t for t in times]}}
     batch.close()
     for c in ctxs:
         c.close()
@@ -997,9 +1006,12 @@ def run_serve(args):
     free, _ = torch.cuda.mem_get_info()
     srv = serve.SpectrumServer(grid, budget_bytes=int(0.5 * free), slots=args.slots, prec=args.prec, qp_mode="hedin",
                                batch=args.batch or 64)
+    clocks = ClockSampler(0)
+    clocks.start()
     t0 = time.perf_counter()
     done = srv.run(reqs, time_limit=args.time_limit)
     makespan = time.perf_counter() - t0
+    clk = clocks.stop()
     summ = serve.summarize(done, makespan)
     out = {"metric": "serving form: spectra/s and p50/p99 latency (arrival to results in host memory)", "unit": "requests/s",
            "value": summ["requests_per_s"], "n_gpus": 1, "data": "synthetic", "dtype": args.prec,
@@ -1009,7 +1021,10 @@ def run_serve(args):
            "serving": summ, "makespan_s": makespan,
            "offered_requests": args.requests, "arrived_by_end": int(sum(1 for a in arr if a <= makespan)),
            "max_sustainable_requests_per_s": summ["requests_per_s"],
+           "contexts": {"created": srv.created, "reused": srv.reused, "classes": list(serve.SIZE_CLASSES)},
+           "sizes_served": [int(r.n_states) for r in done], "clocks": clk,
            "note": "completed/makespan under saturation is the sustainable rate; p50/p99 include queueing"}
+    srv.close()
     print(json.dumps(out), flush=True)
     return 0
 

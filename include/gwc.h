@@ -113,6 +113,9 @@ typedef struct {
                             MMAs it issued, frees its tensor memory and records
                             GWC_ERR_TIMEOUT (reported by gwc_sync); the results of that call
                             are undefined, and the context stays usable. 0..60000000          */
+  int chi0_ctas;         /* launch shape of the tensor-core polarizability build: 0 one CTA per
+                            (128 x 128 tile, frequency group) item; > 0 at most that many CTAs,
+                            each looping over the items (persistent). gwc_autotune may change it */
 } gwc_options;
 
 /* GWC_QP_SECANT: iterate the G_dH W0 QP equation (eq quasiparticle_equation with the shifted
@@ -142,7 +145,7 @@ typedef struct {
 typedef struct gwc_ctx gwc_ctx;
 
 /* Fills o with the defaults: eta 1e-3, n_im 32, xi0 1, BF16X3, DIAG, n_t 2^16, t_max 2000,
- * max_qp_iter 50, qp_tol 1e-7, batch 0, profile 0, qp_mode SECANT, wait_us 0 (one second). */
+ * max_qp_iter 50, qp_tol 1e-7, batch 0, profile 0, qp_mode SECANT, wait_us 0 (one second), chi0_ctas 0. */
 gwc_status gwc_default_options(gwc_options* o);
 
 /* Device bytes a context of this shape allocates (resident copies + workspace + the
@@ -352,23 +355,35 @@ gwc_status gwc_request_results_get(const gwc_ctx* ctx, gwc_request_results* out)
 gwc_status gwc_request_copy_results(const gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, double* im_sigma,
                                     double* a, double* nu, void* stream);
 
-/* Frequencies per internal batch chosen by timing one residue batch (chi0 build, factorisation and
- * contraction of that many frequencies) for 16, 32, ... and the capacity the context was created
- * with, keeping the lowest time per frequency (cached per shape bucket and precision for the
- * process). Needs a request plan; synchronises `stream`; *chosen receives the batch now used. */
+/* Launch shape chosen by timing one residue batch (chi0 build, factorisation and contraction of that many
+ * frequencies) per candidate: frequencies per batch 16, 32, ... up to one SM wave, whole SM waves and the
+ * capacity the context was created with, each with the polarizability build as one CTA per tile item and
+ * as a persistent launch of one CTA per SM; the lowest time per frequency wins (cached per shape bucket
+ * and precision for the process). Needs a request plan; synchronises `stream`; *chosen receives the batch
+ * now used (the chi0 launch shape is in the context's options, gwc_options.chi0_ctas). */
 gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen);
 
 /* ---- Batched form: many molecules of uneven size in one CUDA-graph launch ----------------------
- * gwc_batch_create captures the request step of every context (each with a request plan) on its
- * own forked stream into one CUDA graph; it first runs each step once outside capture, and
- * synchronises `stream` before capturing on a private stream. The contexts
- * must outlive the batch and must not be used concurrently with a launch of it.
- * gwc_batch_launch replays the whole graph on `stream` (results in each context, see
+ * gwc_batch_create captures the request steps of the contexts (each with a request plan) into one CUDA
+ * graph. Grouped form (every context in a tensor-core precision mode with the default factorisation,
+ * GWC_QP_HEDIN, DIAG decoupling): the polarizability builds of each phase (W tables, QP residues, spectrum
+ * residues, chunk by chunk) of ALL molecules go through one persistent grouped chi0 launch (one CTA per
+ * SM, each looping over the (molecule, frequency batch, 128 x 128 tile) items) and the complex
+ * factorisations through one grouped LDL^T launch, with the small per-molecule kernels in between;
+ * otherwise (or with the environment variable GWC_BATCH set) each context's step is captured on its own
+ * forked stream. It first runs the work once outside capture, and synchronises `stream` before capturing
+ * on a private stream. The contexts must outlive the batch and must not be used concurrently with a
+ * launch of it. gwc_batch_launch replays the whole graph on `stream` (results in each context, see
  * gwc_request_results_get). */
 typedef struct gwc_batch gwc_batch;
 gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* stream);
 gwc_status gwc_batch_launch(gwc_batch* batch, void* stream);
 void gwc_batch_destroy(gwc_batch* batch);
+/* 1 if the batch runs in the grouped form, 0 if it is the graph of per-molecule steps. */
+int gwc_batch_is_grouped(const gwc_batch* batch);
+
+/* The options the context runs with (as created, with what gwc_autotune chose). */
+gwc_status gwc_get_options(const gwc_ctx* ctx, gwc_options* out);
 
 /* Synchronises `stream` and reports the first device-side status raised since the
  * previous gwc_sync (then clears it). */

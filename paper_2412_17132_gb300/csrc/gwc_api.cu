@@ -212,6 +212,7 @@ gwc_status validate_options(const gwc_options* o, int n_core) {
   if (o->batch < 0 || o->batch > 4096) return fail(nullptr, GWC_ERR_INVALID_ARG, "batch must be in 0..4096");
   if (o->qp_mode < 0 || o->qp_mode > 2) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad qp_mode");
   if (o->wait_us < 0 || o->wait_us > 60000000) return fail(nullptr, GWC_ERR_INVALID_ARG, "wait_us must be in 0..6e7");
+  if (o->chi0_ctas < 0) return fail(nullptr, GWC_ERR_INVALID_ARG, "chi0_ctas must be >= 0");
   (void)n_core;
   return GWC_OK;
 }
@@ -334,7 +335,8 @@ gwc_status run_chi0_any(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, 
   } else {
     int n = launch_chi0_tc(prec != GWC_PREC_BF16, ctx->d_o_hi, ctx->d_o_lo, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux,
                            ctx->n_aux_pad, ctx->n_ov_pad, (const float*)ctx->d_dtab, ctx->ld_dtab, F, complex_z, alpha,
-                           beta, out, ctx->ldm, stride, active, ctx->d_status, ctx->wait_ns, factor64(prec), st);
+                           beta, out, ctx->ldm, stride, active, ctx->d_status, ctx->wait_ns, factor64(prec), st,
+                           ctx->opt.chi0_ctas);
     if (n == -2) return fail(ctx, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for this shape/device");
     LAUNCH(n);
     if (full) {
@@ -379,18 +381,34 @@ gwc_status run_chi0_stride(gwc_ctx* ctx, bool complex_z, int F, const double* d_
 // ---- imaginary-axis W table --------------------------------------------------------------------
 // Enqueues W^c_mn(i xi_k) for all states m and cores n, k = 0..n_im (node n_im is xi = 0), without
 // host synchronisation or allocation (the frequencies were uploaded at creation).
+// Imaginary-axis nodes per table batch (all n_im + 1 in one batch when the workspace holds them).
+int wim_batch(const gwc_ctx* ctx) {
+  const size_t per_real = (size_t)ctx->n_aux * ctx->ldm * mat_elem_bytes(real_kind(ctx));
+  const int fb = (int)std::max<size_t>(1, std::min<size_t>(ctx->mats_bytes / per_real, (size_t)ctx->batch));
+  return std::min(fb, ctx->opt.n_im + 1);
+}
+
+gwc_status enqueue_wim_tail(gwc_ctx* ctx, int k0, int nb, cudaStream_t st);
+
 gwc_status enqueue_wim(gwc_ctx* ctx, cudaStream_t st) {
   const int nodes = ctx->opt.n_im + 1;
-  MatKind rk = real_kind(ctx);
-  const size_t per_real = (size_t)ctx->n_aux * ctx->ldm * mat_elem_bytes(rk);
-  int fb = (int)std::max<size_t>(1, std::min<size_t>(ctx->mats_bytes / per_real, (size_t)ctx->batch));
-  fb = std::min(fb, nodes);
-  const int r = ctx->n_states * ctx->n_core;
-  const size_t plane = (size_t)ctx->n_states * ctx->n_core;
-  const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  const int fb = wim_batch(ctx);
   for (int k0 = 0; k0 < nodes; k0 += fb) {
     const int nb = std::min(fb, nodes - k0);
     TRY(run_chi0(ctx, false, nb, ctx->d_zim + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st));
+    TRY(enqueue_wim_tail(ctx, k0, nb, st));
+  }
+  return GWC_OK;
+}
+
+// Nodes k0 .. k0+nb-1 of the W table once their eps = 1 - Pi(i xi) are in the workspace: factorisations,
+// right-hand sides, solves and the copy into the table.
+gwc_status enqueue_wim_tail(gwc_ctx* ctx, int k0, int nb, cudaStream_t st) {
+  MatKind rk = real_kind(ctx);
+  const int r = ctx->n_states * ctx->n_core;
+  const size_t plane = (size_t)ctx->n_states * ctx->n_core;
+  const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  {
     cudaEvent_t ev = ev_begin(ctx, st);
     LAUNCH(launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st));
     ev_end(ctx, kClsFactor, ev, st);
@@ -568,6 +586,7 @@ gwc_status gwc_default_options(gwc_options* o) {
   o->profile = 0;
   o->qp_mode = GWC_QP_SECANT;
   o->wait_us = 0;
+  o->chi0_ctas = 0;
   return GWC_OK;
 }
 
@@ -1402,7 +1421,8 @@ gwc_status gwc_request_copy_results(const gwc_ctx* ctx, double* eps_qp, double* 
 // ---- autotuner: frequencies per batch, timed on the request step, cached per shape bucket ------------
 namespace {
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int, int>, int> g_tune_cache;  // (n_aux/128, n_ov/4096, n_core, prec) -> batch
+// (n_aux/128, n_ov/4096, n_core, prec) -> (frequencies per batch, chi0 CTAs: 0 one per item, else persistent)
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 }  // namespace
 
 gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
@@ -1414,7 +1434,8 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      ctx->batch = std::min(it->second, ctx->batch_cap);
+      ctx->batch = std::min(it->second.first, ctx->batch_cap);
+      ctx->opt.chi0_ctas = it->second.second;
       if (chosen) *chosen = ctx->batch;
       return GWC_OK;
     }
@@ -1435,22 +1456,29 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
   for (int f = ctx->n_sm; f < ctx->batch_cap; f += ctx->n_sm) cands.push_back(f);
   cands.push_back(ctx->batch_cap);
   const int np = ctx->req_n_pairs;
+  const bool tc = ctx->opt.prec == GWC_PREC_BF16 || ctx->opt.prec == GWC_PREC_BF16X3 || ctx->opt.prec == GWC_PREC_BF16X3_F64;
+  const int saved_ctas = ctx->opt.chi0_ctas;
+  int best_ctas = saved_ctas;
   for (int f : cands) {
     if (res != GWC_OK || np <= 0) break;
     const int nb = std::min(f, np);
     ctx->batch = nb;
-    res = residue_batches(ctx, nb, ctx->d_req_z, ctx->d_req_rows, ctx->n_core, ctx->d_req_w, nullptr, st);
-    if (res != GWC_OK) break;
-    cudaEventRecord(e0, st);
-    res = residue_batches(ctx, nb, ctx->d_req_z, ctx->d_req_rows, ctx->n_core, ctx->d_req_w, nullptr, st);
-    cudaEventRecord(e1, st);
-    if (cudaEventSynchronize(e1) != cudaSuccess) res = fail(ctx, GWC_ERR_CUDA, "autotune sync failed");
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    const double per = ms / nb;
-    if (res == GWC_OK && per < best_per) {
-      best_per = per;
-      best = f;
+    for (int shape = 0; shape < (tc ? 2 : 1) && res == GWC_OK; ++shape) {
+      ctx->opt.chi0_ctas = tc ? (shape == 0 ? 0 : ctx->n_sm) : saved_ctas;
+      res = residue_batches(ctx, nb, ctx->d_req_z, ctx->d_req_rows, ctx->n_core, ctx->d_req_w, nullptr, st);
+      if (res != GWC_OK) break;
+      cudaEventRecord(e0, st);
+      res = residue_batches(ctx, nb, ctx->d_req_z, ctx->d_req_rows, ctx->n_core, ctx->d_req_w, nullptr, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) res = fail(ctx, GWC_ERR_CUDA, "autotune sync failed");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per = ms / nb;
+      if (res == GWC_OK && per < best_per) {
+        best_per = per;
+        best = f;
+        best_ctas = ctx->opt.chi0_ctas;
+      }
     }
     if (nb < f) break;  // fewer pairs than the candidate: larger batches change nothing
   }
@@ -1458,16 +1486,249 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
   cudaEventDestroy(e1);
   ctx->opt.profile = saved_profile;
   ctx->batch = best;
+  ctx->opt.chi0_ctas = best_ctas;
   if (res != GWC_OK) return res;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = best;
+    g_tune_cache[key] = std::make_pair(best, best_ctas);
   }
   if (chosen) *chosen = best;
   return GWC_OK;
 }
 
 // ---- batched form: one CUDA graph over many contexts ----------------------------------------------------
+// Grouped form (all contexts in a tensor-core mode, Hedin QP, DIAG decoupling): every polarizability build of
+// a phase, over all molecules, goes through ONE persistent grouped chi0 launch (n_SM CTAs looping over the
+// (molecule, frequency batch, tile) items) and every complex factorisation through ONE grouped LDL^T launch;
+// the small per-molecule kernels (D tables, appended rows, contractions, QP update, spectra) sit between
+// them. The whole sequence is captured into one CUDA graph.
+namespace {
+
+struct GroupedLaunch {
+  bool complex_z = false;
+  std::vector<int> ctx_of;      // context of each chi0 group / factor group
+  std::vector<int> p0, nb;      // pair range of each context in this launch
+  size_t chi0_off = 0;          // byte offset of the chi0 descriptors in the batch's device buffer
+  int chi0_groups = 0, chi0_items = 0;
+  size_t fac_off = 0;           // byte offset of the factor descriptors (complex launches)
+  int fac_groups = 0, fac_ctas = 0;
+};
+
+struct GroupedPlan {
+  std::vector<GroupedLaunch> table, qp, spec;  // one per chunk of imaginary nodes / pairs
+  void* d_desc = nullptr;
+  size_t desc_bytes = 0;
+  int chi0_ctas = 0;
+};
+
+bool grouped_eligible(gwc_ctx* const* ctxs, int n) {
+  for (int i = 0; i < n; ++i) {
+    const gwc_ctx* c = ctxs[i];
+    if (!(c->opt.prec == GWC_PREC_BF16 || c->opt.prec == GWC_PREC_BF16X3) || !c->factor_tc) return false;
+    if (c->opt.qp_mode != GWC_QP_HEDIN || c->opt.dec != GWC_DECOUPLE_DIAG || c->req_n_omega <= 0) return false;
+    if (c->n_core > c->border_max) return false;
+  }
+  return true;
+}
+
+// Residue chunks of one context: whole SM waves of its batch, as residue_batches_buf makes them.
+int chunk_of(const gwc_ctx* c) {
+  int chunk = std::max(1, c->batch);
+  if (chunk >= c->n_sm) chunk -= chunk % c->n_sm;
+  return chunk;
+}
+
+// Appends the descriptors of one grouped launch: a chi0 group and (complex) a factor group per context
+// chunk. kind 0: table, 1: QP pairs, 2: spectrum pairs; k: chunk index.
+gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, std::vector<uint8_t>& host, GroupedLaunch& L) {
+  const size_t gb = chi0_group_bytes();
+  L.complex_z = kind != 0;
+  std::vector<uint8_t> chi0((size_t)n * gb);
+  std::vector<LdltGroup> fac;
+  int items = 0, ctas = 0, groups = 0;
+  // largest contraction first: with the items dealt round-robin to the persistent CTAs, the long items are
+  // spread over all CTAs and the short ones fill in behind them
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)ctxs[a]->n_ov_pad * ctxs[a]->n_aux_pad > (long long)ctxs[b]->n_ov_pad * ctxs[b]->n_aux_pad;
+  });
+  for (int i : order) {
+    gwc_ctx* c = ctxs[i];
+    int F, p0 = 0;
+    const int* act = nullptr;
+    long long stride;
+    int r = 0;
+    if (kind == 0) {
+      const int fb = wim_batch(c);
+      p0 = k * fb;
+      if (p0 >= c->opt.n_im + 1) continue;
+      F = std::min(fb, c->opt.n_im + 1 - p0);
+      stride = (long long)c->n_aux * c->ldm;
+    } else {
+      const int np = kind == 1 ? c->n_core * c->n_occ : c->req_n_pairs;
+      const int chunk = chunk_of(c);
+      p0 = k * chunk;
+      if (p0 >= np) continue;
+      F = std::min(chunk, np - p0);
+      r = kind == 1 ? 1 : c->n_core;
+      stride = (long long)(c->n_aux + r) * c->ldm;
+      if (kind == 1) act = c->d_qp_active + p0;
+    }
+    const int got = chi0_group_fill(chi0.data() + (size_t)groups * gb, c->opt.prec != GWC_PREC_BF16, c->d_o_hi, c->d_o_lo,
+                                    c->d_o_f32, c->n_ov_pad, c->n_aux, c->n_aux_pad, c->n_ov_pad,
+                                    (const float*)c->d_dtab, c->ld_dtab, F, kind != 0, -1.0, 1.0, c->d_mats, c->ldm, stride,
+                                    act, false, items);
+    if (got < 0) return fail(nullptr, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for a batch member");
+    items += got;
+    if (kind != 0) {
+      LdltGroup G;
+      G.mats = static_cast<float2*>(c->d_mats);
+      G.ldm = c->ldm;
+      G.stride = stride;
+      G.active = act;
+      G.n = c->n_aux;
+      G.nrow = c->n_aux + r;
+      G.F = F;
+      G.cta0 = ctas;
+      ctas += F;
+      fac.push_back(G);
+    }
+    L.ctx_of.push_back(i);
+    L.p0.push_back(p0);
+    L.nb.push_back(F);
+    ++groups;
+  }
+  L.chi0_groups = groups;
+  L.chi0_items = items;
+  if (groups == 0) return GWC_OK;
+  // descriptors, 64-byte aligned pieces of one buffer
+  auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+  L.chi0_off = align(host.size());
+  host.resize(L.chi0_off + (size_t)groups * gb);
+  std::memcpy(host.data() + L.chi0_off, chi0.data(), (size_t)groups * gb);
+  if (!fac.empty()) {
+    L.fac_off = align(host.size());
+    host.resize(L.fac_off + fac.size() * sizeof(LdltGroup));
+    std::memcpy(host.data() + L.fac_off, fac.data(), fac.size() * sizeof(LdltGroup));
+    L.fac_groups = (int)fac.size();
+    L.fac_ctas = ctas;
+  }
+  return GWC_OK;
+}
+
+gwc_status build_plan(gwc_ctx* const* ctxs, int n, GroupedPlan& P) {
+  std::vector<uint8_t> host;
+  for (int k = 0;; ++k) {
+    GroupedLaunch L;
+    TRY(plan_launch(ctxs, n, 0, k, host, L));
+    if (L.chi0_groups == 0) break;
+    P.table.push_back(L);
+  }
+  for (int k = 0;; ++k) {
+    GroupedLaunch L;
+    TRY(plan_launch(ctxs, n, 1, k, host, L));
+    if (L.chi0_groups == 0) break;
+    P.qp.push_back(L);
+  }
+  for (int k = 0;; ++k) {
+    GroupedLaunch L;
+    TRY(plan_launch(ctxs, n, 2, k, host, L));
+    if (L.chi0_groups == 0) break;
+    P.spec.push_back(L);
+  }
+  P.desc_bytes = host.size();
+  if (cudaMalloc(&P.d_desc, std::max<size_t>(host.size(), 256)) != cudaSuccess)
+    return fail(nullptr, GWC_ERR_OOM, "batch descriptor allocation failed");
+  if (cudaMemcpy(P.d_desc, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(nullptr, GWC_ERR_CUDA, "batch descriptor upload failed");
+  return GWC_OK;
+}
+
+#define BCU(call)                                                                                              \
+  do {                                                                                                         \
+    if ((call) < 0) return fail(nullptr, GWC_ERR_CUDA, std::string("batch launch failed: ") + #call);        \
+  } while (0)
+
+// One grouped launch of residue builds: D tables of every member, one chi0 launch, the appended rows, one
+// factorisation launch, the contractions.
+gwc_status enqueue_grouped_residues(gwc_ctx* const* ctxs, const GroupedPlan& P, const GroupedLaunch& L, int kind,
+                                    cudaStream_t st) {
+  const char* base = static_cast<const char*>(P.d_desc);
+  unsigned* status = ctxs[L.ctx_of[0]]->d_status;
+  unsigned long long wait_ns = ctxs[L.ctx_of[0]]->wait_ns;
+  for (size_t j = 0; j < L.ctx_of.size(); ++j) {
+    gwc_ctx* c = ctxs[L.ctx_of[j]];
+    const double* z = (kind == 1 ? c->d_qp_z : c->d_req_z) + 2 * (size_t)L.p0[j];
+    BCU(launch_dtable(z, L.nb[j], c->d_delta, c->n_ov, c->ld_dtab, true, c->d_dtab, st));
+  }
+  BCU(launch_chi0_tc_grouped(base + L.chi0_off, L.chi0_groups, L.chi0_items, true, P.chi0_ctas, status, wait_ns, st));
+  for (size_t j = 0; j < L.ctx_of.size(); ++j) {
+    gwc_ctx* c = ctxs[L.ctx_of[j]];
+    const int r = kind == 1 ? 1 : c->n_core;
+    const long long stride = (long long)(c->n_aux + r) * c->ldm;
+    const int* rows = (kind == 1 ? c->d_qp_rowmap : c->d_req_rows) + (size_t)L.p0[j] * r;
+    BCU(launch_border_rows(MatKind::CplxF32, c->d_mats, c->n_aux, c->ldm, stride, c->d_o_core, c->n_aux, rows, L.nb[j], r,
+                           c->d_bnorm, st));
+  }
+  BCU(launch_ldlt_tc_grouped(reinterpret_cast<const LdltGroup*>(base + L.fac_off), L.fac_groups, L.fac_ctas, status,
+                             wait_ns, st));
+  for (size_t j = 0; j < L.ctx_of.size(); ++j) {
+    gwc_ctx* c = ctxs[L.ctx_of[j]];
+    const int r = kind == 1 ? 1 : c->n_core;
+    const long long stride = (long long)(c->n_aux + r) * c->ldm;
+    double* w = (kind == 1 ? c->d_qp_w : c->d_req_w) + (size_t)L.p0[j] * r * 2;
+    const int* act = kind == 1 ? c->d_qp_active + L.p0[j] : nullptr;
+    BCU(launch_border_w(MatKind::CplxF32, c->d_mats, c->n_aux, c->ldm, stride, L.nb[j], r, c->d_bnorm, w, (long long)r * 2,
+                        act, st));
+  }
+  return GWC_OK;
+}
+
+// The request step of every context as grouped launches, enqueued on `st` (capturable: no host sync).
+gwc_status enqueue_grouped_step(gwc_ctx* const* ctxs, int n, const GroupedPlan& P, cudaStream_t st) {
+  const char* base = static_cast<const char*>(P.d_desc);
+  // imaginary-axis W tables: one grouped chi0 launch over all molecules' nodes (per chunk of nodes)
+  for (const GroupedLaunch& L : P.table) {
+    for (size_t j = 0; j < L.ctx_of.size(); ++j) {
+      gwc_ctx* c = ctxs[L.ctx_of[j]];
+      BCU(launch_dtable(c->d_zim + 2 * (size_t)L.p0[j], L.nb[j], c->d_delta, c->n_ov, c->ld_dtab, true, c->d_dtab, st));
+    }
+    BCU(launch_chi0_tc_grouped(base + L.chi0_off, L.chi0_groups, L.chi0_items, false, P.chi0_ctas,
+                               ctxs[L.ctx_of[0]]->d_status, ctxs[L.ctx_of[0]]->wait_ns, st));
+    for (size_t j = 0; j < L.ctx_of.size(); ++j) TRY(enqueue_wim_tail(ctxs[L.ctx_of[j]], L.p0[j], L.nb[j], st));
+  }
+  for (int i = 0; i < n; ++i) ctxs[i]->wim_valid = true;
+  // QP: the Hedin shift of every core (eq QPGWC), its residue pairs in grouped launches
+  for (int i = 0; i < n; ++i) {
+    gwc_ctx* c = ctxs[i];
+    BCU(launch_qp_init(c->d_eps, c->d_core_idx, c->n_core, c->qp_mask_set ? c->d_qp_mask : nullptr, c->d_qp, st));
+    BCU(launch_qp_pairs(c->d_eps, c->d_core_idx, c->n_core, c->n_occ, c->eps_f, c->opt.eta, c->d_qp, c->d_qp_z,
+                        c->d_qp_active, c->d_qp_fac, c->d_all_done, c->d_active_builds, st));
+  }
+  for (const GroupedLaunch& L : P.qp) TRY(enqueue_grouped_residues(ctxs, P, L, 1, st));
+  for (int i = 0; i < n; ++i) {
+    gwc_ctx* c = ctxs[i];
+    BCU(launch_qp_assemble_update(c->d_eps, c->n_states, c->n_occ, c->n_core, c->d_core_idx, c->eps_f, c->d_xi, c->d_wxi,
+                                  c->opt.n_im, c->d_wim, c->d_qp_w, c->d_qp_fac, c->d_sx, c->d_vxc_eff, c->opt.qp_tol,
+                                  c->opt.max_qp_iter, 0, c->d_qp, c->d_all_done, st));
+    BCU(launch_qp_finish_hedin(c->d_qp, c->d_eps, c->d_core_idx, c->n_core, c->d_req_eqp, c->d_req_dh, c->d_req_it, st));
+  }
+  // decoupled Im Sigma on the relative grid and the spectra
+  for (const GroupedLaunch& L : P.spec) TRY(enqueue_grouped_residues(ctxs, P, L, 2, st));
+  for (int i = 0; i < n; ++i) {
+    gwc_ctx* c = ctxs[i];
+    BCU(launch_request_dec(c->d_eps, c->d_core_idx, c->n_core, c->eps_f, c->d_req_wrel, c->req_n_omega, c->d_req_pair_of,
+                           c->d_req_w, c->d_req_im, st));
+    BCU(launch_cumulant_spectrum(c->d_req_wrel, c->req_n_omega, c->d_req_im, c->n_core, c->opt.n_t, c->opt.t_max,
+                                 c->opt.eta, c->d_cw_a, c->d_cw_b, c->d_coef, c->d_tw, c->d_req_a, c->d_req_nu, st));
+  }
+  return GWC_OK;
+}
+#undef BCU
+
+}  // namespace
+
 struct gwc_batch {
   cudaStream_t cap = nullptr;  // internal capture origin (the caller's stream may be the legacy one)
   cudaGraph_t graph = nullptr;
@@ -1475,6 +1736,8 @@ struct gwc_batch {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   std::vector<gwc_ctx*> ctxs;
+  bool grouped = false;
+  GroupedPlan plan;
 };
 
 void gwc_batch_destroy(gwc_batch* b) {
@@ -1484,8 +1747,11 @@ void gwc_batch_destroy(gwc_batch* b) {
   for (auto e : b->events) cudaEventDestroy(e);
   for (auto s : b->streams) cudaStreamDestroy(s);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->plan.d_desc) cudaFree(b->plan.d_desc);
   delete b;
 }
+
+int gwc_batch_is_grouped(const gwc_batch* b) { return b && b->grouped ? 1 : 0; }
 
 gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* stream) {
   // errors of this function go to gwc_last_error(NULL)
@@ -1504,49 +1770,89 @@ gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* 
       cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
     return bail(GWC_ERR_CUDA, "capture stream creation failed");
   cudaStream_t st = b->cap;
-  b->streams.resize(n);
-  b->events.resize(n + 1);
-  for (int i = 0; i < n; ++i)
-    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess)
-      return bail(GWC_ERR_CUDA, "stream creation failed");
-  for (int i = 0; i <= n; ++i)
-    if (cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming) != cudaSuccess)
-      return bail(GWC_ERR_CUDA, "event creation failed");
-  // one uncaptured run per context sets function attributes and first-use state
   std::vector<int> saved(n);
   for (int i = 0; i < n; ++i) {
     saved[i] = ctxs[i]->opt.profile;
     ctxs[i]->opt.profile = 0;
-    if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK) {
-      for (int k = 0; k <= i; ++k) ctxs[k]->opt.profile = saved[k];
-      return bail(GWC_ERR_CUDA, std::string("warm-up step failed: ") + ctxs[i]->last_error);
-    }
   }
-  for (int i = 0; i < n; ++i)
-    if (cudaStreamSynchronize(b->streams[i]) != cudaSuccess) return bail(GWC_ERR_CUDA, "warm-up sync failed");
+  auto restore = [&]() {
+    for (int i = 0; i < n; ++i) ctxs[i]->opt.profile = saved[i];
+  };
+  b->grouped = grouped_eligible(ctxs, n) && std::getenv("GWC_BATCH") == nullptr;
   gwc_status res = GWC_OK;
   std::string msg;
-  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-    res = GWC_ERR_CUDA;
-    msg = "cudaStreamBeginCapture failed";
-  } else {
-    cudaEventRecord(b->events[n], st);
-    for (int i = 0; i < n && res == GWC_OK; ++i) {
-      cudaStreamWaitEvent(b->streams[i], b->events[n], 0);
-      if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK) {
-        res = GWC_ERR_CUDA;
-        msg = std::string("capture of a step failed: ") + ctxs[i]->last_error;
-      }
-      cudaEventRecord(b->events[i], b->streams[i]);
-      cudaStreamWaitEvent(st, b->events[i], 0);
+  if (b->grouped) {
+    if (build_plan(ctxs, n, b->plan) != GWC_OK) {
+      restore();
+      return bail(GWC_ERR_CUDA, std::string("grouped plan: ") + g_create_error);
     }
-    cudaError_t e = cudaStreamEndCapture(st, &b->graph);
-    if (res == GWC_OK && e != cudaSuccess) {
+    b->plan.chi0_ctas = ctxs[0]->n_sm;  // persistent: one CTA per SM (the kernel's shared memory allows one)
+    // one uncaptured run sets function attributes and first-use state
+    if (enqueue_grouped_step(ctxs, n, b->plan, st) != GWC_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+      restore();
+      return bail(GWC_ERR_CUDA, std::string("grouped warm-up step failed: ") + g_create_error);
+    }
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
       res = GWC_ERR_CUDA;
-      msg = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+      msg = "cudaStreamBeginCapture failed";
+    } else {
+      if (enqueue_grouped_step(ctxs, n, b->plan, st) != GWC_OK) {
+        res = GWC_ERR_CUDA;
+        msg = std::string("capture of the grouped step failed: ") + g_create_error;
+      }
+      cudaError_t e = cudaStreamEndCapture(st, &b->graph);
+      if (res == GWC_OK && e != cudaSuccess) {
+        res = GWC_ERR_CUDA;
+        msg = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+      }
+    }
+  } else {
+    b->streams.resize(n);
+    b->events.resize(n + 1);
+    for (int i = 0; i < n; ++i)
+      if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+        restore();
+        return bail(GWC_ERR_CUDA, "stream creation failed");
+      }
+    for (int i = 0; i <= n; ++i)
+      if (cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming) != cudaSuccess) {
+        restore();
+        return bail(GWC_ERR_CUDA, "event creation failed");
+      }
+    // one uncaptured run per context sets function attributes and first-use state
+    for (int i = 0; i < n; ++i) {
+      if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK) {
+        restore();
+        return bail(GWC_ERR_CUDA, std::string("warm-up step failed: ") + ctxs[i]->last_error);
+      }
+    }
+    for (int i = 0; i < n; ++i)
+      if (cudaStreamSynchronize(b->streams[i]) != cudaSuccess) {
+        restore();
+        return bail(GWC_ERR_CUDA, "warm-up sync failed");
+      }
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      res = GWC_ERR_CUDA;
+      msg = "cudaStreamBeginCapture failed";
+    } else {
+      cudaEventRecord(b->events[n], st);
+      for (int i = 0; i < n && res == GWC_OK; ++i) {
+        cudaStreamWaitEvent(b->streams[i], b->events[n], 0);
+        if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK) {
+          res = GWC_ERR_CUDA;
+          msg = std::string("capture of a step failed: ") + ctxs[i]->last_error;
+        }
+        cudaEventRecord(b->events[i], b->streams[i]);
+        cudaStreamWaitEvent(st, b->events[i], 0);
+      }
+      cudaError_t e = cudaStreamEndCapture(st, &b->graph);
+      if (res == GWC_OK && e != cudaSuccess) {
+        res = GWC_ERR_CUDA;
+        msg = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+      }
     }
   }
-  for (int i = 0; i < n; ++i) ctxs[i]->opt.profile = saved[i];
+  restore();
   if (res != GWC_OK) return bail(res, msg);
   cudaError_t e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   if (e != cudaSuccess) return bail(GWC_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
@@ -1574,6 +1880,12 @@ gwc_status gwc_sync(gwc_ctx* ctx, void* stream) {
   if (flags & kStatSingular) return fail(ctx, GWC_ERR_SINGULAR, "zero pivot in a dielectric factorisation");
   if (flags & kStatNotConverged) return fail(ctx, GWC_ERR_NOT_CONVERGED, "QP secant iteration hit max_qp_iter");
   if (flags & kStatBadIndex) return fail(ctx, GWC_ERR_INVALID_ARG, "device-side index check failed");
+  return GWC_OK;
+}
+
+gwc_status gwc_get_options(const gwc_ctx* ctx, gwc_options* out) {
+  if (!ctx || !out) return GWC_ERR_INVALID_ARG;
+  *out = ctx->opt;
   return GWC_OK;
 }
 

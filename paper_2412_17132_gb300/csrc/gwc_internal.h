@@ -115,7 +115,19 @@ int launch_chi0_simt(MatKind kind, const void* o_ov /*double or float [n_aux][ld
 int launch_chi0_tc(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32, int ld_pad,
                    int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F, bool complex_out,
                    double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
-                   unsigned* status, unsigned long long wait_ns, bool out64 /*FP64 matrices*/, cudaStream_t s);
+                   unsigned* status, unsigned long long wait_ns, bool out64 /*FP64 matrices*/, cudaStream_t s,
+                   int persist = 0 /*0: one CTA per item; > 0: at most that many CTAs looping over items*/);
+// Grouped chi0: several molecules' frequency batches in one launch. chi0_group_fill writes one descriptor
+// (chi0_group_bytes() bytes, 64-byte aligned in device memory) whose items are numbered from item0 and
+// returns its item count (or -2 if unsupported); launch_chi0_tc_grouped runs n_items items of the
+// n_groups descriptors (ascending item0) on `grid` CTAs, each looping over items.
+size_t chi0_group_bytes();
+int chi0_group_fill(void* dst, bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32,
+                    int ld_pad, int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F,
+                    bool complex_out, double alpha, double beta, void* out, long long ldm, long long mat_stride,
+                    const int* active, bool out64, int item0);
+int launch_chi0_tc_grouped(const void* d_groups, int n_groups, int n_items, bool complex_out, int grid, unsigned* status,
+                           unsigned long long wait_ns, cudaStream_t s);
 
 // Batched in-place LDL^T of F matrices [nrow][ldm]: the first n columns are factored (W = L D below
 // the diagonal, d on it, L^T above it); rows n..nrow-1 are appended right-hand sides that the row
@@ -126,6 +138,17 @@ int launch_ldlt(MatKind kind, void* mats, int n, int nrow, long long ldm, long l
 // Returns -2 if the device has no tcgen05.
 int launch_ldlt_tc(void* mats, int n, int nrow, long long ldm, long long mat_stride, int F, const int* active,
                    unsigned* status, unsigned long long wait_ns, cudaStream_t s);
+// Grouped tensor-core factorisation: several batches of complex FP32 matrices (of different sizes) in one
+// launch, one CTA per matrix; group g owns CTAs cta0 .. cta0 + F - 1 (groups ascending in cta0). The
+// layout rules of launch_ldlt_tc hold per group (ldm, stride multiples of 4, 16-byte aligned mats).
+struct LdltGroup {
+  float2* mats;
+  long long ldm, stride;
+  const int* active;  // per matrix, or null
+  int n, nrow, F, cta0;
+};
+int launch_ldlt_tc_grouped(const LdltGroup* d_groups, int n_groups, int n_ctas, unsigned* status,
+                           unsigned long long wait_ns, cudaStream_t s);
 // Appended rows: row n+q of matrix f = o_core row row_of[f*r+q]; bnorm2 = |b|^2.
 int launch_border_rows(MatKind kind, void* mats, int n, long long ldm, long long stride, const double* src,
                        long long src_row_stride, const int* row_of, int F, int r, double* bnorm2, cudaStream_t s);

@@ -607,12 +607,9 @@ __device__ void epilogue_role(const TcSmem& sm, uint32_t tmem_base, float2* __re
   }
 }
 
-__global__ void __launch_bounds__(NT_TC, 1)
-    ldlt_tc_kernel(float2* __restrict__ mats, int n, int nrow, long long ldm, long long stride,
-                   const int* __restrict__ active, unsigned* __restrict__ status, unsigned long long wait_ns) {
-  const int f = blockIdx.x;
-  if (active && !active[f]) return;  // uniform across the CTA, before any barrier or TMEM use
-  float2* A = mats + f * stride;
+// The factorisation of one matrix A (n columns, nrow rows) by one CTA.
+__device__ __forceinline__ void ldlt_tc_matrix(float2* __restrict__ A, int n, int nrow, long long ldm,
+                                               unsigned* __restrict__ status, unsigned long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   TcSmem sm;
   sm.base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -702,7 +699,45 @@ __global__ void __launch_bounds__(NT_TC, 1)
   }
 }
 
+__global__ void __launch_bounds__(NT_TC, 1)
+    ldlt_tc_kernel(float2* __restrict__ mats, int n, int nrow, long long ldm, long long stride,
+                   const int* __restrict__ active, unsigned* __restrict__ status, unsigned long long wait_ns) {
+  const int f = blockIdx.x;
+  if (active && !active[f]) return;  // uniform across the CTA, before any barrier or TMEM use
+  ldlt_tc_matrix(mats + f * stride, n, nrow, ldm, status, wait_ns);
+}
+
+// Grouped: CTA b factors matrix b - cta0 of the group whose CTA range holds b (groups ascending in cta0).
+__global__ void __launch_bounds__(NT_TC, 1)
+    ldlt_tc_grouped_kernel(const LdltGroup* __restrict__ gs, int n_groups, unsigned* __restrict__ status,
+                           unsigned long long wait_ns) {
+  int lo = 0, hi = n_groups - 1;
+  while (lo < hi) {  // last group with cta0 <= blockIdx.x
+    const int mid = (lo + hi + 1) / 2;
+    if (gs[mid].cta0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const LdltGroup& G = gs[lo];
+  const int f = blockIdx.x - G.cta0;
+  if (f >= G.F) return;
+  if (G.active && !G.active[f]) return;  // uniform across the CTA, before any barrier or TMEM use
+  ldlt_tc_matrix(G.mats + f * G.stride, G.n, G.nrow, G.ldm, status, wait_ns);
+}
+
 }  // namespace
+
+int launch_ldlt_tc_grouped(const LdltGroup* d_groups, int n_groups, int n_ctas, unsigned* status,
+                           unsigned long long wait_ns, cudaStream_t s) {
+  if (!tc_supported()) return -2;
+  if (n_groups < 1 || n_ctas < 1) return -1;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(ldlt_tc_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC) != cudaSuccess)
+      return -1;
+    attr = true;
+  }
+  ldlt_tc_grouped_kernel<<<n_ctas, NT_TC, SMEM_TC, s>>>(d_groups, n_groups, status, wait_ns);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 // Returns 1 (launches), -1 on a launch error or bad layout, -2 if the device has no tcgen05.
 int launch_ldlt_tc(void* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active,

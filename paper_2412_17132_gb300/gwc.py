@@ -70,6 +70,7 @@ class Options(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("qp_mode", ctypes.c_int),
         ("wait_us", ctypes.c_int),
+        ("chi0_ctas", ctypes.c_int),
     ]
 
 
@@ -125,6 +126,8 @@ _SIGS = {
                                         ctypes.c_void_p]),
     "gwc_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_batch_destroy": (None, [ctypes.c_void_p]),
+    "gwc_batch_is_grouped": (ctypes.c_int, [ctypes.c_void_p]),
+    "gwc_get_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options)]),
     "gwc_set_qp_cores": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "gwc_copy_out": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "gwc_cumulant_spectrum_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -199,6 +202,10 @@ class Batch:
     def launch(self, stream=None):
         _check(lib().gwc_batch_launch(self._b, _stream(stream)), None)
 
+    @property
+    def grouped(self) -> bool:
+        return bool(lib().gwc_batch_is_grouped(self._b))
+
     def close(self):
         if self._b:
             lib().gwc_batch_destroy(self._b)
@@ -220,7 +227,7 @@ class Context:
 
     def __init__(self, eps, n_occ, core_idx, o_ov, o_core, *, vxc=None, eps_f=math.nan, eta=1e-3, n_im=32, xi0=1.0,
                  prec="bf16x3", dec="diag", groups=None, n_t=1 << 16, t_max=2000.0, max_qp_iter=50, qp_tol=1e-7,
-                 batch=0, profile=False, qp_mode="secant", wait_us=0, stream=None):
+                 batch=0, profile=False, qp_mode="secant", wait_us=0, chi0_ctas=0, stream=None):
         self._ctx = ctypes.c_void_p()
         host = isinstance(eps, np.ndarray)
         self._keep = []
@@ -243,6 +250,7 @@ class Context:
         opt.profile = 1 if profile else 0
         opt.qp_mode = QP[qp_mode]
         opt.wait_us = int(wait_us)
+        opt.chi0_ctas = int(chi0_ctas)
         self.opt = opt
         self.prec = prec
         _check(lib().gwc_create(ctypes.byref(self._ctx), ctypes.byref(sysd), ctypes.byref(opt), _stream(stream)), None)
@@ -443,6 +451,12 @@ class Context:
         c = ctypes.c_int()
         _check(lib().gwc_autotune(self._ctx, _stream(stream), ctypes.byref(c)), self._ctx)
         return c.value
+
+    def chi0_ctas(self) -> int:
+        """The context's polarizability launch shape (gwc_options.chi0_ctas) after gwc_autotune."""
+        o = Options()
+        _check(lib().gwc_get_options(self._ctx, ctypes.byref(o)), self._ctx)
+        return o.chi0_ctas
 
     def sync(self, stream=None):
         _check(lib().gwc_sync(self._ctx, _stream(stream)), self._ctx)

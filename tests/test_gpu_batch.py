@@ -66,8 +66,13 @@ def test_request_secant_agrees_with_closed_form(gwc):
     assert int(it_s.min()) >= 2
 
 
-def test_batch_graph_equals_individual_steps(gwc):
-    """Each molecule's result is the same alone and inside the batched graph (uneven sizes)."""
+@pytest.mark.parametrize("grouped", [True, False])
+def test_batch_graph_equals_individual_steps(gwc, grouped, monkeypatch):
+    """Each molecule's result is the same alone and inside the batched graph (uneven sizes): the grouped
+    form (persistent grouped chi0 and grouped factorisation launches over all molecules) and the graph of
+    per-molecule steps (GWC_BATCH set)."""
+    if not grouped:
+        monkeypatch.setenv("GWC_BATCH", "per-molecule")
     mols = [synth.small(n_states=n, n_occ=max(2, n // 8), n_core=1 + (n % 2), n_aux=int(2.5 * n), seed=100 + n)
             for n in (24, 41, 57, 33)]
     alone = []
@@ -81,6 +86,7 @@ def test_batch_graph_equals_individual_steps(gwc):
         c.request_plan(_rel_grid())
         ctxs.append(c)
     batch = gwc.Batch(ctxs)
+    assert batch.grouped == grouped
     for rep in range(2):  # two launches of the same graph
         batch.launch()
         torch.cuda.synchronize()
@@ -103,9 +109,56 @@ def test_autotune_picks_a_valid_batch(gwc):
     ctx.request_plan(_rel_grid())
     chosen = ctx.autotune()
     assert chosen in (16, 32, 64, 128)
+    assert ctx.chi0_ctas() in (0, torch.cuda.get_device_properties(0).multi_processor_count)
     ctx.request_step()
     ctx.sync()
     # the second context of the same shape bucket reuses the cached choice
     ctx2 = gwc.Context.from_molecule(mol, prec="bf16x3", qp_mode="hedin", batch=128)
     ctx2.request_plan(_rel_grid())
     assert ctx2.autotune() == chosen
+
+
+def test_persistent_chi0_equals_one_cta_per_item(gwc):
+    """The polarizability build as a persistent launch (one CTA per SM looping over the tile items, running
+    barrier phases across items) gives the same matrices as one CTA per item, real and complex z."""
+    mol = synth.small(n_states=60, n_occ=9, n_core=2, n_aux=300, seed=53)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    z = torch.tensor([[0.0, 0.6], [0.0, 0.0], [0.41, 1e-3], [3.3, 1e-3], [0.0, 5.0]], dtype=torch.float64, device="cuda")
+    outs = []
+    for ctas in (0, n_sm, 7):  # 7 CTAs: many items per CTA
+        ctx = gwc.Context.from_molecule(mol, prec="bf16x3", chi0_ctas=ctas)
+        outs.append(ctx.build_chi0(z))
+        ctx.sync()
+        ctx.close()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_grouped_batch_with_many_chunks(gwc):
+    """Small workspaces (16 frequencies per batch) give each molecule several residue chunks, and the grouped
+    launches hold different numbers of molecules chunk by chunk; results as the molecules alone."""
+    mols = [synth.small(n_states=n, n_occ=max(2, n // 8), n_core=1 + (n % 3), n_aux=int(2.5 * n), seed=200 + n)
+            for n in (36, 52, 29)]
+    alone = []
+    for m in mols:
+        ctx, res = _request(gwc, m)
+        alone.append(res)
+        ctx.close()
+    ctxs = []
+    for m in mols:
+        c = gwc.Context.from_molecule(m, prec="bf16x3", qp_mode="hedin", batch=16)
+        c.request_plan(_rel_grid())
+        ctxs.append(c)
+    batch = gwc.Batch(ctxs)
+    assert batch.grouped
+    batch.launch()
+    torch.cuda.synchronize()
+    for c, ref in zip(ctxs, alone):
+        got = c.request_results()
+        torch.cuda.synchronize()
+        for g, r in zip(got, ref):
+            if g.dtype == torch.int32:
+                assert torch.equal(g, r)
+            else:
+                assert float((g - r).abs().max()) <= 1e-12 * max(1.0, float(r.abs().max()))
+        c.sync()
+    batch.close()

@@ -63,3 +63,24 @@ def test_pentacene_sigma_points_vs_oracle(gold, ctx):
         got = sig[:, 0, 0].cpu().numpy() + 1j * sig[:, 0, 1].cpu().numpy()
         ref = np.array([complex(a, b) for a, b in pt["sigma_c"]])
         assert np.all(np.abs(got - ref) <= 2e-2 * np.abs(ref) + 2e-3), np.max(np.abs(got - ref))
+
+
+def test_pentacene_decoupled_im_sigma_vs_oracle(gold, ctx):
+    """The decoupled Im Sigma the spectra start from (request mode, relative grid of 800 points over 30 eV),
+    cores 0, 11 and 21 at the stored grid points, within the bound the benzene-sized gates use."""
+    from test_gpu_benzene_gates import DEC_ABS
+
+    d = gold.get("dec_rel")
+    if not d or not d["values"]:
+        pytest.skip("no decoupled values in the oracle file")
+    mol, c = ctx
+    grid = np.linspace(-25.0 / EV, 5.0 / EV, 800)
+    c.request_plan(grid)
+    c.set_qp_cores([0])
+    c.request_step()
+    im = c.request_results()[3].cpu().numpy()
+    c.sync()
+    c.set_qp_cores(None)
+    for k, core in enumerate(d["cores"][: len(d["values"])]):
+        err = np.max(np.abs(im[core, d["nu_idx"]] - np.array(d["values"][k])))
+        assert err <= DEC_ABS, (core, err)
