@@ -1508,6 +1508,7 @@ struct GroupedLaunch {
   bool complex_z = false;
   std::vector<int> ctx_of;      // context of each chi0 group / factor group
   std::vector<int> p0, nb;      // pair range of each context in this launch
+  std::vector<int> half;        // first matrix of the workspace half each context's chunk uses
   size_t chi0_off = 0;          // byte offset of the chi0 descriptors in the batch's device buffer
   int chi0_groups = 0, chi0_items = 0;
   size_t fac_off = 0;           // byte offset of the factor descriptors (complex launches)
@@ -1531,12 +1532,8 @@ bool grouped_eligible(gwc_ctx* const* ctxs, int n) {
   return true;
 }
 
-// Residue chunks of one context: whole SM waves of its batch, as residue_batches_buf makes them.
-int chunk_of(const gwc_ctx* c) {
-  int chunk = std::max(1, c->batch);
-  if (chunk >= c->n_sm) chunk -= chunk % c->n_sm;
-  return chunk;
-}
+// Residue chunk of one context in the grouped form: half its workspace, so that two chunks are in flight.
+int grouped_chunk(const gwc_ctx* c) { return std::max(1, c->batch / 2); }
 
 // Appends the descriptors of one grouped launch: a chi0 group and (complex) a factor group per context
 // chunk. kind 0: table, 1: QP pairs, 2: spectrum pairs; k: chunk index.
@@ -1567,7 +1564,7 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, std::vector
       stride = (long long)c->n_aux * c->ldm;
     } else {
       const int np = kind == 1 ? c->n_core * c->n_occ : c->req_n_pairs;
-      const int chunk = chunk_of(c);
+      const int chunk = grouped_chunk(c);
       p0 = k * chunk;
       if (p0 >= np) continue;
       F = std::min(chunk, np - p0);
@@ -1575,15 +1572,19 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, std::vector
       stride = (long long)(c->n_aux + r) * c->ldm;
       if (kind == 1) act = c->d_qp_active + p0;
     }
+    // residue chunks alternate between the two halves of the workspace (the build of chunk k + 1 overlaps
+    // the factorisation of chunk k); the table uses the whole workspace
+    const int half = kind == 0 ? 0 : (k & 1) * grouped_chunk(c);
+    float* dtab = reinterpret_cast<float*>(c->d_dtab) + (size_t)half * 2 * c->ld_dtab;
+    float2* mats = static_cast<float2*>(c->d_mats) + (size_t)half * stride;
     const int got = chi0_group_fill(chi0.data() + (size_t)groups * gb, c->opt.prec != GWC_PREC_BF16, c->d_o_hi, c->d_o_lo,
-                                    c->d_o_f32, c->n_ov_pad, c->n_aux, c->n_aux_pad, c->n_ov_pad,
-                                    (const float*)c->d_dtab, c->ld_dtab, F, kind != 0, -1.0, 1.0, c->d_mats, c->ldm, stride,
-                                    act, false, items);
+                                    c->d_o_f32, c->n_ov_pad, c->n_aux, c->n_aux_pad, c->n_ov_pad, dtab, c->ld_dtab, F,
+                                    kind != 0, -1.0, 1.0, mats, c->ldm, stride, act, false, items);
     if (got < 0) return fail(nullptr, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for a batch member");
     items += got;
     if (kind != 0) {
       LdltGroup G;
-      G.mats = static_cast<float2*>(c->d_mats);
+      G.mats = mats;
       G.ldm = c->ldm;
       G.stride = stride;
       G.active = act;
@@ -1597,6 +1598,7 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, std::vector
     L.ctx_of.push_back(i);
     L.p0.push_back(p0);
     L.nb.push_back(F);
+    L.half.push_back(half);
     ++groups;
   }
   L.chi0_groups = groups;
@@ -1650,43 +1652,73 @@ gwc_status build_plan(gwc_ctx* const* ctxs, int n, GroupedPlan& P) {
     if ((call) < 0) return fail(nullptr, GWC_ERR_CUDA, std::string("batch launch failed: ") + #call);        \
   } while (0)
 
-// One grouped launch of residue builds: D tables of every member, one chi0 launch, the appended rows, one
-// factorisation launch, the contractions.
-gwc_status enqueue_grouped_residues(gwc_ctx* const* ctxs, const GroupedPlan& P, const GroupedLaunch& L, int kind,
-                                    cudaStream_t st) {
+// One grouped launch of residue builds, in two parts: (a) the D tables of every member and one chi0 launch,
+// (b) the appended rows, one factorisation launch and the contractions. Part (a) of the next chunk runs
+// on its own stream beside part (b) of this one (they use the two halves of each workspace).
+gwc_status enqueue_grouped_build(gwc_ctx* const* ctxs, const GroupedPlan& P, const GroupedLaunch& L, int kind,
+                                 cudaStream_t st) {
   const char* base = static_cast<const char*>(P.d_desc);
-  unsigned* status = ctxs[L.ctx_of[0]]->d_status;
-  unsigned long long wait_ns = ctxs[L.ctx_of[0]]->wait_ns;
   for (size_t j = 0; j < L.ctx_of.size(); ++j) {
     gwc_ctx* c = ctxs[L.ctx_of[j]];
     const double* z = (kind == 1 ? c->d_qp_z : c->d_req_z) + 2 * (size_t)L.p0[j];
-    BCU(launch_dtable(z, L.nb[j], c->d_delta, c->n_ov, c->ld_dtab, true, c->d_dtab, st));
+    float* dtab = reinterpret_cast<float*>(c->d_dtab) + (size_t)L.half[j] * 2 * c->ld_dtab;
+    BCU(launch_dtable(z, L.nb[j], c->d_delta, c->n_ov, c->ld_dtab, true, dtab, st));
   }
-  BCU(launch_chi0_tc_grouped(base + L.chi0_off, L.chi0_groups, L.chi0_items, true, P.chi0_ctas, status, wait_ns, st));
+  BCU(launch_chi0_tc_grouped(base + L.chi0_off, L.chi0_groups, L.chi0_items, true, P.chi0_ctas,
+                             ctxs[L.ctx_of[0]]->d_status, ctxs[L.ctx_of[0]]->wait_ns, st));
+  return GWC_OK;
+}
+
+gwc_status enqueue_grouped_factor(gwc_ctx* const* ctxs, const GroupedPlan& P, const GroupedLaunch& L, int kind,
+                                  cudaStream_t st) {
+  const char* base = static_cast<const char*>(P.d_desc);
   for (size_t j = 0; j < L.ctx_of.size(); ++j) {
     gwc_ctx* c = ctxs[L.ctx_of[j]];
     const int r = kind == 1 ? 1 : c->n_core;
     const long long stride = (long long)(c->n_aux + r) * c->ldm;
     const int* rows = (kind == 1 ? c->d_qp_rowmap : c->d_req_rows) + (size_t)L.p0[j] * r;
-    BCU(launch_border_rows(MatKind::CplxF32, c->d_mats, c->n_aux, c->ldm, stride, c->d_o_core, c->n_aux, rows, L.nb[j], r,
-                           c->d_bnorm, st));
+    float2* mats = static_cast<float2*>(c->d_mats) + (size_t)L.half[j] * stride;
+    BCU(launch_border_rows(MatKind::CplxF32, mats, c->n_aux, c->ldm, stride, c->d_o_core, c->n_aux, rows, L.nb[j], r,
+                           c->d_bnorm + (size_t)L.half[j] * r, st));
   }
-  BCU(launch_ldlt_tc_grouped(reinterpret_cast<const LdltGroup*>(base + L.fac_off), L.fac_groups, L.fac_ctas, status,
-                             wait_ns, st));
+  BCU(launch_ldlt_tc_grouped(reinterpret_cast<const LdltGroup*>(base + L.fac_off), L.fac_groups, L.fac_ctas,
+                             ctxs[L.ctx_of[0]]->d_status, ctxs[L.ctx_of[0]]->wait_ns, st));
   for (size_t j = 0; j < L.ctx_of.size(); ++j) {
     gwc_ctx* c = ctxs[L.ctx_of[j]];
     const int r = kind == 1 ? 1 : c->n_core;
     const long long stride = (long long)(c->n_aux + r) * c->ldm;
     double* w = (kind == 1 ? c->d_qp_w : c->d_req_w) + (size_t)L.p0[j] * r * 2;
     const int* act = kind == 1 ? c->d_qp_active + L.p0[j] : nullptr;
-    BCU(launch_border_w(MatKind::CplxF32, c->d_mats, c->n_aux, c->ldm, stride, L.nb[j], r, c->d_bnorm, w, (long long)r * 2,
-                        act, st));
+    float2* mats = static_cast<float2*>(c->d_mats) + (size_t)L.half[j] * stride;
+    BCU(launch_border_w(MatKind::CplxF32, mats, c->n_aux, c->ldm, stride, L.nb[j], r, c->d_bnorm + (size_t)L.half[j] * r,
+                        w, (long long)r * 2, act, st));
   }
   return GWC_OK;
 }
 
+// The chunks of one residue phase: builds on `st`, factorisations on `side`, two chunks in flight.
+gwc_status enqueue_grouped_phase(gwc_ctx* const* ctxs, const GroupedPlan& P, const std::vector<GroupedLaunch>& Ls,
+                                 int kind, cudaStream_t st, cudaStream_t side, const std::vector<cudaEvent_t>& ev) {
+  const size_t n = Ls.size();
+  if (n == 0) return GWC_OK;
+  if (ev.size() < 2 * n) return fail(nullptr, GWC_ERR_INVALID_ARG, "batch event pool too small");
+  const cudaEvent_t* ev_a = ev.data();      // build of chunk k done
+  const cudaEvent_t* ev_b = ev.data() + n;  // factorisation of chunk k done: its workspace half is free
+  for (size_t k = 0; k < n; ++k) {
+    if (k >= 2 && cudaStreamWaitEvent(st, ev_b[k - 2], 0) != cudaSuccess) return fail(nullptr, GWC_ERR_CUDA, "wait");
+    TRY(enqueue_grouped_build(ctxs, P, Ls[k], kind, st));
+    if (cudaEventRecord(ev_a[k], st) != cudaSuccess || cudaStreamWaitEvent(side, ev_a[k], 0) != cudaSuccess)
+      return fail(nullptr, GWC_ERR_CUDA, "batch event record failed");
+    TRY(enqueue_grouped_factor(ctxs, P, Ls[k], kind, side));
+    if (cudaEventRecord(ev_b[k], side) != cudaSuccess) return fail(nullptr, GWC_ERR_CUDA, "batch event record failed");
+  }
+  if (cudaStreamWaitEvent(st, ev_b[n - 1], 0) != cudaSuccess) return fail(nullptr, GWC_ERR_CUDA, "batch join failed");
+  return GWC_OK;
+}
+
 // The request step of every context as grouped launches, enqueued on `st` (capturable: no host sync).
-gwc_status enqueue_grouped_step(gwc_ctx* const* ctxs, int n, const GroupedPlan& P, cudaStream_t st) {
+gwc_status enqueue_grouped_step(gwc_ctx* const* ctxs, int n, const GroupedPlan& P, cudaStream_t st, cudaStream_t side,
+                                const std::vector<cudaEvent_t>& ev) {
   const char* base = static_cast<const char*>(P.d_desc);
   // imaginary-axis W tables: one grouped chi0 launch over all molecules' nodes (per chunk of nodes)
   for (const GroupedLaunch& L : P.table) {
@@ -1706,7 +1738,7 @@ gwc_status enqueue_grouped_step(gwc_ctx* const* ctxs, int n, const GroupedPlan& 
     BCU(launch_qp_pairs(c->d_eps, c->d_core_idx, c->n_core, c->n_occ, c->eps_f, c->opt.eta, c->d_qp, c->d_qp_z,
                         c->d_qp_active, c->d_qp_fac, c->d_all_done, c->d_active_builds, st));
   }
-  for (const GroupedLaunch& L : P.qp) TRY(enqueue_grouped_residues(ctxs, P, L, 1, st));
+  TRY(enqueue_grouped_phase(ctxs, P, P.qp, 1, st, side, ev));
   for (int i = 0; i < n; ++i) {
     gwc_ctx* c = ctxs[i];
     BCU(launch_qp_assemble_update(c->d_eps, c->n_states, c->n_occ, c->n_core, c->d_core_idx, c->eps_f, c->d_xi, c->d_wxi,
@@ -1715,7 +1747,7 @@ gwc_status enqueue_grouped_step(gwc_ctx* const* ctxs, int n, const GroupedPlan& 
     BCU(launch_qp_finish_hedin(c->d_qp, c->d_eps, c->d_core_idx, c->n_core, c->d_req_eqp, c->d_req_dh, c->d_req_it, st));
   }
   // decoupled Im Sigma on the relative grid and the spectra
-  for (const GroupedLaunch& L : P.spec) TRY(enqueue_grouped_residues(ctxs, P, L, 2, st));
+  TRY(enqueue_grouped_phase(ctxs, P, P.spec, 2, st, side, ev));
   for (int i = 0; i < n; ++i) {
     gwc_ctx* c = ctxs[i];
     BCU(launch_request_dec(c->d_eps, c->d_core_idx, c->n_core, c->eps_f, c->d_req_wrel, c->req_n_omega, c->d_req_pair_of,
@@ -1738,6 +1770,8 @@ struct gwc_batch {
   std::vector<gwc_ctx*> ctxs;
   bool grouped = false;
   GroupedPlan plan;
+  cudaStream_t side = nullptr;          // grouped form: the factorisation stream
+  std::vector<cudaEvent_t> gev;         // grouped form: events of the two-chunk pipeline
 };
 
 void gwc_batch_destroy(gwc_batch* b) {
@@ -1747,6 +1781,8 @@ void gwc_batch_destroy(gwc_batch* b) {
   for (auto e : b->events) cudaEventDestroy(e);
   for (auto s : b->streams) cudaStreamDestroy(s);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->side) cudaStreamDestroy(b->side);
+  for (auto e : b->gev) cudaEventDestroy(e);
   if (b->plan.d_desc) cudaFree(b->plan.d_desc);
   delete b;
 }
@@ -1787,8 +1823,16 @@ gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* 
       return bail(GWC_ERR_CUDA, std::string("grouped plan: ") + g_create_error);
     }
     b->plan.chi0_ctas = ctxs[0]->n_sm;  // persistent: one CTA per SM (the kernel's shared memory allows one)
+    const size_t n_ev = 2 * std::max(b->plan.qp.size(), b->plan.spec.size());
+    b->gev.resize(n_ev, nullptr);
+    bool ok_ev = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto& e : b->gev) ok_ev = ok_ev && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok_ev) {
+      restore();
+      return bail(GWC_ERR_CUDA, "batch stream/event creation failed");
+    }
     // one uncaptured run sets function attributes and first-use state
-    if (enqueue_grouped_step(ctxs, n, b->plan, st) != GWC_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+    if (enqueue_grouped_step(ctxs, n, b->plan, st, b->side, b->gev) != GWC_OK || cudaStreamSynchronize(st) != cudaSuccess) {
       restore();
       return bail(GWC_ERR_CUDA, std::string("grouped warm-up step failed: ") + g_create_error);
     }
@@ -1796,7 +1840,7 @@ gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* 
       res = GWC_ERR_CUDA;
       msg = "cudaStreamBeginCapture failed";
     } else {
-      if (enqueue_grouped_step(ctxs, n, b->plan, st) != GWC_OK) {
+      if (enqueue_grouped_step(ctxs, n, b->plan, st, b->side, b->gev) != GWC_OK) {
         res = GWC_ERR_CUDA;
         msg = std::string("capture of the grouped step failed: ") + g_create_error;
       }

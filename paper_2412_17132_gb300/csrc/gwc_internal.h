@@ -80,6 +80,18 @@ __host__ __device__ inline double sim(double) { return 0.0; }
 __host__ __device__ inline double sim(float2 a) { return a.y; }
 __host__ __device__ inline double sim(double2 a) { return a.y; }
 
+#ifdef __CUDACC__
+// Butterfly exchange within a warp (all 32 lanes take part) of a scalar of each kind.
+__device__ inline float shfl_xor_s(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ inline double shfl_xor_s(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ inline float2 shfl_xor_s(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+__device__ inline double2 shfl_xor_s(double2 v, int m) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+#endif
+
 // Device status bits (ORed into ctx->d_status[0]).
 enum : unsigned { kStatSingular = 1u, kStatNotConverged = 2u, kStatTimeout = 4u, kStatBadIndex = 8u };
 

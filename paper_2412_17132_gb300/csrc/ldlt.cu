@@ -52,11 +52,26 @@ __global__ void __launch_bounds__(256) ldlt_kernel(S* __restrict__ mats, int n, 
   if (threadIdx.x == 0 && sing) atomicOr(status, kStatSingular);
 }
 
-// Forward substitution with the W storage, for a block of RB right-hand sides (in place):
+// Forward substitution with the W storage, for a block of SR right-hand sides (in place):
 //   y_i = b_i - sum_{l<i} W_il u_l,  u_l = y_l / d_l   (since L_il = W_il / d_l)
 //   w_q = sum_i y_i^2 / d_i - |b_q|^2 = sum_i u_i^2 d_i - |b_q|^2.
-// The right-hand-side buffer ends up holding u. Grid: (matrix f, RHS block).
-constexpr int RB = 32;
+// The right-hand-side buffer ends up holding u. Grid: (matrix f, RHS block). Per 64-row panel:
+//   * update: acc = -W[panel rows][0 .. k0) U[0 .. k0)[block], a product in 32-deep chunks staged through
+//     shared memory, 4 x 4 outputs per thread (rows strided by 16 so that a warp reads distinct rows);
+//   * panel: the 64 x 64 diagonal block by four threads per right-hand side (strided partial sums of the
+//     row, two shuffles), u_i = (b_i + acc_i - sum_{l<i} W_il u_l) / d_i, u_i^2 d_i summed in FP64.
+constexpr int SB = 64;  // panel rows
+constexpr int SR = 64;  // right-hand sides per CTA
+constexpr int SK = 32;  // depth of the staged update chunks
+
+template <typename S>
+struct SolveSmem {
+  // update phase: ls[SB][SK + 1], us[SK][SR + 1]; panel phase: acc (then u) [SB][SR + 1], wd [SB][SB + 1], dv [SB]
+  static constexpr size_t upd = (size_t)SB * (SK + 1) + (size_t)SK * (SR + 1);
+  static constexpr size_t pan = (size_t)SB * (SR + 1) + (size_t)SB * (SB + 1) + SB;
+  static constexpr size_t elems = upd > pan ? upd : pan;
+  static size_t bytes() { return elems * sizeof(S); }
+};
 
 template <typename S>
 __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ mats, int n, long long ldm, long long stride,
@@ -65,100 +80,92 @@ __global__ void __launch_bounds__(256) ldlt_solve_kernel(const S* __restrict__ m
                                                           long long w_stride, const int* __restrict__ active) {
   const int f = blockIdx.x;
   if (active && !active[f]) return;
-  const int q0 = blockIdx.y * RB;
-  const int nq = min(RB, r - q0);
+  const int q0 = blockIdx.y * SR;
+  const int nq = min(SR, r - q0);
   const S* L = mats + f * stride;
   S* Y = rhs + f * rhs_stride + (long long)q0 * ldr;
   const int tid = threadIdx.x;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S(*ls)[NB + 1] = reinterpret_cast<S(*)[NB + 1]>(smem_raw);                             // W[k0+i][l0+l]
-  S(*ys)[RB + 1] = reinterpret_cast<S(*)[RB + 1]>(smem_raw + sizeof(S) * NB * (NB + 1));  // u[l0+l][q]
-  S(*accs)[RB + 1] = ys + NB;                                                              // panel partial sums
-  S* dv = reinterpret_cast<S*>(accs + NB);                                                 // d of the panel
+  S(*ls)[SK + 1] = reinterpret_cast<S(*)[SK + 1]>(smem_raw);
+  S(*us)[SR + 1] = reinterpret_cast<S(*)[SR + 1]>(smem_raw + sizeof(S) * SB * (SK + 1));
+  S(*acc_s)[SR + 1] = reinterpret_cast<S(*)[SR + 1]>(smem_raw);
+  S(*wd)[SB + 1] = reinterpret_cast<S(*)[SB + 1]>(smem_raw + sizeof(S) * SB * (SR + 1));
+  S* dv = reinterpret_cast<S*>(smem_raw + sizeof(S) * (SB * (SR + 1) + SB * (SB + 1)));
 
-  const int ii = tid & 31, qg = tid >> 5;  // row in panel, group of 4 rhs
-  for (int k0 = 0; k0 < n; k0 += NB) {
-    const int kb = min(NB, n - k0);
-    S acc[4];
+  const int tr = tid & 15, tc = tid >> 4;         // update: rows tr + 16 a, columns 4 tc + b
+  const int cq = tid >> 2, cp = tid & 3;           // panel: right-hand side cq, quarter cp of each row sum
+  double wr = 0.0, wi = 0.0;                       // sum u_i^2 d_i of right-hand side cq (kept by cp == 0)
+  for (int k0 = 0; k0 < n; k0 += SB) {
+    const int kb = min(SB, n - k0);
+    S acc[4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = szero<S>();
-    for (int l0 = 0; l0 < k0; l0 += NB) {
-      for (int e = tid; e < NB * NB; e += 256) {
-        const int i = e / NB, l = e % NB;
-        ls[i][l] = (i < kb) ? L[(long long)(k0 + i) * ldm + l0 + l] : szero<S>();
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = szero<S>();
+    for (int l0 = 0; l0 < k0; l0 += SK) {
+      for (int e = tid; e < SB * SK; e += 256) {
+        const int i = e / SK, l = e % SK;
+        ls[i][l] = i < kb ? L[(long long)(k0 + i) * ldm + l0 + l] : szero<S>();
       }
-      for (int e = tid; e < NB * RB; e += 256) {
-        const int q = e / NB, l = e % NB;
-        ys[l][q] = (q < nq) ? Y[(long long)q * ldr + l0 + l] : szero<S>();
+      for (int e = tid; e < SR * SK; e += 256) {
+        const int q = e / SK, l = e % SK;
+        us[l][q] = q < nq ? Y[(long long)q * ldr + l0 + l] : szero<S>();
       }
       __syncthreads();
-#pragma unroll 8
-      for (int l = 0; l < NB; ++l) {
-        const S a = ls[ii][l];
+#pragma unroll 4
+      for (int l = 0; l < SK; ++l) {
+        S av[4], bv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = sfnms(a, ys[l][qg * 4 + u], acc[u]);
+        for (int a = 0; a < 4; ++a) av[a] = ls[tr + 16 * a][l];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = us[l][4 * tc + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = sfnms(av[a], bv[b], acc[a][b]);
       }
       __syncthreads();
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) accs[ii][qg * 4 + u] = acc[u];
-    for (int e = tid; e < NB * NB; e += 256) {
-      const int i = e / NB, l = e % NB;
-      ls[i][l] = (i < kb && l < i) ? L[(long long)(k0 + i) * ldm + k0 + l] : szero<S>();
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc_s[tr + 16 * a][4 * tc + b] = acc[a][b];
+    for (int e = tid; e < SB * SB; e += 256) {
+      const int i = e / SB, l = e % SB;
+      wd[i][l] = (i < kb && l < i) ? L[(long long)(k0 + i) * ldm + k0 + l] : szero<S>();
     }
-    if (tid < NB) dv[tid] = tid < kb ? L[(long long)(k0 + tid) * ldm + k0 + tid] : sfrom<S>(1.0, 0.0);
+    if (tid < SB) dv[tid] = tid < kb ? L[(long long)(k0 + tid) * ldm + k0 + tid] : sfrom<S>(1.0, 0.0);
     __syncthreads();
-    if (tid < nq) {
-      const int q = tid;
-      S* y = Y + (long long)q * ldr + k0;
-      for (int i = 0; i < kb; ++i) {
-        S v = sadd(y[i], accs[i][q]);
-        for (int l = 0; l < i; ++l) v = sfnms(ls[i][l], ys[l][q], v);
+    // the panel's rows in order; the four threads of a right-hand side are consecutive lanes of one warp
+    for (int i = 0; i < kb; ++i) {
+      S part = szero<S>();
+      for (int l = cp; l < i; l += 4) part = sadd(part, smul(wd[i][l], acc_s[l][cq]));
+      part = sadd(part, shfl_xor_s(part, 1));
+      part = sadd(part, shfl_xor_s(part, 2));
+      if (cp == 0 && cq < nq) {
+        const S v = ssub(sadd(Y[(long long)cq * ldr + k0 + i], acc_s[i][cq]), part);
         const S u = smul(v, sinv(dv[i]));
-        ys[i][q] = u;
-        y[i] = u;
+        acc_s[i][cq] = u;
+        Y[(long long)cq * ldr + k0 + i] = u;
+        const S t = smul(smul(u, u), dv[i]);
+        wr += sre(t);
+        wi += sim(t);
       }
+      __syncwarp();
     }
     __syncthreads();
   }
-  // w_q = sum_i u_i^2 d_i - |b|^2  (FP64 accumulation)
-  __shared__ double red[2][8];
-  for (int q = 0; q < nq; ++q) {
-    double sr = 0.0, si = 0.0;
-    const S* u = Y + (long long)q * ldr;
-    for (int i = tid; i < n; i += 256) {
-      const S ui = u[i];
-      const S t = smul(smul(ui, ui), L[(long long)i * ldm + i]);
-      sr += sre(t);
-      si += sim(t);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_down_sync(0xffffffffu, sr, o);
-      si += __shfl_down_sync(0xffffffffu, si, o);
-    }
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = sr;
-      red[1][tid >> 5] = si;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 0.0;
-      for (int v = 0; v < 8; ++v) {
-        a += red[0][v];
-        b += red[1][v];
-      }
-      double* o = w + f * w_stride + (long long)(q0 + q) * 2;
-      o[0] = a - bnorm2[(long long)f * r + q0 + q];
-      o[1] = b;
-    }
-    __syncthreads();
+  if (cp == 0 && cq < nq) {
+    double* o = w + f * w_stride + (long long)(q0 + cq) * 2;
+    o[0] = wr - bnorm2[(long long)f * r + q0 + cq];
+    o[1] = wi;
   }
 }
 
 template <typename S>
 size_t solve_smem() {
-  return sizeof(S) * (NB * (NB + 1) + 2 * NB * (RB + 1) + NB);
+  return SolveSmem<S>::bytes();
 }
 
 template <typename S>
@@ -184,7 +191,7 @@ int run_solve(const S* mats, int n, long long ldm, long long stride, S* rhs, int
       return -1;
     attr = true;
   }
-  dim3 g(F, (r + RB - 1) / RB);
+  dim3 g(F, (r + SR - 1) / SR);
   ldlt_solve_kernel<S><<<g, 256, sm, s>>>(mats, n, ldm, stride, rhs, r, ldr, rhs_stride, bnorm2, w, w_stride, active);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
