@@ -255,6 +255,21 @@ gwc_status gwc_copy_out(gwc_ctx* ctx, void* dst, const void* src, size_t bytes, 
 gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
                               double* sigma_c, double* im_sigma_dec, void* stream);
 
+/* CD-WAC with a choice of which residues are continued:
+ *   GWC_WAC_ALL        : every residue W^c_mn(|eps_m - w| + i eta) from the continued fraction (gwc_sigma_core_wac);
+ *   GWC_WAC_EXACT_CORES: the residues of the core states m (core_idx) from their own dielectric builds, as in
+ *                        gwc_sigma_core (all cores' right-hand sides per build), the other occupied residues from
+ *                        the continued fraction through the imaginary nodes, i0 and the n_val_ref valence-region
+ *                        reference points (no core-region references). The decoupled Im Sigma is then exactly the
+ *                        contour-deformation value. Where the RPA excitations are dense on the scale of eta around
+ *                        |eps_c - w| (as in the synthetic molecules: poles ~1e-3 Ha apart above ~0.25 Ha), no
+ *                        interpolant through references 0.4 eV apart follows W_cc there; the valence residues
+ *                        (|eps_m - w| ~ 10 Ha) are continued to rounding accuracy.
+ * Other arguments and results as gwc_sigma_core_wac. */
+typedef enum { GWC_WAC_ALL = 0, GWC_WAC_EXACT_CORES = 1 } gwc_wac_mode;
+gwc_status gwc_sigma_core_cdwac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref, int mode,
+                                double* sigma_c, double* im_sigma_dec, void* stream);
+
 /* Graphical solutions of the plain G0W0 QP equation (eq quasiparticle_equation; Sec. "Satellites
  * in the G0W0 approximation": for 1s levels the equation has several solutions). On the ascending
  * grid omega, f(w) = eps_n + Sigma^x_n - v^xc_n + Re Sigma^c_n(w) - w; a grid point with f = 0 is a
@@ -379,7 +394,9 @@ typedef struct gwc_batch gwc_batch;
 gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* stream);
 gwc_status gwc_batch_launch(gwc_batch* batch, void* stream);
 void gwc_batch_destroy(gwc_batch* batch);
-/* 1 if the batch runs in the grouped form, 0 if it is the graph of per-molecule steps. */
+/* 0: the batch is the graph of per-molecule steps; 1: grouped form with one CTA per chi0 work item; 2: grouped
+ * form with the persistent chi0 launch (one CTA per SM looping over the items). gwc_batch_create times one
+ * run of each grouped shape and keeps the faster. */
 int gwc_batch_is_grouped(const gwc_batch* batch);
 
 /* The options the context runs with (as created, with what gwc_autotune chose). */

@@ -1179,6 +1179,13 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
 
 gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
                               double* sigma_c, double* im_sigma_dec, void* stream) {
+  return gwc_sigma_core_cdwac(ctx, omega, n_omega, n_core_ref, n_val_ref, GWC_WAC_ALL, sigma_c, im_sigma_dec, stream);
+}
+
+gwc_status gwc_sigma_core_cdwac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref, int mode,
+                                double* sigma_c, double* im_sigma_dec, void* stream) {
+  if (mode != GWC_WAC_ALL && mode != GWC_WAC_EXACT_CORES)
+    return fail(ctx, GWC_ERR_INVALID_ARG, "mode must be GWC_WAC_ALL or GWC_WAC_EXACT_CORES");
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
   if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   TRY(need_occupied_cores(ctx, "gwc_sigma_core_wac"));
@@ -1186,6 +1193,7 @@ gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, in
       n_core_ref + n_val_ref > 4096)
     return fail(ctx, GWC_ERR_INVALID_ARG, "need omega, sigma_c, 1 <= n_omega <= 2^20, reference counts in 0..4096");
   if (n_core_ref == 0 && n_val_ref == 0) n_core_ref = n_val_ref = 100;
+  if (mode == GWC_WAC_EXACT_CORES) n_core_ref = 0;  // the core-region references serve only the core residues
   cudaStream_t st = (cudaStream_t)stream;
   TRY(compute_wim(ctx, st));
   auto th = [](double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); };
@@ -1257,11 +1265,59 @@ gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, in
       cudaMemcpyAsync(d_om, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, st) != cudaSuccess)
     res = fail(ctx, GWC_ERR_CUDA, "CD-WAC upload failed");
   if (res == GWC_OK) res = residue_batches_buf(ctx, n_ref, d_zreal, d_rows, pairs, d_wref, nullptr, d_rhs, d_bn, chunk, st);
+  // GWC_WAC_EXACT_CORES: the residues of the core states m by their own dielectric builds (as gwc_sigma_core
+  // does), all n_core right-hand sides per build; the other residues by the continued fraction
+  std::vector<int> pidx, pm, crow;
+  std::vector<double> pw;
+  int n_cpairs = 0;
+  if (res == GWC_OK && mode == GWC_WAC_EXACT_CORES) {
+    const int ns = ctx->n_states, nc = ctx->n_core;
+    pidx.assign((size_t)n_omega * ns, -1);
+    for (int j = 0; j < n_omega; ++j)
+      for (int m : ctx->h_core) {
+        const double em = ctx->h_eps[m], w = omega[j];
+        const double f = -th(ctx->eps_f - em) * th(em - w) + th(em - ctx->eps_f) * th(w - em);
+        if (f == 0.0 || pidx[(size_t)j * ns + m] >= 0) continue;
+        pidx[(size_t)j * ns + m] = (int)pm.size();
+        pm.push_back(m);
+        pw.push_back(w);
+      }
+    n_cpairs = (int)pm.size();
+    for (int p = 0; p < n_cpairs; ++p)
+      for (int c = 0; c < nc; ++c) crow.push_back(pm[p] * nc + c);
+    if ((size_t)n_omega * ns > (size_t)ctx->pidx_cap) {
+      res = dalloc(ctx, &ctx->d_pidx, (size_t)n_omega * ns);
+      if (res == GWC_OK) ctx->pidx_cap = n_omega * ns;
+    }
+    if (res == GWC_OK && (size_t)std::max(1, n_cpairs) > (size_t)ctx->wres_cap) {
+      const size_t cap = std::max(1, n_cpairs);
+      if ((res = dalloc(ctx, &ctx->d_wres, cap * nc * 2)) == GWC_OK && (res = dalloc(ctx, &ctx->d_pair_m, cap)) == GWC_OK &&
+          (res = dalloc(ctx, &ctx->d_pair_w, cap)) == GWC_OK && (res = dalloc(ctx, &ctx->d_pair_z, cap * 2)) == GWC_OK &&
+          (res = dalloc(ctx, &ctx->d_pair_rows, cap * nc)) == GWC_OK)
+        ctx->wres_cap = (int)cap;
+    }
+    if (res == GWC_OK &&
+        (cudaMemcpyAsync(ctx->d_pidx, pidx.data(), sizeof(int) * pidx.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         (n_cpairs > 0 &&
+          (cudaMemcpyAsync(ctx->d_pair_m, pm.data(), sizeof(int) * n_cpairs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+           cudaMemcpyAsync(ctx->d_pair_w, pw.data(), sizeof(double) * n_cpairs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+           cudaMemcpyAsync(ctx->d_pair_rows, crow.data(), sizeof(int) * crow.size(), cudaMemcpyHostToDevice, st) !=
+               cudaSuccess))))
+      res = fail(ctx, GWC_ERR_CUDA, "CD-WAC core residue upload failed");
+    if (res == GWC_OK && n_cpairs > 0) {
+      if (launch_fill_z_pairs(ctx->d_eps, ctx->d_pair_m, ctx->d_pair_w, n_cpairs, ctx->opt.eta, ctx->d_pair_z, st) < 0)
+        res = fail(ctx, GWC_ERR_CUDA, "launch failed");
+      else
+        res = residue_batches(ctx, n_cpairs, ctx->d_pair_z, ctx->d_pair_rows, nc, ctx->d_wres, nullptr, st);
+    }
+  }
   if (res == GWC_OK) {
     int n1 = launch_thiele_fit(ctx->d_wim, ctx->n_states, ctx->n_core, n_im, d_wref, n_ref, pairs, d_zall, d_coef, st);
+    const bool exact = mode == GWC_WAC_EXACT_CORES;
     int n2 = launch_sigma_grid_wac(ctx->d_eps, ctx->n_states, ctx->n_occ, ctx->n_core, ctx->d_core_idx, d_om, n_omega,
                                    ctx->eps_f, ctx->opt.eta, ctx->d_xi, ctx->d_wxi, n_im, ctx->d_wim, d_coef, d_zall, n_pts,
-                                   sigma_c, im_sigma_dec, ctx->d_status, st);
+                                   exact ? ctx->d_pidx : nullptr, exact ? ctx->d_wres : nullptr, sigma_c, im_sigma_dec,
+                                   ctx->d_status, st);
     if (n1 < 0 || n2 < 0) res = fail(ctx, GWC_ERR_CUDA, "CD-WAC launch failed");
     ctx->stats.kernel_launches += std::max(0, n1) + std::max(0, n2);
   }
@@ -1787,7 +1843,7 @@ void gwc_batch_destroy(gwc_batch* b) {
   delete b;
 }
 
-int gwc_batch_is_grouped(const gwc_batch* b) { return b && b->grouped ? 1 : 0; }
+int gwc_batch_is_grouped(const gwc_batch* b) { return b && b->grouped ? (b->plan.chi0_ctas < (1 << 30) ? 2 : 1) : 0; }
 
 gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* stream) {
   // errors of this function go to gwc_last_error(NULL)
@@ -1822,7 +1878,6 @@ gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* 
       restore();
       return bail(GWC_ERR_CUDA, std::string("grouped plan: ") + g_create_error);
     }
-    b->plan.chi0_ctas = ctxs[0]->n_sm;  // persistent: one CTA per SM (the kernel's shared memory allows one)
     const size_t n_ev = 2 * std::max(b->plan.qp.size(), b->plan.spec.size());
     b->gev.resize(n_ev, nullptr);
     bool ok_ev = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess;
@@ -1831,10 +1886,39 @@ gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* 
       restore();
       return bail(GWC_ERR_CUDA, "batch stream/event creation failed");
     }
-    // one uncaptured run sets function attributes and first-use state
-    if (enqueue_grouped_step(ctxs, n, b->plan, st, b->side, b->gev) != GWC_OK || cudaStreamSynchronize(st) != cudaSuccess) {
-      restore();
-      return bail(GWC_ERR_CUDA, std::string("grouped warm-up step failed: ") + g_create_error);
+    // two uncaptured runs set function attributes and first-use state and choose the chi0 launch shape:
+    // the persistent grid (one CTA per SM, items dealt round-robin) or one CTA per item (the hardware
+    // hands out the items as SMs free up, which also fills SMs left idle beside the factorisations); the
+    // faster of the two timed runs is kept (the kernels' modules are loaded by then: every context ran
+    // them when its request plan was tuned or its table built)
+    {
+      cudaEvent_t t0 = nullptr, t1 = nullptr;
+      cudaEventCreate(&t0);
+      cudaEventCreate(&t1);
+      const int shapes[2] = {ctxs[0]->n_sm, 1 << 30};
+      float best_ms = 1e30f;
+      int best_shape = shapes[0];
+      bool ok = true;
+      for (int k = 0; k < 2 && ok; ++k) {
+        b->plan.chi0_ctas = shapes[k];
+        cudaEventRecord(t0, st);
+        ok = enqueue_grouped_step(ctxs, n, b->plan, st, b->side, b->gev) == GWC_OK;
+        cudaEventRecord(t1, st);
+        ok = ok && cudaEventSynchronize(t1) == cudaSuccess;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (ok && ms < best_ms) {
+          best_ms = ms;
+          best_shape = b->plan.chi0_ctas;
+        }
+      }
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      if (!ok) {
+        restore();
+        return bail(GWC_ERR_CUDA, std::string("grouped warm-up step failed: ") + g_create_error);
+      }
+      b->plan.chi0_ctas = best_shape;
     }
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
       res = GWC_ERR_CUDA;
