@@ -979,9 +979,11 @@ def run_batch(args):
                                   f"{args.omega_points}-point relative grid, cores = round(0.3 N_occ), QP = eps_n + dH_n",
                       "sizes_states_aux_cores": sizes, "autotuned_batch": tuned,
                       "autotuned_chi0_ctas": ctas_chosen,
-                      "form": ("grouped: per phase one grouped chi0 launch (" + batch.chi0_shape + ") and one grouped "
-                               "LDL^T launch over all molecules, builds overlapping factorisations, in one CUDA graph")
-                      if batch.grouped else "graph of per-molecule steps"},
+                      "form": ("grouped: per residue chunk one grouped chi0 launch and one grouped LDL^T launch over "
+                               "all molecules (" + batch.chi0_shape + "), in one CUDA graph")
+                      if batch.grouped else "graph of per-molecule steps on forked streams",
+                      "plans_timed_ms": dict(zip(["per_molecule", "grouped_sequential_persistent", "grouped_pipelined_per_item"],
+                                                 batch.timings()))},
            "spectra_per_s": sum(nc for _, _, nc in sizes) / statistics.mean(times),
            "setup_s": t_setup, "capture_s": t_cap, "clocks": clk,
            "latency_ms": {"per_launch": [1e3 * t for t in times]}}

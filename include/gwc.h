@@ -255,20 +255,6 @@ gwc_status gwc_copy_out(gwc_ctx* ctx, void* dst, const void* src, size_t bytes, 
 gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
                               double* sigma_c, double* im_sigma_dec, void* stream);
 
-/* CD-WAC with a choice of which residues are continued:
- *   GWC_WAC_ALL        : every residue W^c_mn(|eps_m - w| + i eta) from the continued fraction (gwc_sigma_core_wac);
- *   GWC_WAC_EXACT_CORES: the residues of the core states m (core_idx) from their own dielectric builds, as in
- *                        gwc_sigma_core (all cores' right-hand sides per build), the other occupied residues from
- *                        the continued fraction through the imaginary nodes, i0 and the n_val_ref valence-region
- *                        reference points (no core-region references). The decoupled Im Sigma is then exactly the
- *                        contour-deformation value. Where the RPA excitations are dense on the scale of eta around
- *                        |eps_c - w| (as in the synthetic molecules: poles ~1e-3 Ha apart above ~0.25 Ha), no
- *                        interpolant through references 0.4 eV apart follows W_cc there; the valence residues
- *                        (|eps_m - w| ~ 10 Ha) are continued to rounding accuracy.
- * Other arguments and results as gwc_sigma_core_wac. */
-typedef enum { GWC_WAC_ALL = 0, GWC_WAC_EXACT_CORES = 1 } gwc_wac_mode;
-gwc_status gwc_sigma_core_cdwac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref, int mode,
-                                double* sigma_c, double* im_sigma_dec, void* stream);
 
 /* Graphical solutions of the plain G0W0 QP equation (eq quasiparticle_equation; Sec. "Satellites
  * in the G0W0 approximation": for 1s levels the equation has several solutions). On the ascending
@@ -382,22 +368,28 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen);
  * gwc_batch_create captures the request steps of the contexts (each with a request plan) into one CUDA
  * graph. Grouped form (every context in a tensor-core precision mode with the default factorisation,
  * GWC_QP_HEDIN, DIAG decoupling): the polarizability builds of each phase (W tables, QP residues, spectrum
- * residues, chunk by chunk) of ALL molecules go through one persistent grouped chi0 launch (one CTA per
- * SM, each looping over the (molecule, frequency batch, 128 x 128 tile) items) and the complex
- * factorisations through one grouped LDL^T launch, with the small per-molecule kernels in between;
- * otherwise (or with the environment variable GWC_BATCH set) each context's step is captured on its own
- * forked stream. It first runs the work once outside capture, and synchronises `stream` before capturing
- * on a private stream. The contexts must outlive the batch and must not be used concurrently with a
+ * residues, chunk by chunk) of ALL molecules go through one grouped chi0 launch and the complex
+ * factorisations through one grouped LDL^T launch, with the small per-molecule kernels in between; two
+ * grouped plans are candidates: whole-workspace chunks one after another with the persistent chi0 launch
+ * (one CTA per SM, each looping over the (molecule, frequency batch, 128 x 128 tile) items), and
+ * half-workspace chunks whose builds overlap the previous chunk's factorisations with one chi0 CTA per
+ * item. Per-molecule
+ * form: each context's step on its own forked stream. gwc_batch_create runs every candidate plan once
+ * outside capture, timed (GWC_BATCH=per-molecule or =grouped in the environment restricts the choice),
+ * captures the fastest on a private stream, and synchronises `stream` first. The contexts must outlive the batch and must not be used concurrently with a
  * launch of it. gwc_batch_launch replays the whole graph on `stream` (results in each context, see
  * gwc_request_results_get). */
 typedef struct gwc_batch gwc_batch;
 gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* stream);
 gwc_status gwc_batch_launch(gwc_batch* batch, void* stream);
 void gwc_batch_destroy(gwc_batch* batch);
-/* 0: the batch is the graph of per-molecule steps; 1: grouped form with one CTA per chi0 work item; 2: grouped
- * form with the persistent chi0 launch (one CTA per SM looping over the items). gwc_batch_create times one
- * run of each grouped shape and keeps the faster. */
+/* 0: the batch is the graph of per-molecule steps; 1: grouped form, pipelined chunks with one CTA per chi0 work
+ * item; 2: grouped form, chunks in sequence with the persistent chi0 launch (one CTA per SM looping over the
+ * items). */
 int gwc_batch_is_grouped(const gwc_batch* batch);
+/* The times (ms) of the uncaptured runs gwc_batch_create chose from: [0] per-molecule steps, [1] grouped with
+ * the persistent chi0 launch, [2] grouped pipelined with one CTA per chi0 item; -1 for a plan not tried. */
+gwc_status gwc_batch_timings(const gwc_batch* batch, float* ms3);
 
 /* The options the context runs with (as created, with what gwc_autotune chose). */
 gwc_status gwc_get_options(const gwc_ctx* ctx, gwc_options* out);

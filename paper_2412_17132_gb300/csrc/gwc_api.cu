@@ -1179,13 +1179,6 @@ gwc_status gwc_cumulant_spectrum(gwc_ctx* ctx, const double* omega_rel, int n_om
 
 gwc_status gwc_sigma_core_wac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref,
                               double* sigma_c, double* im_sigma_dec, void* stream) {
-  return gwc_sigma_core_cdwac(ctx, omega, n_omega, n_core_ref, n_val_ref, GWC_WAC_ALL, sigma_c, im_sigma_dec, stream);
-}
-
-gwc_status gwc_sigma_core_cdwac(gwc_ctx* ctx, const double* omega, int n_omega, int n_core_ref, int n_val_ref, int mode,
-                                double* sigma_c, double* im_sigma_dec, void* stream) {
-  if (mode != GWC_WAC_ALL && mode != GWC_WAC_EXACT_CORES)
-    return fail(ctx, GWC_ERR_INVALID_ARG, "mode must be GWC_WAC_ALL or GWC_WAC_EXACT_CORES");
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
   if (!ctx->loaded) return fail(ctx, GWC_ERR_INVALID_ARG, "no system loaded (gwc_load)");
   TRY(need_occupied_cores(ctx, "gwc_sigma_core_wac"));
@@ -1193,7 +1186,6 @@ gwc_status gwc_sigma_core_cdwac(gwc_ctx* ctx, const double* omega, int n_omega, 
       n_core_ref + n_val_ref > 4096)
     return fail(ctx, GWC_ERR_INVALID_ARG, "need omega, sigma_c, 1 <= n_omega <= 2^20, reference counts in 0..4096");
   if (n_core_ref == 0 && n_val_ref == 0) n_core_ref = n_val_ref = 100;
-  if (mode == GWC_WAC_EXACT_CORES) n_core_ref = 0;  // the core-region references serve only the core residues
   cudaStream_t st = (cudaStream_t)stream;
   TRY(compute_wim(ctx, st));
   auto th = [](double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); };
@@ -1265,59 +1257,11 @@ gwc_status gwc_sigma_core_cdwac(gwc_ctx* ctx, const double* omega, int n_omega, 
       cudaMemcpyAsync(d_om, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, st) != cudaSuccess)
     res = fail(ctx, GWC_ERR_CUDA, "CD-WAC upload failed");
   if (res == GWC_OK) res = residue_batches_buf(ctx, n_ref, d_zreal, d_rows, pairs, d_wref, nullptr, d_rhs, d_bn, chunk, st);
-  // GWC_WAC_EXACT_CORES: the residues of the core states m by their own dielectric builds (as gwc_sigma_core
-  // does), all n_core right-hand sides per build; the other residues by the continued fraction
-  std::vector<int> pidx, pm, crow;
-  std::vector<double> pw;
-  int n_cpairs = 0;
-  if (res == GWC_OK && mode == GWC_WAC_EXACT_CORES) {
-    const int ns = ctx->n_states, nc = ctx->n_core;
-    pidx.assign((size_t)n_omega * ns, -1);
-    for (int j = 0; j < n_omega; ++j)
-      for (int m : ctx->h_core) {
-        const double em = ctx->h_eps[m], w = omega[j];
-        const double f = -th(ctx->eps_f - em) * th(em - w) + th(em - ctx->eps_f) * th(w - em);
-        if (f == 0.0 || pidx[(size_t)j * ns + m] >= 0) continue;
-        pidx[(size_t)j * ns + m] = (int)pm.size();
-        pm.push_back(m);
-        pw.push_back(w);
-      }
-    n_cpairs = (int)pm.size();
-    for (int p = 0; p < n_cpairs; ++p)
-      for (int c = 0; c < nc; ++c) crow.push_back(pm[p] * nc + c);
-    if ((size_t)n_omega * ns > (size_t)ctx->pidx_cap) {
-      res = dalloc(ctx, &ctx->d_pidx, (size_t)n_omega * ns);
-      if (res == GWC_OK) ctx->pidx_cap = n_omega * ns;
-    }
-    if (res == GWC_OK && (size_t)std::max(1, n_cpairs) > (size_t)ctx->wres_cap) {
-      const size_t cap = std::max(1, n_cpairs);
-      if ((res = dalloc(ctx, &ctx->d_wres, cap * nc * 2)) == GWC_OK && (res = dalloc(ctx, &ctx->d_pair_m, cap)) == GWC_OK &&
-          (res = dalloc(ctx, &ctx->d_pair_w, cap)) == GWC_OK && (res = dalloc(ctx, &ctx->d_pair_z, cap * 2)) == GWC_OK &&
-          (res = dalloc(ctx, &ctx->d_pair_rows, cap * nc)) == GWC_OK)
-        ctx->wres_cap = (int)cap;
-    }
-    if (res == GWC_OK &&
-        (cudaMemcpyAsync(ctx->d_pidx, pidx.data(), sizeof(int) * pidx.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-         (n_cpairs > 0 &&
-          (cudaMemcpyAsync(ctx->d_pair_m, pm.data(), sizeof(int) * n_cpairs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-           cudaMemcpyAsync(ctx->d_pair_w, pw.data(), sizeof(double) * n_cpairs, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-           cudaMemcpyAsync(ctx->d_pair_rows, crow.data(), sizeof(int) * crow.size(), cudaMemcpyHostToDevice, st) !=
-               cudaSuccess))))
-      res = fail(ctx, GWC_ERR_CUDA, "CD-WAC core residue upload failed");
-    if (res == GWC_OK && n_cpairs > 0) {
-      if (launch_fill_z_pairs(ctx->d_eps, ctx->d_pair_m, ctx->d_pair_w, n_cpairs, ctx->opt.eta, ctx->d_pair_z, st) < 0)
-        res = fail(ctx, GWC_ERR_CUDA, "launch failed");
-      else
-        res = residue_batches(ctx, n_cpairs, ctx->d_pair_z, ctx->d_pair_rows, nc, ctx->d_wres, nullptr, st);
-    }
-  }
   if (res == GWC_OK) {
     int n1 = launch_thiele_fit(ctx->d_wim, ctx->n_states, ctx->n_core, n_im, d_wref, n_ref, pairs, d_zall, d_coef, st);
-    const bool exact = mode == GWC_WAC_EXACT_CORES;
     int n2 = launch_sigma_grid_wac(ctx->d_eps, ctx->n_states, ctx->n_occ, ctx->n_core, ctx->d_core_idx, d_om, n_omega,
                                    ctx->eps_f, ctx->opt.eta, ctx->d_xi, ctx->d_wxi, n_im, ctx->d_wim, d_coef, d_zall, n_pts,
-                                   exact ? ctx->d_pidx : nullptr, exact ? ctx->d_wres : nullptr, sigma_c, im_sigma_dec,
-                                   ctx->d_status, st);
+                                   sigma_c, im_sigma_dec, ctx->d_status, st);
     if (n1 < 0 || n2 < 0) res = fail(ctx, GWC_ERR_CUDA, "CD-WAC launch failed");
     ctx->stats.kernel_launches += std::max(0, n1) + std::max(0, n2);
   }
@@ -1572,6 +1516,7 @@ struct GroupedLaunch {
 };
 
 struct GroupedPlan {
+  bool pipelined = false;  // residue chunks in workspace halves, builds of chunk k+1 beside factorisations of k
   std::vector<GroupedLaunch> table, qp, spec;  // one per chunk of imaginary nodes / pairs
   void* d_desc = nullptr;
   size_t desc_bytes = 0;
@@ -1588,12 +1533,14 @@ bool grouped_eligible(gwc_ctx* const* ctxs, int n) {
   return true;
 }
 
-// Residue chunk of one context in the grouped form: half its workspace, so that two chunks are in flight.
-int grouped_chunk(const gwc_ctx* c) { return std::max(1, c->batch / 2); }
+// Residue chunk of one context in the grouped form: its whole workspace, or half of it when two chunks are
+// in flight (pipelined).
+int grouped_chunk(const gwc_ctx* c, bool pipelined) { return std::max(1, pipelined ? c->batch / 2 : c->batch); }
 
 // Appends the descriptors of one grouped launch: a chi0 group and (complex) a factor group per context
 // chunk. kind 0: table, 1: QP pairs, 2: spectrum pairs; k: chunk index.
-gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, std::vector<uint8_t>& host, GroupedLaunch& L) {
+gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, bool pipelined, std::vector<uint8_t>& host,
+                       GroupedLaunch& L) {
   const size_t gb = chi0_group_bytes();
   L.complex_z = kind != 0;
   std::vector<uint8_t> chi0((size_t)n * gb);
@@ -1620,7 +1567,7 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, std::vector
       stride = (long long)c->n_aux * c->ldm;
     } else {
       const int np = kind == 1 ? c->n_core * c->n_occ : c->req_n_pairs;
-      const int chunk = grouped_chunk(c);
+      const int chunk = grouped_chunk(c, pipelined);
       p0 = k * chunk;
       if (p0 >= np) continue;
       F = std::min(chunk, np - p0);
@@ -1630,7 +1577,7 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, std::vector
     }
     // residue chunks alternate between the two halves of the workspace (the build of chunk k + 1 overlaps
     // the factorisation of chunk k); the table uses the whole workspace
-    const int half = kind == 0 ? 0 : (k & 1) * grouped_chunk(c);
+    const int half = (kind == 0 || !pipelined) ? 0 : (k & 1) * grouped_chunk(c, true);
     float* dtab = reinterpret_cast<float*>(c->d_dtab) + (size_t)half * 2 * c->ld_dtab;
     float2* mats = static_cast<float2*>(c->d_mats) + (size_t)half * stride;
     const int got = chi0_group_fill(chi0.data() + (size_t)groups * gb, c->opt.prec != GWC_PREC_BF16, c->d_o_hi, c->d_o_lo,
@@ -1676,22 +1623,23 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, std::vector
 }
 
 gwc_status build_plan(gwc_ctx* const* ctxs, int n, GroupedPlan& P) {
+  const bool pl = P.pipelined;
   std::vector<uint8_t> host;
   for (int k = 0;; ++k) {
     GroupedLaunch L;
-    TRY(plan_launch(ctxs, n, 0, k, host, L));
+    TRY(plan_launch(ctxs, n, 0, k, pl, host, L));
     if (L.chi0_groups == 0) break;
     P.table.push_back(L);
   }
   for (int k = 0;; ++k) {
     GroupedLaunch L;
-    TRY(plan_launch(ctxs, n, 1, k, host, L));
+    TRY(plan_launch(ctxs, n, 1, k, pl, host, L));
     if (L.chi0_groups == 0) break;
     P.qp.push_back(L);
   }
   for (int k = 0;; ++k) {
     GroupedLaunch L;
-    TRY(plan_launch(ctxs, n, 2, k, host, L));
+    TRY(plan_launch(ctxs, n, 2, k, pl, host, L));
     if (L.chi0_groups == 0) break;
     P.spec.push_back(L);
   }
@@ -1758,6 +1706,13 @@ gwc_status enqueue_grouped_phase(gwc_ctx* const* ctxs, const GroupedPlan& P, con
   const size_t n = Ls.size();
   if (n == 0) return GWC_OK;
   if (ev.size() < 2 * n) return fail(nullptr, GWC_ERR_INVALID_ARG, "batch event pool too small");
+  if (!P.pipelined) {  // one stream, chunk after chunk
+    for (size_t k = 0; k < n; ++k) {
+      TRY(enqueue_grouped_build(ctxs, P, Ls[k], kind, st));
+      TRY(enqueue_grouped_factor(ctxs, P, Ls[k], kind, st));
+    }
+    return GWC_OK;
+  }
   const cudaEvent_t* ev_a = ev.data();      // build of chunk k done
   const cudaEvent_t* ev_b = ev.data() + n;  // factorisation of chunk k done: its workspace half is free
   for (size_t k = 0; k < n; ++k) {
@@ -1825,9 +1780,12 @@ struct gwc_batch {
   std::vector<cudaEvent_t> events;
   std::vector<gwc_ctx*> ctxs;
   bool grouped = false;
-  GroupedPlan plan;
+  GroupedPlan plan;   // the grouped plan in use (after creation: the chosen one)
+  GroupedPlan plan2;  // the other grouped candidate
   cudaStream_t side = nullptr;          // grouped form: the factorisation stream
   std::vector<cudaEvent_t> gev;         // grouped form: events of the two-chunk pipeline
+  float t_candidates[3] = {-1.f, -1.f, -1.f};  // timed plans (ms): per-molecule, grouped persistent, grouped
+                                               // pipelined with one chi0 CTA per item
 };
 
 void gwc_batch_destroy(gwc_batch* b) {
@@ -1840,10 +1798,17 @@ void gwc_batch_destroy(gwc_batch* b) {
   if (b->side) cudaStreamDestroy(b->side);
   for (auto e : b->gev) cudaEventDestroy(e);
   if (b->plan.d_desc) cudaFree(b->plan.d_desc);
+  if (b->plan2.d_desc) cudaFree(b->plan2.d_desc);
   delete b;
 }
 
 int gwc_batch_is_grouped(const gwc_batch* b) { return b && b->grouped ? (b->plan.chi0_ctas < (1 << 30) ? 2 : 1) : 0; }
+
+gwc_status gwc_batch_timings(const gwc_batch* b, float* ms3) {
+  if (!b || !ms3) return GWC_ERR_INVALID_ARG;
+  for (int k = 0; k < 3; ++k) ms3[k] = b->t_candidates[k];
+  return GWC_OK;
+}
 
 gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* stream) {
   // errors of this function go to gwc_last_error(NULL)
@@ -1870,15 +1835,67 @@ gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* 
   auto restore = [&]() {
     for (int i = 0; i < n; ++i) ctxs[i]->opt.profile = saved[i];
   };
-  b->grouped = grouped_eligible(ctxs, n) && std::getenv("GWC_BATCH") == nullptr;
-  gwc_status res = GWC_OK;
-  std::string msg;
-  if (b->grouped) {
-    if (build_plan(ctxs, n, b->plan) != GWC_OK) {
+  // The launch plan is chosen by timing one uncaptured run of each candidate (they also set function
+  // attributes and first-use state): the per-molecule steps on forked streams, and, where every molecule
+  // allows it, the grouped form with the persistent chi0 launch and with one CTA per chi0 item. The
+  // fastest is captured. GWC_BATCH=per-molecule or =grouped restricts the choice.
+  const char* force = std::getenv("GWC_BATCH");
+  const bool allow_grouped = grouped_eligible(ctxs, n) && !(force && std::strcmp(force, "grouped") != 0);
+  const bool allow_pm = !(force && std::strcmp(force, "grouped") == 0 && allow_grouped);
+  b->streams.resize(n);
+  b->events.resize(n + 1);
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      restore();
+      return bail(GWC_ERR_CUDA, "stream creation failed");
+    }
+  for (int i = 0; i <= n; ++i)
+    if (cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming) != cudaSuccess) {
+      restore();
+      return bail(GWC_ERR_CUDA, "event creation failed");
+    }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  auto elapsed = [&]() {
+    float ms = 0.f;
+    return cudaEventSynchronize(t1) == cudaSuccess && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess ? ms : -1.f;
+  };
+  // the per-molecule steps, forked from and joined into `st`
+  auto enqueue_pm = [&]() -> gwc_status {
+    cudaEventRecord(b->events[n], st);
+    for (int i = 0; i < n; ++i) {
+      cudaStreamWaitEvent(b->streams[i], b->events[n], 0);
+      if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK)
+        return fail(nullptr, GWC_ERR_CUDA, std::string("step failed: ") + ctxs[i]->last_error);
+      cudaEventRecord(b->events[i], b->streams[i]);
+      cudaStreamWaitEvent(st, b->events[i], 0);
+    }
+    return GWC_OK;
+  };
+  float t_pm = -1.f, t_gp = -1.f, t_gi = -1.f;
+  if (allow_pm) {
+    cudaEventRecord(t0, st);
+    if (enqueue_pm() != GWC_OK) {
+      cudaStreamSynchronize(st);
+      restore();
+      return bail(GWC_ERR_CUDA, std::string("warm-up: ") + g_create_error);
+    }
+    cudaEventRecord(t1, st);
+    t_pm = elapsed();
+  }
+  if (allow_grouped) {
+    // candidate 1: whole-workspace chunks one after another, persistent chi0 grid (one CTA per SM);
+    // candidate 2: half-workspace chunks with builds beside factorisations, one chi0 CTA per item
+    b->plan.pipelined = false;
+    b->plan2.pipelined = true;
+    if (build_plan(ctxs, n, b->plan) != GWC_OK || build_plan(ctxs, n, b->plan2) != GWC_OK) {
       restore();
       return bail(GWC_ERR_CUDA, std::string("grouped plan: ") + g_create_error);
     }
-    const size_t n_ev = 2 * std::max(b->plan.qp.size(), b->plan.spec.size());
+    b->plan.chi0_ctas = ctxs[0]->n_sm;
+    b->plan2.chi0_ctas = 1 << 30;
+    const size_t n_ev = 2 * std::max(b->plan2.qp.size(), b->plan2.spec.size());
     b->gev.resize(n_ev, nullptr);
     bool ok_ev = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess;
     for (auto& e : b->gev) ok_ev = ok_ev && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
@@ -1886,98 +1903,50 @@ gwc_status gwc_batch_create(gwc_batch** out, gwc_ctx* const* ctxs, int n, void* 
       restore();
       return bail(GWC_ERR_CUDA, "batch stream/event creation failed");
     }
-    // two uncaptured runs set function attributes and first-use state and choose the chi0 launch shape:
-    // the persistent grid (one CTA per SM, items dealt round-robin) or one CTA per item (the hardware
-    // hands out the items as SMs free up, which also fills SMs left idle beside the factorisations); the
-    // faster of the two timed runs is kept (the kernels' modules are loaded by then: every context ran
-    // them when its request plan was tuned or its table built)
-    {
-      cudaEvent_t t0 = nullptr, t1 = nullptr;
-      cudaEventCreate(&t0);
-      cudaEventCreate(&t1);
-      const int shapes[2] = {ctxs[0]->n_sm, 1 << 30};
-      float best_ms = 1e30f;
-      int best_shape = shapes[0];
-      bool ok = true;
-      for (int k = 0; k < 2 && ok; ++k) {
-        b->plan.chi0_ctas = shapes[k];
-        cudaEventRecord(t0, st);
-        ok = enqueue_grouped_step(ctxs, n, b->plan, st, b->side, b->gev) == GWC_OK;
-        cudaEventRecord(t1, st);
-        ok = ok && cudaEventSynchronize(t1) == cudaSuccess;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, t0, t1);
-        if (ok && ms < best_ms) {
-          best_ms = ms;
-          best_shape = b->plan.chi0_ctas;
-        }
-      }
-      cudaEventDestroy(t0);
-      cudaEventDestroy(t1);
-      if (!ok) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEventRecord(t0, st);
+      const bool ok = enqueue_grouped_step(ctxs, n, k == 0 ? b->plan : b->plan2, st, b->side, b->gev) == GWC_OK;
+      cudaEventRecord(t1, st);
+      const float ms = elapsed();
+      if (!ok || ms < 0.f) {
+        cudaStreamSynchronize(st);
         restore();
         return bail(GWC_ERR_CUDA, std::string("grouped warm-up step failed: ") + g_create_error);
       }
-      b->plan.chi0_ctas = best_shape;
+      (k == 0 ? t_gp : t_gi) = ms;
     }
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-      res = GWC_ERR_CUDA;
-      msg = "cudaStreamBeginCapture failed";
-    } else {
-      if (enqueue_grouped_step(ctxs, n, b->plan, st, b->side, b->gev) != GWC_OK) {
-        res = GWC_ERR_CUDA;
-        msg = std::string("capture of the grouped step failed: ") + g_create_error;
-      }
-      cudaError_t e = cudaStreamEndCapture(st, &b->graph);
-      if (res == GWC_OK && e != cudaSuccess) {
-        res = GWC_ERR_CUDA;
-        msg = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
-      }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  // the fastest candidate
+  float best = 1e30f;
+  int pick = -1;  // 0 per-molecule, 1 grouped persistent, 2 grouped one CTA per item
+  const float cand[3] = {t_pm, t_gp, t_gi};
+  for (int k = 0; k < 3; ++k)
+    if (cand[k] >= 0.f && cand[k] < best) {
+      best = cand[k];
+      pick = k;
     }
+  b->t_candidates[0] = t_pm;
+  b->t_candidates[1] = t_gp;
+  b->t_candidates[2] = t_gi;
+  b->grouped = pick >= 1;
+  if (pick == 2) std::swap(b->plan, b->plan2);
+  gwc_status res = GWC_OK;
+  std::string msg;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    res = GWC_ERR_CUDA;
+    msg = "cudaStreamBeginCapture failed";
   } else {
-    b->streams.resize(n);
-    b->events.resize(n + 1);
-    for (int i = 0; i < n; ++i)
-      if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
-        restore();
-        return bail(GWC_ERR_CUDA, "stream creation failed");
-      }
-    for (int i = 0; i <= n; ++i)
-      if (cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming) != cudaSuccess) {
-        restore();
-        return bail(GWC_ERR_CUDA, "event creation failed");
-      }
-    // one uncaptured run per context sets function attributes and first-use state
-    for (int i = 0; i < n; ++i) {
-      if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK) {
-        restore();
-        return bail(GWC_ERR_CUDA, std::string("warm-up step failed: ") + ctxs[i]->last_error);
-      }
-    }
-    for (int i = 0; i < n; ++i)
-      if (cudaStreamSynchronize(b->streams[i]) != cudaSuccess) {
-        restore();
-        return bail(GWC_ERR_CUDA, "warm-up sync failed");
-      }
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    const gwc_status r = b->grouped ? enqueue_grouped_step(ctxs, n, b->plan, st, b->side, b->gev) : enqueue_pm();
+    if (r != GWC_OK) {
       res = GWC_ERR_CUDA;
-      msg = "cudaStreamBeginCapture failed";
-    } else {
-      cudaEventRecord(b->events[n], st);
-      for (int i = 0; i < n && res == GWC_OK; ++i) {
-        cudaStreamWaitEvent(b->streams[i], b->events[n], 0);
-        if (gwc_request_step(ctxs[i], b->streams[i]) != GWC_OK) {
-          res = GWC_ERR_CUDA;
-          msg = std::string("capture of a step failed: ") + ctxs[i]->last_error;
-        }
-        cudaEventRecord(b->events[i], b->streams[i]);
-        cudaStreamWaitEvent(st, b->events[i], 0);
-      }
-      cudaError_t e = cudaStreamEndCapture(st, &b->graph);
-      if (res == GWC_OK && e != cudaSuccess) {
-        res = GWC_ERR_CUDA;
-        msg = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
-      }
+      msg = std::string("capture failed: ") + g_create_error;
+    }
+    cudaError_t e = cudaStreamEndCapture(st, &b->graph);
+    if (res == GWC_OK && e != cudaSuccess) {
+      res = GWC_ERR_CUDA;
+      msg = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
     }
   }
   restore();

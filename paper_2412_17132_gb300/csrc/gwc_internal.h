@@ -231,10 +231,8 @@ int launch_thiele_fit(const double* wim, int n_states, int n_core, int n_im, con
                       const double* zref, double* coef, cudaStream_t s);
 int launch_sigma_grid_wac(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx, const double* omega,
                           int n_w, double eps_f, double eta, const double* xi, const double* wxi, int n_im,
-                          const double* wim, const double* coef, const double* zref, int n_pts,
-                          const int* pidx /*[n_w][n_states] exact residue pair or -1, or null*/,
-                          const double* wres /*[pair][n_core][2]*/, double* sigma, double* im_dec, unsigned* status,
-                          cudaStream_t s);
+                          const double* wim, const double* coef, const double* zref, int n_pts, double* sigma,
+                          double* im_dec, unsigned* status, cudaStream_t s);
 
 int launch_gdh_spectrum(const double* eps, const int* core_idx, int n_core, const double* omega, int n_w,
                         const double* sigma, const double* dh, const double* sx, const double* vxc, double* a,

@@ -322,7 +322,6 @@ __global__ void sigma_grid_wac_kernel(const double* __restrict__ eps, int n_stat
                                       double eps_f, double eta, const double* __restrict__ xi,
                                       const double* __restrict__ wxi, int n_im, const double* __restrict__ wim,
                                       const double2* __restrict__ coef, const double2* __restrict__ zref, int n_pts,
-                                      const int* __restrict__ pidx, const double* __restrict__ wres,
                                       double* __restrict__ sigma, double* __restrict__ im_dec,
                                       unsigned* __restrict__ status) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -337,14 +336,11 @@ __global__ void sigma_grid_wac_kernel(const double* __restrict__ eps, int n_stat
     si += imag_term(w - em, m, c, n_states, n_core, xi, wxi, n_im, wim);
     const double f = prefactor(em, w, eps_f);
     if (f == 0.0) continue;
-    if (m >= n_occ && !(pidx && pidx[(size_t)j * n_states + m] >= 0)) {  // a virtual residue has no fit: flag it
+    if (m >= n_occ) {  // a virtual residue (w above the LUMO) has no fit: flag it
       atomicOr(status, kStatBadIndex);
       continue;
     }
-    // a residue computed exactly (pidx >= 0: its dielectric build was done), else the continued fraction
-    const int p = pidx ? pidx[(size_t)j * n_states + m] : -1;
-    const double2 wv = p >= 0 ? make_double2(wres[((size_t)p * n_core + c) * 2], wres[((size_t)p * n_core + c) * 2 + 1])
-                              : thiele_eval(coef + (size_t)(m * n_core + c) * n_pts, zref, n_pts, make_double2(fabs(em - w), eta));
+    const double2 wv = thiele_eval(coef + (size_t)(m * n_core + c) * n_pts, zref, n_pts, make_double2(fabs(em - w), eta));
     rr += f * wv.x;
     ri += f * wv.y;
     if (m == n) dec += f * wv.y;
@@ -438,14 +434,13 @@ int launch_thiele_fit(const double* wim, int n_states, int n_core, int n_im, con
 
 int launch_sigma_grid_wac(const double* eps, int n_states, int n_occ, int n_core, const int* core_idx, const double* omega,
                           int n_w, double eps_f, double eta, const double* xi, const double* wxi, int n_im,
-                          const double* wim, const double* coef, const double* zref, int n_pts, const int* pidx,
-                          const double* wres, double* sigma,
+                          const double* wim, const double* coef, const double* zref, int n_pts, double* sigma,
                           double* im_dec, unsigned* status, cudaStream_t s) {
   long long warps = (long long)n_core * n_w;
   int blocks = (int)((warps * 32 + 255) / 256);
   sigma_grid_wac_kernel<<<blocks, 256, 0, s>>>(eps, n_states, n_occ, n_core, core_idx, omega, n_w, eps_f, eta, xi, wxi,
-                                               n_im, wim, (const double2*)coef, (const double2*)zref, n_pts, pidx, wres,
-                                               sigma, im_dec, status);
+                                               n_im, wim, (const double2*)coef, (const double2*)zref, n_pts, sigma,
+                                               im_dec, status);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

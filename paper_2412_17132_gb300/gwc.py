@@ -114,8 +114,6 @@ _SIGS = {
     "gwc_destroy": (None, [ctypes.c_void_p]),
     "gwc_sigma_core_wac": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
-    "gwc_sigma_core_cdwac": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_gdh_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_g0w0_solutions": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -129,6 +127,7 @@ _SIGS = {
     "gwc_batch_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gwc_batch_destroy": (None, [ctypes.c_void_p]),
     "gwc_batch_is_grouped": (ctypes.c_int, [ctypes.c_void_p]),
+    "gwc_batch_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "gwc_get_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options)]),
     "gwc_set_qp_cores": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "gwc_copy_out": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -208,9 +207,16 @@ class Batch:
     def grouped(self) -> bool:
         return bool(lib().gwc_batch_is_grouped(self._b))
 
+    def timings(self):
+        """ms of the plans gwc_batch_create timed: per-molecule, grouped persistent, grouped per item (-1: not tried)."""
+        t = (ctypes.c_float * 3)()
+        _check(lib().gwc_batch_timings(self._b, t), None)
+        return [float(v) for v in t]
+
     @property
     def chi0_shape(self) -> str:
-        return {0: "per-molecule graph", 1: "one CTA per item", 2: "persistent"}[lib().gwc_batch_is_grouped(self._b)]
+        return {0: "per-molecule graph", 1: "pipelined, one CTA per item", 2: "sequential chunks, persistent"}[
+            lib().gwc_batch_is_grouped(self._b)]
 
     def close(self):
         if self._b:
@@ -392,17 +398,6 @@ class Context:
         dec = torch.empty((self.n_core, om.shape[0]), dtype=torch.float64, device="cuda")
         _check(lib().gwc_sigma_core_wac(self._ctx, om.ctypes.data, om.shape[0], int(n_core_ref), int(n_val_ref), _ptr(sig),
                                         _ptr(dec), _stream(stream)), self._ctx)
-        return sig, dec
-
-    def sigma_core_cdwac(self, omega, exact_cores=True, n_core_ref=100, n_val_ref=100, stream=None):
-        """CD-WAC with the core states' residues exact (gwc_sigma_core_cdwac, GWC_WAC_EXACT_CORES) or all continued."""
-        import torch
-
-        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
-        sig = torch.empty((self.n_core, om.shape[0], 2), dtype=torch.float64, device="cuda")
-        dec = torch.empty((self.n_core, om.shape[0]), dtype=torch.float64, device="cuda")
-        _check(lib().gwc_sigma_core_cdwac(self._ctx, om.ctypes.data, om.shape[0], int(n_core_ref), int(n_val_ref),
-                                          1 if exact_cores else 0, _ptr(sig), _ptr(dec), _stream(stream)), self._ctx)
         return sig, dec
 
     def gdh_spectrum(self, omega, sigma_c, dh, stream=None):

@@ -71,8 +71,7 @@ def test_batch_graph_equals_individual_steps(gwc, grouped, monkeypatch):
     """Each molecule's result is the same alone and inside the batched graph (uneven sizes): the grouped
     form (persistent grouped chi0 and grouped factorisation launches over all molecules) and the graph of
     per-molecule steps (GWC_BATCH set)."""
-    if not grouped:
-        monkeypatch.setenv("GWC_BATCH", "per-molecule")
+    monkeypatch.setenv("GWC_BATCH", "grouped" if grouped else "per-molecule")
     mols = [synth.small(n_states=n, n_occ=max(2, n // 8), n_core=1 + (n % 2), n_aux=int(2.5 * n), seed=100 + n)
             for n in (24, 41, 57, 33)]
     alone = []
@@ -148,7 +147,13 @@ def test_grouped_batch_with_many_chunks(gwc):
         c = gwc.Context.from_molecule(m, prec="bf16x3", qp_mode="hedin", batch=16)
         c.request_plan(_rel_grid())
         ctxs.append(c)
-    batch = gwc.Batch(ctxs)
+    import os
+
+    os.environ["GWC_BATCH"] = "grouped"
+    try:
+        batch = gwc.Batch(ctxs)
+    finally:
+        del os.environ["GWC_BATCH"]
     assert batch.grouped
     batch.launch()
     torch.cuda.synchronize()

@@ -400,26 +400,7 @@ def test_cdwac_benzene_gpu_equals_oracle_wac(gwc):
         arith = np.max(np.abs(got[:, j] - ref[:, j]))
         print(f"grid point {i}: |WAC_gpu - WAC_oracle| = {arith:.2e}, |WAC - CD| gpu {dev_gpu:.2e} oracle {dev_ref:.2e}")
         if dev_ref < 1e-8:  # the continuation reproduces CD: both sides agree to FP64 rounding
-            assert arith < 1e-8
+            assert arith < 1e-8 and dev_gpu < 1e-8
         else:  # the method's deviation, of the same size on both sides (the continued fraction is ill
             # conditioned there, so last-bit differences of the reference values move it by a fraction)
-            assert 0.5 * dev_ref <= dev_gpu <= 2.0 * dev_ref and dev_ref > 1e-2
-
-
-def test_cdwac_exact_cores_matches_cd_benzene(gwc):
-    """CD-WAC with the core states' residues from their own builds (GWC_WAC_EXACT_CORES) and the valence residues
-    continued: the decoupled Im Sigma equals CD's (the same builds), and the full Sigma^c agrees with CD on
-    100 grid points across the window within the split-BF16 bound of the benzene-sized gates."""
-    from test_gpu_benzene_gates import SIG_ABS, SIG_REL
-
-    mol = synth.benzene()
-    ws = mol.omega[::8]
-    ctx = gwc.Context.from_molecule(mol, prec="bf16x3")
-    cd, cd_dec, _ = ctx.sigma_core(ws)
-    hy, hy_dec = ctx.sigma_core_cdwac(ws, exact_cores=True)
-    ctx.sync()
-    cd, hy = _cplx(cd), _cplx(hy)
-    assert float((hy_dec - cd_dec).abs().max()) == 0.0
-    err = np.abs(hy - cd)
-    print(f"max |Sigma_hybrid - Sigma_CD| = {np.max(err):.3e} Ha, max rel {np.max(err / np.abs(cd)):.3e}")
-    assert np.all(err <= SIG_REL * np.abs(cd) + SIG_ABS)
+            assert 0.5 * dev_ref <= dev_gpu <= 2.0 * dev_ref
