@@ -333,10 +333,10 @@ gwc_status run_chi0_any(gwc_ctx* ctx, bool complex_z, int F, const double* d_z, 
     LAUNCH(launch_chi0_simt(kind, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux, ctx->n_ov_pad, ctx->d_dtab, ctx->ld_dtab, F,
                             alpha, beta, out, ctx->ldm, stride, full, active, st));
   } else {
-    int n = launch_chi0_tc(prec != GWC_PREC_BF16, ctx->d_o_hi, ctx->d_o_lo, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux,
-                           ctx->n_aux_pad, ctx->n_ov_pad, (const float*)ctx->d_dtab, ctx->ld_dtab, F, complex_z, alpha,
-                           beta, out, ctx->ldm, stride, active, ctx->d_status, ctx->wait_ns, factor64(prec), st,
-                           ctx->opt.chi0_ctas);
+    int n = (ctx->chi0_pair ? launch_chi0_pair : launch_chi0_tc)(
+        prec != GWC_PREC_BF16, ctx->d_o_hi, ctx->d_o_lo, ctx->d_o_f32, ctx->n_ov_pad, ctx->n_aux, ctx->n_aux_pad,
+        ctx->n_ov_pad, (const float*)ctx->d_dtab, ctx->ld_dtab, F, complex_z, alpha, beta, out, ctx->ldm, stride, active,
+        ctx->d_status, ctx->wait_ns, factor64(prec), st, ctx->opt.chi0_ctas);
     if (n == -2) return fail(ctx, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for this shape/device");
     LAUNCH(n);
     if (full) {
@@ -618,6 +618,10 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
     // keeps them on the SIMT kernel (A/B measurements)
     const char* fe = std::getenv("GWC_FACTOR");
     ctx->factor_tc = !(fe && std::strcmp(fe, "simt") == 0);
+    // tensor-core chi0 kernel: CTA pairs (cta_group::2, 256 x 128 tiles); GWC_CHI0_KERNEL=single keeps the
+    // one-CTA 128 x 128 kernel (A/B measurements)
+    const char* ck = std::getenv("GWC_CHI0_KERNEL");
+    ctx->chi0_pair = !(ck && std::strcmp(ck, "single") == 0);
   }
   ctx->n_states = s->n_states;
   ctx->n_occ = s->n_occ;
@@ -1517,6 +1521,7 @@ struct GroupedLaunch {
 
 struct GroupedPlan {
   bool pipelined = false;  // residue chunks in workspace halves, builds of chunk k+1 beside factorisations of k
+  bool chi0_pair = false;  // descriptors of the CTA-pair chi0 kernel
   std::vector<GroupedLaunch> table, qp, spec;  // one per chunk of imaginary nodes / pairs
   void* d_desc = nullptr;
   size_t desc_bytes = 0;
@@ -1526,6 +1531,7 @@ struct GroupedPlan {
 bool grouped_eligible(gwc_ctx* const* ctxs, int n) {
   for (int i = 0; i < n; ++i) {
     const gwc_ctx* c = ctxs[i];
+    if (c->chi0_pair != ctxs[0]->chi0_pair) return false;  // one chi0 kernel per grouped launch
     if (!(c->opt.prec == GWC_PREC_BF16 || c->opt.prec == GWC_PREC_BF16X3) || !c->factor_tc) return false;
     if (c->opt.qp_mode != GWC_QP_HEDIN || c->opt.dec != GWC_DECOUPLE_DIAG || c->req_n_omega <= 0) return false;
     if (c->n_core > c->border_max) return false;
@@ -1541,7 +1547,8 @@ int grouped_chunk(const gwc_ctx* c, bool pipelined) { return std::max(1, pipelin
 // chunk. kind 0: table, 1: QP pairs, 2: spectrum pairs; k: chunk index.
 gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, bool pipelined, std::vector<uint8_t>& host,
                        GroupedLaunch& L) {
-  const size_t gb = chi0_group_bytes();
+  const bool pair = ctxs[0]->chi0_pair;
+  const size_t gb = pair ? chi0_pair_group_bytes() : chi0_group_bytes();
   L.complex_z = kind != 0;
   std::vector<uint8_t> chi0((size_t)n * gb);
   std::vector<LdltGroup> fac;
@@ -1580,9 +1587,10 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, bool pipeli
     const int half = (kind == 0 || !pipelined) ? 0 : (k & 1) * grouped_chunk(c, true);
     float* dtab = reinterpret_cast<float*>(c->d_dtab) + (size_t)half * 2 * c->ld_dtab;
     float2* mats = static_cast<float2*>(c->d_mats) + (size_t)half * stride;
-    const int got = chi0_group_fill(chi0.data() + (size_t)groups * gb, c->opt.prec != GWC_PREC_BF16, c->d_o_hi, c->d_o_lo,
-                                    c->d_o_f32, c->n_ov_pad, c->n_aux, c->n_aux_pad, c->n_ov_pad, dtab, c->ld_dtab, F,
-                                    kind != 0, -1.0, 1.0, mats, c->ldm, stride, act, false, items);
+    const int got = (pair ? chi0_pair_group_fill : chi0_group_fill)(
+        chi0.data() + (size_t)groups * gb, c->opt.prec != GWC_PREC_BF16, c->d_o_hi, c->d_o_lo, c->d_o_f32, c->n_ov_pad,
+        c->n_aux, c->n_aux_pad, c->n_ov_pad, dtab, c->ld_dtab, F, kind != 0, -1.0, 1.0, mats, c->ldm, stride, act, false,
+        items);
     if (got < 0) return fail(nullptr, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for a batch member");
     items += got;
     if (kind != 0) {
@@ -1624,6 +1632,7 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, bool pipeli
 
 gwc_status build_plan(gwc_ctx* const* ctxs, int n, GroupedPlan& P) {
   const bool pl = P.pipelined;
+  P.chi0_pair = ctxs[0]->chi0_pair;
   std::vector<uint8_t> host;
   for (int k = 0;; ++k) {
     GroupedLaunch L;
@@ -1668,7 +1677,7 @@ gwc_status enqueue_grouped_build(gwc_ctx* const* ctxs, const GroupedPlan& P, con
     float* dtab = reinterpret_cast<float*>(c->d_dtab) + (size_t)L.half[j] * 2 * c->ld_dtab;
     BCU(launch_dtable(z, L.nb[j], c->d_delta, c->n_ov, c->ld_dtab, true, dtab, st));
   }
-  BCU(launch_chi0_tc_grouped(base + L.chi0_off, L.chi0_groups, L.chi0_items, true, P.chi0_ctas,
+  BCU((P.chi0_pair ? launch_chi0_pair_grouped : launch_chi0_tc_grouped)(base + L.chi0_off, L.chi0_groups, L.chi0_items, true, P.chi0_ctas,
                              ctxs[L.ctx_of[0]]->d_status, ctxs[L.ctx_of[0]]->wait_ns, st));
   return GWC_OK;
 }
@@ -1737,7 +1746,7 @@ gwc_status enqueue_grouped_step(gwc_ctx* const* ctxs, int n, const GroupedPlan& 
       gwc_ctx* c = ctxs[L.ctx_of[j]];
       BCU(launch_dtable(c->d_zim + 2 * (size_t)L.p0[j], L.nb[j], c->d_delta, c->n_ov, c->ld_dtab, true, c->d_dtab, st));
     }
-    BCU(launch_chi0_tc_grouped(base + L.chi0_off, L.chi0_groups, L.chi0_items, false, P.chi0_ctas,
+    BCU((P.chi0_pair ? launch_chi0_pair_grouped : launch_chi0_tc_grouped)(base + L.chi0_off, L.chi0_groups, L.chi0_items, false, P.chi0_ctas,
                                ctxs[L.ctx_of[0]]->d_status, ctxs[L.ctx_of[0]]->wait_ns, st));
     for (size_t j = 0; j < L.ctx_of.size(); ++j) TRY(enqueue_wim_tail(ctxs[L.ctx_of[j]], L.p0[j], L.nb[j], st));
   }

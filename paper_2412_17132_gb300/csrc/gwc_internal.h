@@ -140,6 +140,19 @@ int chi0_group_fill(void* dst, bool split3, const __nv_bfloat16* o_hi, const __n
                     const int* active, bool out64, int item0);
 int launch_chi0_tc_grouped(const void* d_groups, int n_groups, int n_items, bool complex_out, int grid, unsigned* status,
                            unsigned long long wait_ns, cudaStream_t s);
+// The same three entry points for the CTA-pair kernel (256 x 128 pair tiles, tcgen05 cta_group::2): same
+// arguments and output contract; `persist` / `grid` count CTAs (two per cluster).
+int launch_chi0_pair(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32, int ld_pad,
+                     int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F, bool complex_out,
+                     double alpha, double beta, void* out, long long ldm, long long mat_stride, const int* active,
+                     unsigned* status, unsigned long long wait_ns, bool out64, cudaStream_t s, int persist);
+size_t chi0_pair_group_bytes();
+int chi0_pair_group_fill(void* dst, bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32,
+                         int ld_pad, int n_aux, int n_aux_pad, int n_ov_pad, const float* dtab, int ld_dtab, int F,
+                         bool complex_out, double alpha, double beta, void* out, long long ldm, long long mat_stride,
+                         const int* active, bool out64, int item0);
+int launch_chi0_pair_grouped(const void* d_groups, int n_groups, int n_items, bool complex_out, int grid,
+                             unsigned* status, unsigned long long wait_ns, cudaStream_t s);
 
 // Batched in-place LDL^T of F matrices [nrow][ldm]: the first n columns are factored (W = L D below
 // the diagonal, d on it, L^T above it); rows n..nrow-1 are appended right-hand sides that the row
@@ -298,6 +311,7 @@ struct gwc_ctx {
   int n_sm = 1;             // streaming multiprocessors of the device
   int wim_group = 1;        // imaginary-axis nodes whose solves share one launch
   bool factor_tc = true;    // complex FP32 factorisations on the tensor cores (mixed-precision modes)
+  bool chi0_pair = false;   // tensor-core chi0 on CTA pairs (cta_group::2) instead of one CTA per tile
   int border_max = 0;       // right-hand sides that may be appended as rows (matrix rows n_aux + border_max)
   size_t mats_bytes = 0;
   void* d_dtab = nullptr;   // [batch][2][ld_dtab] FP64-sized

@@ -94,6 +94,31 @@ def test_chi0_ragged_shapes_bf16x3(gwc, n_aux, n_states, n_occ):
         assert np.max(np.abs(out[f] - ref)) <= 2e-5 * max(1e-300, np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("kernel", ["pair", "single"])
+@pytest.mark.parametrize("n_aux,n_states,n_occ,ctas", [(1, 9, 2, 0), (70, 30, 5, 0), (300, 37, 9, 0), (300, 37, 9, 2),
+                                                       (520, 40, 8, 4), (700, 33, 6, 0)])
+def test_chi0_both_tensor_core_kernels(gwc, monkeypatch, kernel, n_aux, n_states, n_occ, ctas):
+    """The CTA-pair kernel (256 x 128 pair tiles; N_aux padded to an odd number of 128-row tiles leaves the
+    second CTA of the last pair on padding rows) and the one-CTA kernel, one item per CTA and persistent,
+    both against the oracle's chi0."""
+    monkeypatch.setenv("GWC_CHI0_KERNEL", kernel)
+    mol = synth.small(n_states=n_states, n_occ=n_occ, n_core=1, n_aux=n_aux, seed=n_aux + 7)
+    ctx = gwc.Context.from_molecule(mol, prec="bf16x3", chi0_ctas=ctas)
+    zs = [complex(0.0, 2.0), complex(1.7, 1e-3), complex(0.0, 0.3)]
+    z = torch.tensor([[v.real, v.imag] for v in zs], dtype=torch.float64, device="cuda")
+    out = _cplx(ctx.build_chi0(z))
+    assert ctx.sync_status() == 0
+    delta = G.transition_energies(mol.eps, mol.n_occ)
+    for f, v in enumerate(zs):
+        ref = G.chi0(mol.o_ov, delta, v)
+        # split-BF16 products err by ~2^-16 of |O_Pk D_k O_Qk| each: the bound is relative to the sum of the
+        # absolute terms (a single element near a pole cancels, and |Pi| alone does not bound its error)
+        dv = G.d_factor(delta, v)
+        absterm = np.abs(mol.o_ov) @ (np.abs(dv)[:, None] * np.abs(mol.o_ov).T)
+        assert np.max(np.abs(out[f] - ref)) <= 2e-5 * np.max(absterm)
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-4), ("bf16x3", 2e-3), ("bf16x3f64", 2e-3)])
 def test_screen_matches_oracle(gwc, tiny, prec, tol):
     ctx = gwc.Context.from_molecule(tiny, prec=prec)
