@@ -252,6 +252,21 @@ def load_traffic(kernel, workload, units_per_launch):
     return None
 
 
+def chi0_kernel_info(n_aux, n_ov):
+    """The tensor-core chi0 kernel the library runs (CTA pairs unless GWC_CHI0_KERNEL=single): its name, its
+    traffic key and the ratio of executed MMA work (whole 128 x 128 tiles of the padded lower triangle, the
+    pair kernel's 256 x 128 tiles) to the algorithmic N_aux (N_aux + 1) N_ov per part."""
+    n_aux_pad = -(-n_aux // 128) * 128
+    n_ov_pad = -(-n_ov // 64) * 64
+    nqb = n_aux_pad // 128
+    if os.environ.get("GWC_CHI0_KERNEL", "") == "single":
+        tiles, name = nqb * (nqb + 1) / 2, "chi0_tc_kernel"
+    else:
+        npb = -(-n_aux_pad // 256)
+        tiles, name = 2 * (npb * (npb - 1) + min(2 * npb, nqb)), "chi0_pair_kernel"
+    return name, tiles * 128 * 128 * 2 * n_ov_pad / (n_aux * (n_aux + 1.0) * n_ov)
+
+
 def job_throughput(local_ms, local_units, pg=None, device=None):
     """Whole-job aggregate over the ranks of a replica run: the slowest rank's time (max over ranks)
     and the units all ranks processed; value = units / slowest time (units/s). Each rank's units
@@ -372,19 +387,16 @@ def run_gpu(args):
         chi0_t = st["chi0_ms"] * 1e-3
         fac_t = st["factor_ms"] * 1e-3
         chi0_alg = st["chi0_flop"] / chi0_t if chi0_t > 0 else 0.0
-        # executed tensor-core work per algorithmic flop: full 128 x 128 lower-triangle tiles over the
-        # padded contraction (64-wide chunks), times the products per split (3 for bf16x3)
-        n_aux_pad = -(-mol.n_aux // 128) * 128
+        # executed tensor-core work per algorithmic flop: the kernel's whole tiles of the padded lower
+        # triangle over the padded contraction (64-wide chunks), times the products per split (3 for bf16x3)
         n_ov = mol.n_occ * mol.n_virt
-        n_ov_pad = -(-n_ov // 64) * 64
-        nt = n_aux_pad // 128
-        tile_ratio = (nt * (nt + 1) / 2 * 128 * 128 * 2 * n_ov_pad) / (mol.n_aux * (mol.n_aux + 1.0) * n_ov)
+        kname, tile_ratio = chi0_kernel_info(mol.n_aux, n_ov)
         mma_mult = {"bf16x3": 3.0, "bf16": 1.0}.get(args.prec, 0.0) * tile_ratio
         if chi0_t >= fac_t and args.prec in ("bf16x3", "bf16"):
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-            roof = {"kernel": "chi0_tc_kernel (tcgen05 " + args.prec + ")", "bound": "tensor", "achieved": chi0_alg / 1e12,
+            roof = {"kernel": kname + " (tcgen05 " + args.prec + ")", "bound": "tensor", "achieved": chi0_alg / 1e12,
                     "peak": peak, "unit": "TFLOP/s", "frac": chi0_alg / 1e12 / peak,
-                    "traffic": load_traffic("chi0_tc_kernel", mol.name, st["chi0_builds"] / max(1, st["chi0_launches"])),
+                    "traffic": load_traffic(kname, mol.name, st["chi0_builds"] / max(1, st["chi0_launches"])),
                     "mma_frac": mma_mult * chi0_alg / 1e12 / peak,
                     "peak_source": f"{src} bf16 sustained (kernel timed inside a long step)",
                     "share_of_step": chi0_t / (total_ms * 1e-3)}
@@ -716,17 +728,16 @@ def run_pentacene_headline(args):
         peaks, src = load_peaks()
         chi0_t, fac_t = st["chi0_ms"] * 1e-3, st["factor_ms"] * 1e-3
         chi0_alg = st["chi0_flop"] / chi0_t if chi0_t > 0 else 0.0
-        n_aux_pad = -(-mol.n_aux // 128) * 128
         n_ov = mol.n_occ * mol.n_virt
-        n_ov_pad = -(-n_ov // 64) * 64
-        ntl = n_aux_pad // 128
-        tile_ratio = (ntl * (ntl + 1) / 2 * 128 * 128 * 2 * n_ov_pad) / (mol.n_aux * (mol.n_aux + 1.0) * n_ov)
+        kname, tile_ratio = chi0_kernel_info(mol.n_aux, n_ov)
         mma_mult = {"bf16x3": 3.0, "bf16x3f64": 3.0, "bf16": 1.0}.get(args.prec, 0.0) * tile_ratio
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        roof = {"kernel": f"chi0_tc_kernel (tcgen05 {args.prec})", "bound": "tensor", "achieved": chi0_alg / 1e12,
+        per_launch = st["chi0_builds"] / max(1, st["chi0_launches"])
+        roof = {"kernel": f"{kname} (tcgen05 {args.prec})", "bound": "tensor", "achieved": chi0_alg / 1e12,
                 "peak": peak, "unit": "TFLOP/s", "frac": chi0_alg / 1e12 / peak,
-                "traffic": load_traffic("chi0_tc_kernel", "pentacene", 1.0),
-                "traffic_unit": "DRAM bytes per frequency (complex z) from the committed ncu capture",
+                "traffic": load_traffic(kname, "pentacene", per_launch),
+                "traffic_unit": f"DRAM bytes per launch ({per_launch:.1f} frequencies) from the committed ncu capture, "
+                                "scaled to N_ov = 89 571 and to the frequencies per launch",
                 "mma_frac": mma_mult * chi0_alg / 1e12 / peak,
                 "peak_source": f"{src} bf16 sustained (kernel timed inside a long step)",
                 "share_of_step": chi0_t / (total_ms * 1e-3),
