@@ -383,7 +383,9 @@ gwc_status run_chi0_stride(gwc_ctx* ctx, bool complex_z, int F, const double* d_
 // host synchronisation or allocation (the frequencies were uploaded at creation).
 // Imaginary-axis nodes per table batch (all n_im + 1 in one batch when the workspace holds them).
 int wim_batch(const gwc_ctx* ctx) {
-  const size_t per_real = (size_t)ctx->n_aux * ctx->ldm * mat_elem_bytes(real_kind(ctx));
+  // the tensor-core table builds and factors the real eps(i xi) in complex storage (zero imaginary parts)
+  const MatKind k = ctx->wtable_tc ? cplx_kind(ctx) : real_kind(ctx);
+  const size_t per_real = (size_t)ctx->n_aux * ctx->ldm * mat_elem_bytes(k);
   const int fb = (int)std::max<size_t>(1, std::min<size_t>(ctx->mats_bytes / per_real, (size_t)ctx->batch));
   return std::min(fb, ctx->opt.n_im + 1);
 }
@@ -395,7 +397,10 @@ gwc_status enqueue_wim(gwc_ctx* ctx, cudaStream_t st) {
   const int fb = wim_batch(ctx);
   for (int k0 = 0; k0 < nodes; k0 += fb) {
     const int nb = std::min(fb, nodes - k0);
-    TRY(run_chi0(ctx, false, nb, ctx->d_zim + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st));
+    // z = i xi: D is real, so a complex build gives Im Pi = 0 exactly (the tensor-core table's storage); only
+    // the real part is algorithmic work, so the second part is not charged to the flop count
+    TRY(run_chi0(ctx, ctx->wtable_tc, nb, ctx->d_zim + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st));
+    if (ctx->wtable_tc) ctx->stats.chi0_flop -= (double)nb * (double)ctx->n_aux * (ctx->n_aux + 1.0) * (double)ctx->n_ov;
     TRY(enqueue_wim_tail(ctx, k0, nb, st));
   }
   return GWC_OK;
@@ -408,11 +413,15 @@ gwc_status enqueue_wim_tail(gwc_ctx* ctx, int k0, int nb, cudaStream_t st) {
   const int r = ctx->n_states * ctx->n_core;
   const size_t plane = (size_t)ctx->n_states * ctx->n_core;
   const long long stride = (long long)ctx->n_aux * ctx->ldm;
+  const bool tc = ctx->wtable_tc && rk == MatKind::RealF32;
   {
     cudaEvent_t ev = ev_begin(ctx, st);
-    LAUNCH(launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st));
+    if (tc)  // complex storage with zero imaginary parts: the tensor-core LDL^T (they stay exactly zero)
+      LAUNCH(launch_factor(ctx, cplx_kind(ctx), ctx->d_mats, ctx->n_aux, ctx->n_aux, stride, nb, nullptr, st));
+    else
+      LAUNCH(launch_ldlt(rk, ctx->d_mats, ctx->n_aux, ctx->n_aux, ctx->ldm, stride, nb, nullptr, ctx->d_status, st));
     ev_end(ctx, kClsFactor, ev, st);
-    ctx->stats.factor_flop += factor_flop(ctx->n_aux, false, nb);
+    ctx->stats.factor_flop += factor_flop(ctx->n_aux, tc, nb);
     ctx->stats.factorizations += nb;
     // W^c for ng nodes per solve launch (one RHS buffer per node)
     const size_t ebytes = mat_elem_bytes(rk);
@@ -422,15 +431,27 @@ gwc_status enqueue_wim_tail(gwc_ctx* ctx, int k0, int nb, cudaStream_t st) {
         LAUNCH(launch_rhs_gather(rk, ctx->d_o_core, ctx->n_aux, ctx->d_rowmap, 1, r, ctx->n_aux,
                                  (char*)ctx->d_rhs_im + (size_t)u * plane * ctx->ldm * ebytes, ctx->ldm, 0,
                                  ctx->d_bnorm + (size_t)u * plane, st));
-      char* mat = (char*)ctx->d_mats + (size_t)u0 * stride * ebytes;
       cudaEvent_t evs = ev_begin(ctx, st);
-      LAUNCH(launch_ldlt_solve_w(rk, mat, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs_im, r, ctx->ldm,
-                                 (long long)plane * ctx->ldm, ctx->d_bnorm, ng, ctx->d_wtmp, (long long)plane * 2, nullptr,
-                                 st));
-      ev_end(ctx, kClsSolve, evs, st);
-      // real parts of w -> W table planes k0+u0 .. k0+u0+ng-1
-      CU(cudaMemcpy2DAsync(ctx->d_wim + (size_t)(k0 + u0) * plane, sizeof(double), ctx->d_wtmp, 2 * sizeof(double),
-                           sizeof(double), (size_t)ng * plane, cudaMemcpyDeviceToDevice, st));
+      if (tc) {
+        // blocked forward substitution on the tensor cores (real parts of the complex factors), straight into
+        // the table planes
+        const float* mat = (const float*)ctx->d_mats + (size_t)u0 * stride * 2;
+        const int n = launch_wtable_tc(mat, 2, ctx->n_aux, ctx->ldm, 2 * stride, (float*)ctx->d_rhs_im, ctx->ldm,
+                                       (long long)plane * ctx->ldm, r, ng, ctx->d_bnorm, ctx->d_wim + (size_t)(k0 + u0) * plane,
+                                       (long long)plane, ctx->d_wt, ctx->wt_bytes, ctx->d_status, ctx->wait_ns, st);
+        if (n == -2) return fail(ctx, GWC_ERR_UNSUPPORTED, "tensor-core W-table solve not available for this shape");
+        LAUNCH(n);
+        ev_end(ctx, kClsSolve, evs, st);
+      } else {
+        char* mat = (char*)ctx->d_mats + (size_t)u0 * stride * ebytes;
+        LAUNCH(launch_ldlt_solve_w(rk, mat, ctx->n_aux, ctx->ldm, stride, ctx->d_rhs_im, r, ctx->ldm,
+                                   (long long)plane * ctx->ldm, ctx->d_bnorm, ng, ctx->d_wtmp, (long long)plane * 2,
+                                   nullptr, st));
+        ev_end(ctx, kClsSolve, evs, st);
+        // real parts of w -> W table planes k0+u0 .. k0+u0+ng-1
+        CU(cudaMemcpy2DAsync(ctx->d_wim + (size_t)(k0 + u0) * plane, sizeof(double), ctx->d_wtmp, 2 * sizeof(double),
+                             sizeof(double), (size_t)ng * plane, cudaMemcpyDeviceToDevice, st));
+      }
     }
   }
   return GWC_OK;
@@ -719,6 +740,16 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
     char* ri = nullptr;
     CTRY(dalloc(ctx, &ri, (size_t)ctx->wim_group * per_node));
     ctx->d_rhs_im = ri;
+    // W-table solves on the tensor cores (mixed modes: real FP32 factors); GWC_WTABLE=simt keeps the SIMT
+    // forward substitution (A/B measurements)
+    const char* wt = std::getenv("GWC_WTABLE");
+    if ((o->prec == GWC_PREC_BF16X3 || o->prec == GWC_PREC_BF16) && !(wt && std::strcmp(wt, "simt") == 0)) {
+      ctx->wt_bytes = wtable_tc_bytes(s->n_aux, (int)plane, ctx->wim_group);
+      char* w = nullptr;
+      CTRY(dalloc(ctx, &w, ctx->wt_bytes));
+      ctx->d_wt = w;
+      ctx->wtable_tc = true;
+    }
   }
   const size_t wim_rows = (size_t)ctx->wim_group * plane;
   CTRY(dalloc(ctx, &ctx->d_z, 2 * (size_t)ctx->batch));
@@ -817,6 +848,7 @@ gwc_status reshape(gwc_ctx* ctx, const gwc_system* s) {
   ctx->batch = (int)b;
   ctx->border_max = border;
   ctx->wim_group = (int)wg;
+  ctx->wtable_tc = ctx->d_wt && wtable_tc_bytes(s->n_aux, (int)plane, (int)wg) <= ctx->wt_bytes;
   ctx->req_n_omega = 0;       // a request plan belongs to the previous system
   ctx->req_n_pairs = 0;
   ctx->qp_mask_set = false;   // so does a QP core selection
@@ -847,7 +879,7 @@ void gwc_destroy(gwc_ctx* ctx) {
                   ctx->d_req_pair_of, ctx->d_req_w, ctx->d_req_im, ctx->d_req_a, ctx->d_req_nu, ctx->d_req_eqp,
                   ctx->d_req_dh, ctx->d_req_it, ctx->d_eps_g, ctx->d_ev_sig, ctx->d_ev_diff, ctx->d_active_builds,
                   ctx->d_ev_pidx, ctx->d_ev_pm, ctx->d_ev_pw, ctx->d_ev_z, ctx->d_ev_rows, ctx->d_ev_wres, ctx->d_ev_w,
-                  ctx->d_qp_mask};
+                  ctx->d_qp_mask, ctx->d_wt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& r : ctx->ev_pending) {
@@ -1532,6 +1564,7 @@ bool grouped_eligible(gwc_ctx* const* ctxs, int n) {
   for (int i = 0; i < n; ++i) {
     const gwc_ctx* c = ctxs[i];
     if (c->chi0_pair != ctxs[0]->chi0_pair) return false;  // one chi0 kernel per grouped launch
+    if (c->wtable_tc != ctxs[0]->wtable_tc) return false;  // one storage of the table builds
     if (!(c->opt.prec == GWC_PREC_BF16 || c->opt.prec == GWC_PREC_BF16X3) || !c->factor_tc) return false;
     if (c->opt.qp_mode != GWC_QP_HEDIN || c->opt.dec != GWC_DECOUPLE_DIAG || c->req_n_omega <= 0) return false;
     if (c->n_core > c->border_max) return false;
@@ -1549,7 +1582,7 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, bool pipeli
                        GroupedLaunch& L) {
   const bool pair = ctxs[0]->chi0_pair;
   const size_t gb = pair ? chi0_pair_group_bytes() : chi0_group_bytes();
-  L.complex_z = kind != 0;
+  L.complex_z = kind != 0 || ctxs[0]->wtable_tc;  // the tensor-core table builds in complex storage
   std::vector<uint8_t> chi0((size_t)n * gb);
   std::vector<LdltGroup> fac;
   int items = 0, ctas = 0, groups = 0;
@@ -1589,7 +1622,7 @@ gwc_status plan_launch(gwc_ctx* const* ctxs, int n, int kind, int k, bool pipeli
     float2* mats = static_cast<float2*>(c->d_mats) + (size_t)half * stride;
     const int got = (pair ? chi0_pair_group_fill : chi0_group_fill)(
         chi0.data() + (size_t)groups * gb, c->opt.prec != GWC_PREC_BF16, c->d_o_hi, c->d_o_lo, c->d_o_f32, c->n_ov_pad,
-        c->n_aux, c->n_aux_pad, c->n_ov_pad, dtab, c->ld_dtab, F, kind != 0, -1.0, 1.0, mats, c->ldm, stride, act, false,
+        c->n_aux, c->n_aux_pad, c->n_ov_pad, dtab, c->ld_dtab, F, L.complex_z, -1.0, 1.0, mats, c->ldm, stride, act, false,
         items);
     if (got < 0) return fail(nullptr, GWC_ERR_UNSUPPORTED, "tensor-core chi0 not available for a batch member");
     items += got;
@@ -1746,7 +1779,7 @@ gwc_status enqueue_grouped_step(gwc_ctx* const* ctxs, int n, const GroupedPlan& 
       gwc_ctx* c = ctxs[L.ctx_of[j]];
       BCU(launch_dtable(c->d_zim + 2 * (size_t)L.p0[j], L.nb[j], c->d_delta, c->n_ov, c->ld_dtab, true, c->d_dtab, st));
     }
-    BCU((P.chi0_pair ? launch_chi0_pair_grouped : launch_chi0_tc_grouped)(base + L.chi0_off, L.chi0_groups, L.chi0_items, false, P.chi0_ctas,
+    BCU((P.chi0_pair ? launch_chi0_pair_grouped : launch_chi0_tc_grouped)(base + L.chi0_off, L.chi0_groups, L.chi0_items, L.complex_z, P.chi0_ctas,
                                ctxs[L.ctx_of[0]]->d_status, ctxs[L.ctx_of[0]]->wait_ns, st));
     for (size_t j = 0; j < L.ctx_of.size(); ++j) TRY(enqueue_wim_tail(ctxs[L.ctx_of[j]], L.p0[j], L.nb[j], st));
   }

@@ -140,6 +140,16 @@ int chi0_group_fill(void* dst, bool split3, const __nv_bfloat16* o_hi, const __n
                     const int* active, bool out64, int item0);
 int launch_chi0_tc_grouped(const void* d_groups, int n_groups, int n_items, bool complex_out, int grid, unsigned* status,
                            unsigned long long wait_ns, cudaStream_t s);
+// Imaginary-axis W table on the tensor cores: for ng factored real matrices (eps = L D L^T; element (P, Q) of node
+// u at mats[u m_node + (P ldm + Q) es] in floats, es = 2 for the real parts of complex FP32 storage) and their
+// right-hand sides ([node][r][ldc] FP32, rewritten), table[node][col] = sum_p y_p^2 / d_p - bnorm[node][col] with
+// y = L^-1 b (table node stride t_node = r). `work` holds wtable_tc_bytes(n, r, ng) bytes (16-byte aligned).
+// Returns the launches, -1 on a launch error, -2 if unsupported.
+size_t wtable_tc_bytes(int n_aux, int r, int ng);
+int launch_wtable_tc(const float* mats, int es, int n, long long ldm, long long m_node, float* rhs, long long ldc, long long c_node,
+                     int r, int ng, const double* bnorm, double* table, long long t_node, void* work, size_t work_bytes,
+                     unsigned* status, unsigned long long wait_ns, cudaStream_t s);
+
 // The same three entry points for the CTA-pair kernel (256 x 128 pair tiles, tcgen05 cta_group::2): same
 // arguments and output contract; `persist` / `grid` count CTAs (two per cluster).
 int launch_chi0_pair(bool split3, const __nv_bfloat16* o_hi, const __nv_bfloat16* o_lo, const float* o_f32, int ld_pad,
@@ -312,6 +322,9 @@ struct gwc_ctx {
   int wim_group = 1;        // imaginary-axis nodes whose solves share one launch
   bool factor_tc = true;    // complex FP32 factorisations on the tensor cores (mixed-precision modes)
   bool chi0_pair = false;   // tensor-core chi0 on CTA pairs (cta_group::2) instead of one CTA per tile
+  bool wtable_tc = false;   // imaginary-axis W-table solves on the tensor cores (else the SIMT forward substitution)
+  void* d_wt = nullptr;     // their workspace (TF32 planes), wt_bytes bytes
+  size_t wt_bytes = 0;
   int border_max = 0;       // right-hand sides that may be appended as rows (matrix rows n_aux + border_max)
   size_t mats_bytes = 0;
   void* d_dtab = nullptr;   // [batch][2][ld_dtab] FP64-sized

@@ -154,6 +154,31 @@ def test_sigma_grid_tiny_full(gwc, tiny, tiny_oracle, prec):
     assert abs(float(sx[0]) - tiny_oracle.sigma_x()[0]) < 1e-10 * abs(tiny_oracle.sigma_x()[0])
 
 
+@pytest.mark.parametrize("n_states,n_occ,n_core,n_aux", [(30, 5, 1, 70), (41, 6, 2, 300), (60, 8, 3, 520)])
+def test_wtable_tensor_core_solve(gwc, monkeypatch, n_states, n_occ, n_core, n_aux):
+    """The imaginary-axis W table by the blocked tensor-core forward substitution (3xTF32 GEMMs over 128-row
+    blocks; N_aux with a ragged last block, right-hand sides R = N_states N_core not a multiple of the 256-wide
+    tiles) against the SIMT forward substitution of the same FP32 factors (FP32-level agreement in Sigma^c),
+    and both against the oracle within the bf16x3 tolerance."""
+    mol = synth.small(n_states=n_states, n_occ=n_occ, n_core=n_core, n_aux=n_aux, seed=n_aux + 11)
+    omega = np.linspace(mol.eps[0] - 1.0, mol.eps[0] + 0.5, 9)
+    out = {}
+    for mode in ("tc", "simt"):
+        if mode == "simt":
+            monkeypatch.setenv("GWC_WTABLE", "simt")
+        else:
+            monkeypatch.delenv("GWC_WTABLE", raising=False)
+        ctx = gwc.Context.from_molecule(mol, prec="bf16x3")
+        sig, _, _ = ctx.sigma_core(omega, want_dec=False)
+        assert ctx.sync_status() == 0
+        out[mode] = _cplx(sig)
+        ctx.close()
+    ref, _ = G.System.from_molecule(mol).sigma_c_grid(omega)
+    rel, ab = SIG_TOL["bf16x3"]
+    assert np.max(np.abs(out["tc"] - out["simt"])) <= 2e-6 * np.max(np.abs(out["simt"])) + 1e-7
+    assert np.all(np.abs(out["tc"] - ref) <= rel * np.abs(ref) + ab)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x3f64"])
 def test_gates_tiny_reduced_precision(gwc, tiny, tiny_oracle, prec):
     """The accuracy gates: QP |dE| <= 1e-3 eV, A(w) max-abs <= 1e-3 of the peak, satellite
