@@ -410,11 +410,14 @@ def run_gpu(args):
                 # trailing updates on the tensor cores in 3xTF32: three TF32 products per FP32-accurate one
                 tf32 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")) * 1.1 / 2.25
                 peak = tf32 / 3.0
-                roof = {"kernel": "ldlt_tc_kernel (batched complex-symmetric LDL^T, FP32: tcgen05 3xTF32 trailing "
-                                  "updates + SIMT panels)",
+                split = os.environ.get("GWC_FACTOR", "") != "tc"
+                roof = {"kernel": ("ldlt_update_kernel + ldlt_panel_kernel (complex-symmetric LDL^T per 64-column "
+                                   "panel over the batch: tcgen05 3xTF32 updates + SIMT panels)") if split else
+                                  ("ldlt_tc_kernel (batched complex-symmetric LDL^T, FP32: tcgen05 3xTF32 trailing "
+                                   "updates + SIMT panels)"),
                         "bound": "tensor", "achieved": fac_alg / 1e12, "peak": peak, "unit": "TFLOP/s",
                         "frac": fac_alg / 1e12 / peak, "alu_frac": fac_alg / 1e12 / fp32_peak,
-                        "traffic": load_traffic("ldlt_tc_kernel", mol.name, units),
+                        "traffic": None if split else load_traffic("ldlt_tc_kernel", mol.name, units),
                         "peak_source": f"{src} bf16 sustained x 1.1/2.25 (nominal TF32/BF16 dense) / 3 (3xTF32)",
                         "share_of_step": fac_t / (total_ms * 1e-3)}
             else:

@@ -357,6 +357,11 @@ int launch_factor(gwc_ctx* ctx, MatKind kind, void* mats, int n, int nrow, long 
                   cudaStream_t st) {
   const bool mixed = ctx->opt.prec == GWC_PREC_BF16 || ctx->opt.prec == GWC_PREC_BF16X3;
   if (kind == MatKind::CplxF32 && mixed && ctx->factor_tc) {
+    if (ctx->factor_split && ldlt_split_bytes(n, nrow, F) <= ctx->lp_bytes) {
+      const int r = launch_ldlt_split(mats, n, nrow, ctx->ldm, stride, F, act, ctx->d_status, ctx->wait_ns, ctx->d_lp,
+                                      ctx->lp_bytes, st);
+      if (r != -2) return r;
+    }
     const int r = launch_ldlt_tc(mats, n, nrow, ctx->ldm, stride, F, act, ctx->d_status, ctx->wait_ns, st);
     if (r != -2) return r;
   }
@@ -635,10 +640,12 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess || ctx->n_sm < 1)
     ctx->n_sm = 1;
   {
-    // complex factorisations of the mixed modes run on the tensor-core kernel; GWC_FACTOR=simt
-    // keeps them on the SIMT kernel (A/B measurements)
+    // complex factorisations of the mixed modes run on the tensor cores, as panel launches + batched updates
+    // (split); GWC_FACTOR=tc keeps the one-CTA-per-matrix tensor-core kernel, =simt the SIMT kernel (A/B
+    // measurements)
     const char* fe = std::getenv("GWC_FACTOR");
     ctx->factor_tc = !(fe && std::strcmp(fe, "simt") == 0);
+    ctx->factor_split = ctx->factor_tc && !(fe && std::strcmp(fe, "tc") == 0);
     // tensor-core chi0 kernel: CTA pairs (cta_group::2, 256 x 128 tiles); GWC_CHI0_KERNEL=single keeps the
     // one-CTA 128 x 128 kernel (A/B measurements)
     const char* ck = std::getenv("GWC_CHI0_KERNEL");
@@ -743,6 +750,12 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
     // W-table solves on the tensor cores (mixed modes: real FP32 factors); GWC_WTABLE=simt keeps the SIMT
     // forward substitution (A/B measurements)
     const char* wt = std::getenv("GWC_WTABLE");
+    if ((o->prec == GWC_PREC_BF16X3 || o->prec == GWC_PREC_BF16) && ctx->factor_split) {
+      ctx->lp_bytes = ldlt_split_bytes(s->n_aux, s->n_aux + ctx->border_max, ctx->batch);
+      char* lp = nullptr;
+      CTRY(dalloc(ctx, &lp, ctx->lp_bytes));
+      ctx->d_lp = lp;
+    }
     if ((o->prec == GWC_PREC_BF16X3 || o->prec == GWC_PREC_BF16) && !(wt && std::strcmp(wt, "simt") == 0)) {
       ctx->wt_bytes = wtable_tc_bytes(s->n_aux, (int)plane, ctx->wim_group);
       char* w = nullptr;
@@ -879,7 +892,7 @@ void gwc_destroy(gwc_ctx* ctx) {
                   ctx->d_req_pair_of, ctx->d_req_w, ctx->d_req_im, ctx->d_req_a, ctx->d_req_nu, ctx->d_req_eqp,
                   ctx->d_req_dh, ctx->d_req_it, ctx->d_eps_g, ctx->d_ev_sig, ctx->d_ev_diff, ctx->d_active_builds,
                   ctx->d_ev_pidx, ctx->d_ev_pm, ctx->d_ev_pw, ctx->d_ev_z, ctx->d_ev_rows, ctx->d_ev_wres, ctx->d_ev_w,
-                  ctx->d_qp_mask, ctx->d_wt};
+                  ctx->d_qp_mask, ctx->d_wt, ctx->d_lp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& r : ctx->ev_pending) {

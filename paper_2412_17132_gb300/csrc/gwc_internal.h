@@ -140,6 +140,14 @@ int chi0_group_fill(void* dst, bool split3, const __nv_bfloat16* o_hi, const __n
                     const int* active, bool out64, int item0);
 int launch_chi0_tc_grouped(const void* d_groups, int n_groups, int n_items, bool complex_out, int grid, unsigned* status,
                            unsigned long long wait_ns, cudaStream_t s);
+// Split factorisation of F complex FP32 matrices (same layout and result as launch_ldlt_tc): per 64-column
+// panel one panel launch (one CTA per matrix) and one batched tensor-core trailing update over all matrices.
+// `work` holds ldlt_split_bytes(n, nrow, F) bytes. Returns the launches, -1 on a launch error or bad layout,
+// -2 if unsupported.
+size_t ldlt_split_bytes(int n, int nrow, int F);
+int launch_ldlt_split(void* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active,
+                      unsigned* status, unsigned long long wait_ns, void* work, size_t work_bytes, cudaStream_t s);
+
 // Imaginary-axis W table on the tensor cores: for ng factored real matrices (eps = L D L^T; element (P, Q) of node
 // u at mats[u m_node + (P ldm + Q) es] in floats, es = 2 for the real parts of complex FP32 storage) and their
 // right-hand sides ([node][r][ldc] FP32, rewritten), table[node][col] = sum_p y_p^2 / d_p - bnorm[node][col] with
@@ -323,6 +331,9 @@ struct gwc_ctx {
   bool factor_tc = true;    // complex FP32 factorisations on the tensor cores (mixed-precision modes)
   bool chi0_pair = false;   // tensor-core chi0 on CTA pairs (cta_group::2) instead of one CTA per tile
   bool wtable_tc = false;   // imaginary-axis W-table solves on the tensor cores (else the SIMT forward substitution)
+  bool factor_split = false;  // complex FP32 factorisations as panel launches + batched tensor-core updates
+  void* d_lp = nullptr;     // their TF32 planes, lp_bytes bytes
+  size_t lp_bytes = 0;
   void* d_wt = nullptr;     // their workspace (TF32 planes), wt_bytes bytes
   size_t wt_bytes = 0;
   int border_max = 0;       // right-hand sides that may be appended as rows (matrix rows n_aux + border_max)

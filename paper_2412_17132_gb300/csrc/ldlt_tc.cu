@@ -29,6 +29,9 @@
 // The panel scratch aliases the operand buffers (the phases alternate).
 // Every mbarrier wait is bounded (one second); on expiry the CTA records kStatTimeout, stops,
 // drains the MMAs it issued and frees TMEM.
+#include <algorithm>
+#include <cstring>
+
 #include "gwc_internal.h"
 #include "ldlt_simt.cuh"
 #include "tc_common.cuh"
@@ -723,6 +726,258 @@ __global__ void __launch_bounds__(NT_TC, 1)
   ldlt_tc_matrix(G.mats + f * G.stride, G.n, G.nrow, G.ldm, status, wait_ns);
 }
 
+// ---- split factorisation: one panel launch and one batched tensor-core update per panel --------------
+// The kernel above gives each matrix one CTA for its whole factorisation, and its tensor phase waits on
+// the per-thread global loads of one SM (a 4500-wide matrix takes ~190 ms). Here every panel is three
+// launches over all matrices of the batch:
+//   ldlt_panel_kernel   the panel [k0, k0 + 64) of every matrix (one CTA each: factor_panel_tc);
+//   ldlt_planes_kernel  the panel's W columns (rows below it) and L rows (row k0 + l of the L^T stored above
+//                       the diagonal, the columns beyond the panel) as TF32 hi / lo planes, K-major;
+//   ldlt_update_kernel  C[i][j] -= sum_l W[i][l] L[j][l] over the trailing 128 x 64 tiles of every matrix,
+//                       one tile per CTA, two CTAs per SM: TMA-fed planes, the P and Q accumulators of the
+//                       one-CTA kernel, and the target tile staged through shared memory by TMA (128-byte
+//                       swizzle, clipped at column n and row nrow; the part of a diagonal tile above the
+//                       diagonal holds nothing yet and is overwritten when its own panel is factored).
+
+constexpr int UP_A = TM * 128;                   // one A plane chunk: 128 rows x 32 FP32 = 16 KB
+constexpr int UP_B = TN * 128;                   // one B plane chunk: 64 rows x 32 FP32 = 8 KB
+constexpr int UP_STAGE = 4 * UP_A + 4 * UP_B;    // Ar, Ai, Ar_lo, Ai_lo | Lr, Li, Lr_lo, Li_lo: 96 KB
+constexpr int UP_SMEM = 1024 + UP_STAGE + 128;
+constexpr int UP_THREADS = 256;                  // warp 0 TMA, 1 MMA, 2 TMEM, 4-7 epilogue
+constexpr int PANEL_SCRATCH = (int)PanelInv::bytes();
+constexpr int PANEL_SMEM = 1024 + PANEL_SCRATCH + 64;
+static_assert(TM * TN * 8 <= UP_STAGE, "the target tile fits in the stage");
+
+struct UpParams {
+  CUtensorMap a[4];  // Ar_hi, Ai_hi, Ar_lo, Ai_lo  [F * nrow][64]
+  CUtensorMap b[4];  // Lr_hi, Li_hi, Lr_lo, Li_lo  [F * n][64]
+  CUtensorMap c;     // targets: (2n FP32 along a row, nrow rows, F matrices)
+  int n, nrow, R0, F, tiles;
+  const int* active;
+  unsigned* status;
+  unsigned long long wait_ns;
+};
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int x, int y, int z, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(x), "r"(y), "r"(z), "r"(src)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(NT_PANEL, 1)
+    ldlt_panel_kernel(float2* __restrict__ mats, int n, int nrow, long long ldm, long long stride, int k0,
+                      const int* __restrict__ active, unsigned* __restrict__ status) {
+  const int f = blockIdx.x;
+  if (active && !active[f]) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const PanelInv ps(base);
+  int* sing = reinterpret_cast<int*>(base + PANEL_SCRATCH);
+  if (threadIdx.x == 0) *sing = 0;
+  __syncthreads();
+  factor_panel_tc(mats + f * stride, n, nrow, ldm, k0, ps, sing);
+  __syncthreads();
+  if (threadIdx.x == 0 && *sing) atomicOr(status, kStatSingular);
+}
+
+// blockIdx.y = matrix; blocks 0 .. nA-1: four rows i of W each; blocks nA ..: 32 columns j of L each
+__global__ void __launch_bounds__(256)
+    ldlt_planes_kernel(const float2* __restrict__ mats, int n, int nrow, long long ldm, long long stride, int k0, int nA,
+                       const int* __restrict__ active, float* __restrict__ ap, float* __restrict__ bp) {
+  const int f = blockIdx.y;
+  if (active && !active[f]) return;
+  const float2* A = mats + f * stride;
+  const int kb = min(PW, n - k0), R0 = k0 + kb;
+  const size_t a_plane = (size_t)gridDim.y * nrow * PW, b_plane = (size_t)gridDim.y * n * PW;
+  if ((int)blockIdx.x < nA) {
+    const int i = R0 + 4 * blockIdx.x + (threadIdx.x >> 6), l = threadIdx.x & 63;
+    if (i >= nrow) return;
+    const float2 v = l < kb ? A[(long long)i * ldm + k0 + l] : make_float2(0.f, 0.f);
+    const size_t o = ((size_t)f * nrow + i) * PW + l;
+    const float rh = tf32_rn(v.x), ih = tf32_rn(v.y);
+    ap[o] = rh;
+    ap[a_plane + o] = ih;
+    ap[2 * a_plane + o] = tf32_rn(v.x - rh);
+    ap[3 * a_plane + o] = tf32_rn(v.y - ih);
+    return;
+  }
+  __shared__ float2 tile[PW][33];
+  const int j0 = R0 + 32 * (blockIdx.x - nA);
+  for (int e = threadIdx.x; e < PW * 32; e += 256) {
+    const int l = e >> 5, jj = e & 31, j = j0 + jj;
+    tile[l][jj] = (l < kb && j < n) ? A[(long long)(k0 + l) * ldm + j] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < PW * 32; e += 256) {
+    const int jj = e >> 6, l = e & 63, j = j0 + jj;
+    if (j >= n) continue;
+    const float2 v = tile[l][jj];
+    const size_t o = ((size_t)f * n + j) * PW + l;
+    const float rh = tf32_rn(v.x), ih = tf32_rn(v.y);
+    bp[o] = rh;
+    bp[b_plane + o] = ih;
+    bp[2 * b_plane + o] = tf32_rn(v.x - rh);
+    bp[3 * b_plane + o] = tf32_rn(v.y - ih);
+  }
+}
+
+__global__ void __launch_bounds__(UP_THREADS, 2) ldlt_update_kernel(const __grid_constant__ UpParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + UP_STAGE);
+  uint64_t* empty = full + 1;
+  uint64_t* done = full + 2;
+  uint64_t* c_full = full + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int f = blockIdx.x / p.tiles;
+  int t = blockIdx.x - f * p.tiles;
+  if (f >= p.F || (p.active && !p.active[f])) return;  // uniform, before any barrier or TMEM use
+  int tI = 0;
+  for (;;) {  // (row tile, column tile) of tile t of the trailing lower part
+    const int nc = tile_cols(p.R0, p.n, tI);
+    if (t < nc) break;
+    t -= nc;
+    ++tI;
+  }
+  const int i0 = p.R0 + TM * tI, j0 = p.R0 + TN * t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(full), 1);
+    mbar_init(smem_u32(empty), 1);
+    mbar_init(smem_u32(done), 1);
+    mbar_init(smem_u32(c_full), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kc = 0; kc < PW / KH; ++kc) {  // one stage, reused by the second chunk
+        if (kc > 0 && !mbar_wait(smem_u32(empty), (uint32_t)(kc - 1) & 1, abort_flag, p.wait_ns)) break;
+        mbar_expect_tx(smem_u32(full), UP_STAGE);
+        const int ay = f * p.nrow + i0, by = f * p.n + j0;
+        for (int q = 0; q < 4; ++q) tma_load_2d(smem_u32(base + q * UP_A), &p.a[q], KH * kc, ay, smem_u32(full));
+        for (int q = 0; q < 4; ++q) tma_load_2d(smem_u32(base + 4 * UP_A + q * UP_B), &p.b[q], KH * kc, by, smem_u32(full));
+        issued = kc + 1;
+      }
+      if (issued > 0) mbar_drain(smem_u32(full), (uint32_t)(issued - 1) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t st = smem_u32(base);
+      const uint64_t dar = sdesc(st), dai = sdesc(st + UP_A), darl = sdesc(st + 2 * UP_A), dail = sdesc(st + 3 * UP_A);
+      const uint64_t dbh = sdesc(st + 4 * UP_A), dbl = sdesc(st + 4 * UP_A + 2 * UP_B);  // [Lr; Li] hi, lo
+      const uint32_t dp = tmem, dq = tmem + 128;
+      bool committed = false;  // `done` takes exactly one commit (a second would flip its phase back)
+      for (int kc = 0; kc < PW / KH; ++kc) {
+        if (!mbar_wait(smem_u32(full), (uint32_t)kc & 1, abort_flag, p.wait_ns)) break;
+        tc_fence_after();
+#pragma unroll
+        for (int k = 0; k < KH / 8; ++k) {
+          const uint64_t o = 2u * k;
+          const uint32_t acc = (kc == 0 && k == 0) ? 0u : 1u;
+          mma_tf32(dp, dar + o, dbh + o, acc);
+          mma_tf32(dp, dar + o, dbl + o, 1u);
+          mma_tf32(dp, darl + o, dbh + o, 1u);
+          mma_tf32(dq, dai + o, dbh + o, acc);
+          mma_tf32(dq, dai + o, dbl + o, 1u);
+          mma_tf32(dq, dail + o, dbh + o, 1u);
+        }
+        if (kc + 1 < PW / KH) {
+          mma_commit(smem_u32(empty));
+        } else {
+          mma_commit(smem_u32(done));
+          committed = true;
+        }
+      }
+      if (!committed) mma_commit(smem_u32(done));  // after an early stop: fires once the issued MMAs complete
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue: C -= (P_re - Q_im, P_im + Q_re) through shared memory -------------------------
+    const int q = warp & 3, r = 32 * q + lane;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(done), 0, abort_flag, p.wait_ns));
+    tc_fence_after();
+    bool landed = false;
+    if (ok && !*abort_flag) {
+      if (threadIdx.x == 128) {
+        mbar_expect_tx(smem_u32(c_full), TM * TN * 8);
+        for (int b = 0; b < 4; ++b) tma_load_3d(smem_u32(base + b * UP_A), &p.c, 2 * j0 + 32 * b, i0, f, smem_u32(c_full));
+      }
+      landed = __all_sync(0xffffffffu, mbar_wait(smem_u32(c_full), 0, abort_flag, p.wait_ns));
+      if (landed) {
+        const uint32_t lb = tmem + ((uint32_t)(32 * q) << 16);
+        for (int c4 = 0; c4 < 4; ++c4) {  // complex columns 16 c4 .. + 15: box c4 of the staged tile
+          uint32_t pr[16], pi[16], qr[16], qi[16];
+          tmem_ld16_nw(lb + 16 * c4, pr);        // Ar Lr^T
+          tmem_ld16_nw(lb + 64 + 16 * c4, pi);   // Ar Li^T
+          tmem_ld16_nw(lb + 128 + 16 * c4, qr);  // Ai Lr^T
+          tmem_ld16_nw(lb + 192 + 16 * c4, qi);  // Ai Li^T
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          uint8_t* rowp = base + c4 * UP_A + r * 128;
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {  // 16-byte chunk ch: complex columns 2 ch, 2 ch + 1
+            float4* cp = reinterpret_cast<float4*>(rowp + ((ch ^ (r & 7)) << 4));
+            float4 v = *cp;
+            const int e0 = 2 * ch, e1 = 2 * ch + 1;
+            v.x -= __uint_as_float(pr[e0]) - __uint_as_float(qi[e0]);
+            v.y -= __uint_as_float(pi[e0]) + __uint_as_float(qr[e0]);
+            v.z -= __uint_as_float(pr[e1]) - __uint_as_float(qi[e1]);
+            v.w -= __uint_as_float(pi[e1]) + __uint_as_float(qr[e1]);
+            *cp = v;
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // every epilogue warp, whatever its waits gave
+    if (threadIdx.x == 128) {
+      if (landed && !*abort_flag) {
+        for (int b = 0; b < 4; ++b) tma_store_3d(&p.c, 2 * j0 + 32 * b, i0, f, smem_u32(base + b * UP_A));
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      } else if (ok) {
+        mbar_drain(smem_u32(c_full), 0);
+      }
+    }
+  }
+  if (warp == 2) {
+    if (lane == 0) mbar_drain(smem_u32(done), 0);
+    __syncwarp();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(p.status, kStatTimeout);
+  if (warp == 2) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  }
+}
+
+int host_tile_cols(int R0, int n, int tI) {
+  const int jmax = std::min(n, R0 + TM * tI + TM);
+  return (jmax - R0 + TN - 1) / TN;
+}
+
 }  // namespace
 
 int launch_ldlt_tc_grouped(const LdltGroup* d_groups, int n_groups, int n_ctas, unsigned* status,
@@ -754,6 +1009,69 @@ int launch_ldlt_tc(void* mats, int n, int nrow, long long ldm, long long stride,
   ldlt_tc_kernel<<<F, NT_TC, SMEM_TC, s>>>(reinterpret_cast<float2*>(mats), n, nrow, ldm, stride, active, status,
                                                 wait_ns);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+size_t ldlt_split_bytes(int n, int nrow, int F) { return (size_t)16 * F * PW * ((size_t)nrow + n) + 1024; }
+
+// Returns the launches, -1 on a launch error or bad layout, -2 if unsupported.
+int launch_ldlt_split(void* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active,
+                      unsigned* status, unsigned long long wait_ns, void* work, size_t work_bytes, cudaStream_t s) {
+  if (!tc_supported()) return -2;
+  if ((ldm % 4) || (stride % 4) || (reinterpret_cast<uintptr_t>(mats) & 15) || nrow < n || n < 1 || F < 1) return -1;
+  if (ldlt_split_bytes(n, nrow, F) > work_bytes || (reinterpret_cast<uintptr_t>(work) & 15)) return -2;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(ldlt_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(ldlt_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, UP_SMEM) != cudaSuccess)
+      return -1;
+    attr = true;
+  }
+  float* ap = static_cast<float*>(work);
+  float* bp = ap + (size_t)4 * F * nrow * PW;
+  UpParams p;
+  std::memset(static_cast<void*>(&p), 0, sizeof(p));
+  for (int q = 0; q < 4; ++q) {
+    if (!make_map(&p.a[q], ap + (size_t)q * F * nrow * PW, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, F * nrow, PW, KH, TM) ||
+        !make_map(&p.b[q], bp + (size_t)q * F * n * PW, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, F * n, PW, KH, TN))
+      return -2;
+  }
+  {
+    EncodeTiledFn enc = encoder();
+    if (!enc) return -2;
+    cuuint64_t dims[3] = {(cuuint64_t)2 * n, (cuuint64_t)nrow, (cuuint64_t)F};
+    cuuint64_t strides[2] = {(cuuint64_t)ldm * 8, (cuuint64_t)stride * 8};
+    cuuint32_t box[3] = {32, (cuuint32_t)TM, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&p.c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, mats, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return -2;
+  }
+  p.n = n;
+  p.nrow = nrow;
+  p.F = F;
+  p.active = active;
+  p.status = status;
+  p.wait_ns = wait_ns;
+  float2* A = reinterpret_cast<float2*>(mats);
+  int launches = 0;
+  for (int k0 = 0; k0 < n; k0 += PW) {
+    const int kb = std::min(PW, n - k0), R0 = k0 + kb;
+    ldlt_panel_kernel<<<F, NT_PANEL, PANEL_SMEM, s>>>(A, n, nrow, ldm, stride, k0, active, status);
+    ++launches;
+    if (R0 < n) {
+      const int nA = (nrow - R0 + 3) / 4, nB = (n - R0 + 31) / 32;
+      ldlt_planes_kernel<<<dim3(nA + nB, F), 256, 0, s>>>(A, n, nrow, ldm, stride, k0, nA, active, ap, bp);
+      int tiles = 0;
+      const int n_ti = (nrow - R0 + TM - 1) / TM;
+      for (int tI = 0; tI < n_ti; ++tI) tiles += host_tile_cols(R0, n, tI);
+      p.R0 = R0;
+      p.tiles = tiles;
+      ldlt_update_kernel<<<F * tiles, UP_THREADS, UP_SMEM, s>>>(p);
+      launches += 2;
+    }
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+  }
+  return launches;
 }
 
 }  // namespace gwc

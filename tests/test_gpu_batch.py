@@ -72,6 +72,8 @@ def test_batch_graph_equals_individual_steps(gwc, grouped, monkeypatch):
     form (persistent grouped chi0 and grouped factorisation launches over all molecules) and the graph of
     per-molecule steps (GWC_BATCH set)."""
     monkeypatch.setenv("GWC_BATCH", "grouped" if grouped else "per-molecule")
+    if grouped:  # the grouped launch factors with the one-CTA tensor-core kernel; so do the steps it is compared to
+        monkeypatch.setenv("GWC_FACTOR", "tc")
     mols = [synth.small(n_states=n, n_occ=max(2, n // 8), n_core=1 + (n % 2), n_aux=int(2.5 * n), seed=100 + n)
             for n in (24, 41, 57, 33)]
     alone = []
@@ -132,9 +134,11 @@ def test_persistent_chi0_equals_one_cta_per_item(gwc):
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
 
 
-def test_grouped_batch_with_many_chunks(gwc):
+def test_grouped_batch_with_many_chunks(gwc, monkeypatch):
     """Small workspaces (16 frequencies per batch) give each molecule several residue chunks, and the grouped
-    launches hold different numbers of molecules chunk by chunk; results as the molecules alone."""
+    launches hold different numbers of molecules chunk by chunk; results as the molecules alone (both with the
+    one-CTA tensor-core factorisation, the grouped launch's kernel)."""
+    monkeypatch.setenv("GWC_FACTOR", "tc")
     mols = [synth.small(n_states=n, n_occ=max(2, n // 8), n_core=1 + (n % 3), n_aux=int(2.5 * n), seed=200 + n)
             for n in (36, 52, 29)]
     alone = []

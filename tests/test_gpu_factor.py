@@ -1,8 +1,9 @@
 """Parity of the dielectric factorisation kernels at ragged sizes (through the C ABI).
 
 The mixed-precision modes factor eps(z) = 1 - Pi(z) with the tensor-core LDL^T (3xTF32 trailing
-updates); the FP32 SIMT kernel stays available (GWC_FACTOR=simt) and the FP64 path uses the SIMT
-kernel in FP64. These tests pin the tensor-core kernel
+updates): by default as one panel launch and one batched update launch per 64-column panel over all
+matrices, with GWC_FACTOR=tc as one CTA per matrix; the FP32 SIMT kernel stays available
+(GWC_FACTOR=simt) and the FP64 path uses the SIMT kernel in FP64. These tests pin the tensor-core forms
   * against the FP64 oracle (W^c = b^T (eps^-1 - 1) b by LU, and Sigma^c through the residue path,
     where the right-hand sides are appended as rows of the factored matrix), at sizes that are not
     multiples of the 64-wide panel or the 128-row tile, down to a single auxiliary function;
@@ -58,11 +59,14 @@ def _context(gwc, mol, prec, factor=None):
 ZS = [complex(0.0, 0.9), complex(0.37, 1e-3), complex(2.9, 1e-3), complex(11.0, 1e-3)]
 
 
+@pytest.mark.parametrize("factor", ["tc", "split"])
 @pytest.mark.parametrize("n_aux,n_states,n_occ", [(1, 9, 2), (63, 30, 5), (64, 30, 5), (65, 31, 6), (130, 40, 6),
-                                                  (257, 45, 7)])
-def test_screen_ragged_tensor_core_factor_vs_oracle(gwc, n_aux, n_states, n_occ):
+                                                  (257, 45, 7), (400, 50, 8)])
+def test_screen_ragged_tensor_core_factor_vs_oracle(gwc, n_aux, n_states, n_occ, factor):
+    """The split form (the default: panel launches + batched tensor-core updates over 128 x 64 tiles,
+    several per matrix) and the one-CTA tensor-core kernel."""
     mol = synth.small(n_states=n_states, n_occ=n_occ, n_core=1, n_aux=n_aux, seed=100 + n_aux)
-    ctx = _context(gwc, mol, "bf16x3")
+    ctx = _context(gwc, mol, "bf16x3", factor=factor)
     z = torch.tensor([[v.real, v.imag] for v in ZS], dtype=torch.float64, device="cuda")
     rows = [0, 1, n_states // 2, n_states - 1]
     rhs_np = np.stack([mol.o_core[rows, 0, :] for _ in ZS])  # [F][4][n_aux]
@@ -75,11 +79,12 @@ def test_screen_ragged_tensor_core_factor_vs_oracle(gwc, n_aux, n_states, n_occ)
         assert err < 2e-3, (n_aux, v, err)
 
 
+@pytest.mark.parametrize("factor", ["tc", "split"])
 @pytest.mark.parametrize("n_aux,n_core", [(65, 2), (130, 3), (257, 4)])
-def test_sigma_ragged_appended_rows_vs_oracle(gwc, n_aux, n_core):
+def test_sigma_ragged_appended_rows_vs_oracle(gwc, n_aux, n_core, factor):
     """Residue path: N_core right-hand sides appended as rows of the factored matrix."""
     mol = synth.small(n_states=30, n_occ=5, n_core=n_core, n_aux=n_aux, seed=7 + n_aux, n_omega=8)
-    ctx = _context(gwc, mol, "bf16x3")
+    ctx = _context(gwc, mol, "bf16x3", factor=factor)
     sig, dec, _ = ctx.sigma_core(mol.omega)
     ctx.sync()
     ref, ref_dec = G.System.from_molecule(mol).sigma_c_grid(mol.omega)
@@ -99,7 +104,7 @@ def test_tensor_core_factor_as_accurate_as_simt_kernel(gwc):
     rhs_np = np.stack([mol.o_core[[0, 5, 17, 40, 59], 0, :] for _ in ZS])
     rhs = torch.as_tensor(rhs_np, device="cuda")
     out = {}
-    for tag in ("tc", "simt"):
+    for tag in ("tc", "split", "simt"):
         ctx = _context(gwc, mol, "bf16x3", factor=tag)
         out[tag] = _cplx(ctx.screen(z, rhs))
         assert ctx.sync_status() == 0
@@ -110,16 +115,28 @@ def test_tensor_core_factor_as_accurate_as_simt_kernel(gwc):
         scale = np.max(np.abs(ref))
         err = {tag: np.max(np.abs(out[tag][f] - ref)) / scale for tag in out}
         assert err["tc"] <= 2.0 * err["simt"] + 1e-6, (v, err)
+        assert err["split"] <= 2.0 * err["simt"] + 1e-6, (v, err)
 
 
-def test_zero_pivot_reported_by_tensor_core_path(gwc):
+@pytest.mark.parametrize("factor", ["tc", "split"])
+def test_zero_pivot_reported_by_tensor_core_path(gwc, factor):
     # eps = 1 - Pi = 0 exactly at z = 3 (one aux function, two pairs with Delta = 1, O = 1): every
     # value is exact in BF16 and FP32, so the mixed path meets the same exact zero pivot
     eps = np.array([-0.5, 0.5, 0.5])
     o_ov = np.array([[1.0, 1.0]])
     o_core = np.array([[[1.0]], [[0.5]], [[0.25]]])
-    ctx = gwc.Context(torch.as_tensor(eps, device="cuda"), 1, [0], torch.as_tensor(o_ov, device="cuda"),
-                      torch.as_tensor(o_core, device="cuda"), prec="bf16x3")
+    old = os.environ.get("GWC_FACTOR")
+    if factor:
+        os.environ["GWC_FACTOR"] = factor
+    try:
+        ctx = gwc.Context(torch.as_tensor(eps, device="cuda"), 1, [0], torch.as_tensor(o_ov, device="cuda"),
+                          torch.as_tensor(o_core, device="cuda"), prec="bf16x3")
+    finally:
+        if factor:
+            if old is None:
+                os.environ.pop("GWC_FACTOR")
+            else:
+                os.environ["GWC_FACTOR"] = old
     zt = torch.tensor([[3.0, 0.0]], dtype=torch.float64, device="cuda")
     ctx.screen(zt, torch.ones((1, 1, 1), dtype=torch.float64, device="cuda"))
     assert ctx.sync_status() == 4
