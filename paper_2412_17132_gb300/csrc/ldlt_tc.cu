@@ -738,6 +738,9 @@ __global__ void __launch_bounds__(NT_TC, 1)
 //                       one-CTA kernel, and the target tile staged through shared memory by TMA (128-byte
 //                       swizzle, clipped at column n and row nrow; the part of a diagonal tile above the
 //                       diagonal holds nothing yet and is overwritten when its own panel is factored).
+// Panels go in pairs with a one-panel lookahead: panel p's update is first applied to panel p + 1's 64
+// columns only, panel p + 1 is factored, and then one rank-128 update (K = 128: both panels' planes side by
+// side) covers the trailing matrix, which is thus read and written once per two panels.
 
 constexpr int UP_A = TM * 128;                   // one A plane chunk: 128 rows x 32 FP32 = 16 KB
 constexpr int UP_B = TN * 128;                   // one B plane chunk: 64 rows x 32 FP32 = 8 KB
@@ -748,11 +751,15 @@ constexpr int PANEL_SCRATCH = (int)PanelInv::bytes();
 constexpr int PANEL_SMEM = 1024 + PANEL_SCRATCH + 64;
 static_assert(TM * TN * 8 <= UP_STAGE, "the target tile fits in the stage");
 
+constexpr int KW = 2 * PW;  // K width of the planes: two panels
+
 struct UpParams {
-  CUtensorMap a[4];  // Ar_hi, Ai_hi, Ar_lo, Ai_lo  [F * nrow][64]
-  CUtensorMap b[4];  // Lr_hi, Li_hi, Lr_lo, Li_lo  [F * n][64]
+  CUtensorMap a[4];  // Ar_hi, Ai_hi, Ar_lo, Ai_lo  [F * nrow][KW]
+  CUtensorMap b[4];  // Lr_hi, Li_hi, Lr_lo, Li_lo  [F * n][KW]
   CUtensorMap c;     // targets: (2n FP32 along a row, nrow rows, F matrices)
   int n, nrow, R0, F, tiles;
+  int nkc;           // 32-wide K chunks of this update (2: one panel, 4: two)
+  int one_col;       // lookahead: only the column tile [R0, R0 + 64)
   const int* active;
   unsigned* status;
   unsigned long long wait_ns;
@@ -790,18 +797,18 @@ __global__ void __launch_bounds__(NT_PANEL, 1)
 
 // blockIdx.y = matrix; blocks 0 .. nA-1: four rows i of W each; blocks nA ..: 32 columns j of L each
 __global__ void __launch_bounds__(256)
-    ldlt_planes_kernel(const float2* __restrict__ mats, int n, int nrow, long long ldm, long long stride, int k0, int nA,
-                       const int* __restrict__ active, float* __restrict__ ap, float* __restrict__ bp) {
+    ldlt_planes_kernel(const float2* __restrict__ mats, int n, int nrow, long long ldm, long long stride, int k0, int koff,
+                       int nA, const int* __restrict__ active, float* __restrict__ ap, float* __restrict__ bp) {
   const int f = blockIdx.y;
   if (active && !active[f]) return;
   const float2* A = mats + f * stride;
   const int kb = min(PW, n - k0), R0 = k0 + kb;
-  const size_t a_plane = (size_t)gridDim.y * nrow * PW, b_plane = (size_t)gridDim.y * n * PW;
+  const size_t a_plane = (size_t)gridDim.y * nrow * KW, b_plane = (size_t)gridDim.y * n * KW;
   if ((int)blockIdx.x < nA) {
     const int i = R0 + 4 * blockIdx.x + (threadIdx.x >> 6), l = threadIdx.x & 63;
     if (i >= nrow) return;
     const float2 v = l < kb ? A[(long long)i * ldm + k0 + l] : make_float2(0.f, 0.f);
-    const size_t o = ((size_t)f * nrow + i) * PW + l;
+    const size_t o = ((size_t)f * nrow + i) * KW + koff + l;
     const float rh = tf32_rn(v.x), ih = tf32_rn(v.y);
     ap[o] = rh;
     ap[a_plane + o] = ih;
@@ -820,7 +827,7 @@ __global__ void __launch_bounds__(256)
     const int jj = e >> 6, l = e & 63, j = j0 + jj;
     if (j >= n) continue;
     const float2 v = tile[l][jj];
-    const size_t o = ((size_t)f * n + j) * PW + l;
+    const size_t o = ((size_t)f * n + j) * KW + koff + l;
     const float rh = tf32_rn(v.x), ih = tf32_rn(v.y);
     bp[o] = rh;
     bp[b_plane + o] = ih;
@@ -843,11 +850,16 @@ __global__ void __launch_bounds__(UP_THREADS, 2) ldlt_update_kernel(const __grid
   int t = blockIdx.x - f * p.tiles;
   if (f >= p.F || (p.active && !p.active[f])) return;  // uniform, before any barrier or TMEM use
   int tI = 0;
-  for (;;) {  // (row tile, column tile) of tile t of the trailing lower part
-    const int nc = tile_cols(p.R0, p.n, tI);
-    if (t < nc) break;
-    t -= nc;
-    ++tI;
+  if (p.one_col) {  // lookahead: row tile t, the column tile [R0, R0 + 64)
+    tI = t;
+    t = 0;
+  } else {
+    for (;;) {  // (row tile, column tile) of tile t of the trailing lower part
+      const int nc = tile_cols(p.R0, p.n, tI);
+      if (t < nc) break;
+      t -= nc;
+      ++tI;
+    }
   }
   const int i0 = p.R0 + TM * tI, j0 = p.R0 + TN * t;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -872,7 +884,7 @@ __global__ void __launch_bounds__(UP_THREADS, 2) ldlt_update_kernel(const __grid
   if (warp == 0) {
     if (lane == 0) {
       int issued = 0;
-      for (int kc = 0; kc < PW / KH; ++kc) {  // one stage, reused by the second chunk
+      for (int kc = 0; kc < p.nkc; ++kc) {  // one stage, reused by every chunk
         if (kc > 0 && !mbar_wait(smem_u32(empty), (uint32_t)(kc - 1) & 1, abort_flag, p.wait_ns)) break;
         mbar_expect_tx(smem_u32(full), UP_STAGE);
         const int ay = f * p.nrow + i0, by = f * p.n + j0;
@@ -889,7 +901,7 @@ __global__ void __launch_bounds__(UP_THREADS, 2) ldlt_update_kernel(const __grid
       const uint64_t dbh = sdesc(st + 4 * UP_A), dbl = sdesc(st + 4 * UP_A + 2 * UP_B);  // [Lr; Li] hi, lo
       const uint32_t dp = tmem, dq = tmem + 128;
       bool committed = false;  // `done` takes exactly one commit (a second would flip its phase back)
-      for (int kc = 0; kc < PW / KH; ++kc) {
+      for (int kc = 0; kc < p.nkc; ++kc) {
         if (!mbar_wait(smem_u32(full), (uint32_t)kc & 1, abort_flag, p.wait_ns)) break;
         tc_fence_after();
 #pragma unroll
@@ -903,7 +915,7 @@ __global__ void __launch_bounds__(UP_THREADS, 2) ldlt_update_kernel(const __grid
           mma_tf32(dq, dai + o, dbl + o, 1u);
           mma_tf32(dq, dail + o, dbh + o, 1u);
         }
-        if (kc + 1 < PW / KH) {
+        if (kc + 1 < p.nkc) {
           mma_commit(smem_u32(empty));
         } else {
           mma_commit(smem_u32(done));
@@ -1011,7 +1023,7 @@ int launch_ldlt_tc(void* mats, int n, int nrow, long long ldm, long long stride,
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-size_t ldlt_split_bytes(int n, int nrow, int F) { return (size_t)16 * F * PW * ((size_t)nrow + n) + 1024; }
+size_t ldlt_split_bytes(int n, int nrow, int F) { return (size_t)16 * F * KW * ((size_t)nrow + n) + 1024; }
 
 // Returns the launches, -1 on a launch error or bad layout, -2 if unsupported.
 int launch_ldlt_split(void* mats, int n, int nrow, long long ldm, long long stride, int F, const int* active,
@@ -1027,12 +1039,12 @@ int launch_ldlt_split(void* mats, int n, int nrow, long long ldm, long long stri
     attr = true;
   }
   float* ap = static_cast<float*>(work);
-  float* bp = ap + (size_t)4 * F * nrow * PW;
+  float* bp = ap + (size_t)4 * F * nrow * KW;
   UpParams p;
   std::memset(static_cast<void*>(&p), 0, sizeof(p));
   for (int q = 0; q < 4; ++q) {
-    if (!make_map(&p.a[q], ap + (size_t)q * F * nrow * PW, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, F * nrow, PW, KH, TM) ||
-        !make_map(&p.b[q], bp + (size_t)q * F * n * PW, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, F * n, PW, KH, TN))
+    if (!make_map(&p.a[q], ap + (size_t)q * F * nrow * KW, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, F * nrow, KW, KH, TM) ||
+        !make_map(&p.b[q], bp + (size_t)q * F * n * KW, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, F * n, KW, KH, TN))
       return -2;
   }
   {
@@ -1054,23 +1066,49 @@ int launch_ldlt_split(void* mats, int n, int nrow, long long ldm, long long stri
   p.wait_ns = wait_ns;
   float2* A = reinterpret_cast<float2*>(mats);
   int launches = 0;
-  for (int k0 = 0; k0 < n; k0 += PW) {
-    const int kb = std::min(PW, n - k0), R0 = k0 + kb;
+  auto panel = [&](int k0) {
     ldlt_panel_kernel<<<F, NT_PANEL, PANEL_SMEM, s>>>(A, n, nrow, ldm, stride, k0, active, status);
     ++launches;
-    if (R0 < n) {
-      const int nA = (nrow - R0 + 3) / 4, nB = (n - R0 + 31) / 32;
-      ldlt_planes_kernel<<<dim3(nA + nB, F), 256, 0, s>>>(A, n, nrow, ldm, stride, k0, nA, active, ap, bp);
-      int tiles = 0;
-      const int n_ti = (nrow - R0 + TM - 1) / TM;
+  };
+  auto planes = [&](int k0, int koff) {
+    const int R0 = k0 + std::min(PW, n - k0);
+    const int nA = (nrow - R0 + 3) / 4, nB = (n - R0 + 31) / 32;
+    ldlt_planes_kernel<<<dim3(nA + nB, F), 256, 0, s>>>(A, n, nrow, ldm, stride, k0, koff, nA, active, ap, bp);
+    ++launches;
+  };
+  auto update = [&](int R0, int nkc, bool one_col) {
+    const int n_ti = (nrow - R0 + TM - 1) / TM;
+    int tiles = 0;
+    if (one_col) {
+      tiles = n_ti;
+    } else {
       for (int tI = 0; tI < n_ti; ++tI) tiles += host_tile_cols(R0, n, tI);
-      p.R0 = R0;
-      p.tiles = tiles;
-      ldlt_update_kernel<<<F * tiles, UP_THREADS, UP_SMEM, s>>>(p);
-      launches += 2;
+    }
+    p.R0 = R0;
+    p.tiles = tiles;
+    p.nkc = nkc;
+    p.one_col = one_col ? 1 : 0;
+    ldlt_update_kernel<<<F * tiles, UP_THREADS, UP_SMEM, s>>>(p);
+    ++launches;
+  };
+  for (int k0 = 0; k0 < n;) {
+    // panel p at k0, with the planes of its W columns and L rows in K columns 0..63
+    const int R0 = k0 + std::min(PW, n - k0);
+    panel(k0);
+    if (R0 >= n) break;
+    planes(k0, 0);
+    // lookahead: panel p's update of panel p + 1's columns only, then panel p + 1
+    update(R0, PW / KH, true);
+    panel(R0);
+    const int R1 = R0 + std::min(PW, n - R0);
+    if (R1 < n) {
+      planes(R0, PW);
+      update(R1, KW / KH, false);  // both panels: K = 128
     }
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    k0 = R1;
   }
+  if (cudaPeekAtLastError() != cudaSuccess) return -1;
   return launches;
 }
 
