@@ -388,9 +388,9 @@ gwc_status run_chi0_stride(gwc_ctx* ctx, bool complex_z, int F, const double* d_
 // host synchronisation or allocation (the frequencies were uploaded at creation).
 // Imaginary-axis nodes per table batch (all n_im + 1 in one batch when the workspace holds them).
 int wim_batch(const gwc_ctx* ctx) {
-  // the tensor-core table builds and factors the real eps(i xi) in complex storage (zero imaginary parts)
-  const MatKind k = ctx->wtable_tc ? cplx_kind(ctx) : real_kind(ctx);
-  const size_t per_real = (size_t)ctx->n_aux * ctx->ldm * mat_elem_bytes(k);
+  // the tensor-core table factors the real eps(i xi) in complex storage (zero imaginary parts), built real
+  // behind the complex matrices and widened: 8 + 4 bytes per element
+  const size_t per_real = (size_t)ctx->n_aux * ctx->ldm * (ctx->wtable_tc ? 12 : mat_elem_bytes(real_kind(ctx)));
   const int fb = (int)std::max<size_t>(1, std::min<size_t>(ctx->mats_bytes / per_real, (size_t)ctx->batch));
   return std::min(fb, ctx->opt.n_im + 1);
 }
@@ -402,10 +402,15 @@ gwc_status enqueue_wim(gwc_ctx* ctx, cudaStream_t st) {
   const int fb = wim_batch(ctx);
   for (int k0 = 0; k0 < nodes; k0 += fb) {
     const int nb = std::min(fb, nodes - k0);
-    // z = i xi: D is real, so a complex build gives Im Pi = 0 exactly (the tensor-core table's storage); only
-    // the real part is algorithmic work, so the second part is not charged to the flop count
-    TRY(run_chi0(ctx, ctx->wtable_tc, nb, ctx->d_zim + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st));
-    if (ctx->wtable_tc) ctx->stats.chi0_flop -= (double)nb * (double)ctx->n_aux * (ctx->n_aux + 1.0) * (double)ctx->n_ov;
+    if (ctx->wtable_tc) {
+      // real builds behind the nb complex matrices, widened into them (Im = 0) for the tensor-core LDL^T
+      const long long per = (long long)ctx->n_aux * ctx->ldm;
+      float* real = reinterpret_cast<float*>(static_cast<char*>(ctx->d_mats) + (size_t)nb * per * 8);
+      TRY(run_chi0(ctx, false, nb, ctx->d_zim + 2 * k0, nullptr, real, -1.0, 1.0, 0, st));
+      LAUNCH(launch_widen_real(real, per, ctx->d_mats, per, per, nb, st));
+    } else {
+      TRY(run_chi0(ctx, false, nb, ctx->d_zim + 2 * k0, nullptr, ctx->d_mats, -1.0, 1.0, 0, st));
+    }
     TRY(enqueue_wim_tail(ctx, k0, nb, st));
   }
   return GWC_OK;

@@ -154,6 +154,9 @@ int launch_ldlt_split(void* mats, int n, int nrow, long long ldm, long long stri
 // y = L^-1 b (table node stride t_node = r). `work` holds wtable_tc_bytes(n, r, ng) bytes (16-byte aligned).
 // Returns the launches, -1 on a launch error, -2 if unsupported.
 size_t wtable_tc_bytes(int n_aux, int r, int ng);
+// dst[u][e] = (src[u][e], 0), e < per, u < nb (real matrices into complex FP32 storage)
+int launch_widen_real(const float* src, long long src_node, void* dst, long long dst_node, long long per, int nb,
+                      cudaStream_t s);
 int launch_wtable_tc(const float* mats, int es, int n, long long ldm, long long m_node, float* rhs, long long ldc, long long c_node,
                      int r, int ng, const double* bnorm, double* table, long long t_node, void* work, size_t work_bytes,
                      unsigned* status, unsigned long long wait_ns, cudaStream_t s);

@@ -346,6 +346,16 @@ __global__ void wt_init_kernel(const double* __restrict__ bnorm, int r, int ng, 
 
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
 
+// complex storage (v, 0) of real matrices: dst[u][e] = (src[u][e], 0) for e < per
+__global__ void widen_kernel(const float* __restrict__ src, long long src_node, float2* __restrict__ dst, long long dst_node,
+                             long long per, int nb) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < per * nb; e += (long long)gridDim.x * blockDim.x) {
+    const int u = (int)(e / per);
+    const long long k = e - (long long)u * per;
+    dst[(long long)u * dst_node + k] = make_float2(src[(long long)u * src_node + k], 0.0f);
+  }
+}
+
 // (P, col, node) view of the right-hand sides [node][col][ldc]: extents n, r, ng; box 128 x 256 x 1, no swizzle
 bool make_c_map(CUtensorMap* tm, float* c, int n, int r, int ng, long long ldc, long long c_node) {
   EncodeTiledFn enc = encoder();
@@ -458,6 +468,12 @@ int launch_wtable_tc(const float* mats, int es, int n, long long ldm, long long 
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
   }
   return launches;
+}
+
+int launch_widen_real(const float* src, long long src_node, void* dst, long long dst_node, long long per, int nb,
+                      cudaStream_t s) {
+  widen_kernel<<<grid_for(per * nb), 256, 0, s>>>(src, src_node, static_cast<float2*>(dst), dst_node, per, nb);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace gwc
