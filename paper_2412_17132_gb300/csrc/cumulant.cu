@@ -32,7 +32,12 @@ __global__ void cumulant_coef_kernel(const double* __restrict__ omega_rel, int n
   coef[t] = wj == 0.0 ? 0.0 : q * beta / (wj * wj);
 }
 
-// g[c][k] = w_k exp(C~(t_k) - eta t_k), C~ summed over the grid in FP64.
+// g[c][k] = w_k exp(C~(t_k) - eta t_k), C~ summed over the grid in FP64. Each thread takes KT consecutive
+// times: per grid point one sincos at its first time and one for the step w_j dt, then the phase advances
+// by that rotation (FP64 sincos runs at the FP64 rate, 1/64 of FP32 on this part; the rotation drifts by
+// ~KT ulp over a block).
+constexpr int KT = 32;
+
 __global__ void cumulant_time_kernel(const double* __restrict__ omega_rel, int n_w, const double* __restrict__ coef,
                                      int n_core, int n_t, double dt, double eta, double2* __restrict__ g) {
   extern __shared__ double sh[];  // [2][n_w]
@@ -44,22 +49,37 @@ __global__ void cumulant_time_kernel(const double* __restrict__ omega_rel, int n
     sc[j] = coef[(size_t)c * n_w + j];
   }
   __syncthreads();
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_t) return;
-  const double t = dt * k;
-  double re = 0.0, im = 0.0;
+  const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * KT;
+  if (k0 >= n_t) return;
+  double re[KT], im[KT];
+#pragma unroll
+  for (int q = 0; q < KT; ++q) re[q] = im[q] = 0.0;
+  const double t0 = dt * k0;
   for (int j = 0; j < n_w; ++j) {
-    double cj = sc[j];
+    const double cj = sc[j];
     if (cj == 0.0) continue;
-    double sn, cs;
-    sincos(sw[j] * t, &sn, &cs);
-    re += cj * (cs - 1.0);
-    im -= cj * sn;
+    double sn, cs, sd, cd;
+    sincos(sw[j] * t0, &sn, &cs);
+    sincos(sw[j] * dt, &sd, &cd);
+#pragma unroll
+    for (int q = 0; q < KT; ++q) {
+      re[q] += cj * (cs - 1.0);
+      im[q] -= cj * sn;
+      const double c2 = cs * cd - sn * sd;  // angle + w_j dt
+      sn = sn * cd + cs * sd;
+      cs = c2;
+    }
   }
-  double mag = exp(re - eta * t) * (k == 0 ? 0.5 : 1.0);
-  double sn, cs;
-  sincos(im, &sn, &cs);
-  g[(size_t)c * n_t + k] = make_double2(mag * cs, mag * sn);
+#pragma unroll
+  for (int q = 0; q < KT; ++q) {
+    const int k = k0 + q;
+    if (k >= n_t) break;
+    const double t = dt * k;
+    const double mag = exp(re[q] - eta * t) * (k == 0 ? 0.5 : 1.0);
+    double sn, cs;
+    sincos(im[q], &sn, &cs);
+    g[(size_t)c * n_t + k] = make_double2(mag * cs, mag * sn);
+  }
 }
 
 __global__ void twiddle_kernel(int n, double2* __restrict__ tw) {
@@ -113,7 +133,7 @@ int launch_cumulant_spectrum(const double* omega_rel, int n_w, const double* im_
     if (cudaFuncSetAttribute(cumulant_time_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
       return -1;
   }
-  dim3 g((n_t + 255) / 256, n_core);
+  dim3 g((n_t + 256 * KT - 1) / (256 * KT), n_core);
   cumulant_time_kernel<<<g, 256, sm, s>>>(omega_rel, n_w, coef, n_core, n_t, dt, eta, (double2*)work_a);
   ++launches;
   twiddle_kernel<<<(n_t / 2 + 255) / 256, 256, 0, s>>>(n_t, (double2*)twiddle);
