@@ -113,9 +113,10 @@ typedef struct {
                             MMAs it issued, frees its tensor memory and records
                             GWC_ERR_TIMEOUT (reported by gwc_sync); the results of that call
                             are undefined, and the context stays usable. 0..60000000          */
-  int chi0_ctas;         /* launch shape of the tensor-core polarizability build: 0 one CTA per
-                            (128 x 128 tile, frequency group) item; > 0 at most that many CTAs,
-                            each looping over the items (persistent). gwc_autotune may change it */
+  int chi0_ctas;         /* launch shape of the tensor-core polarizability build: 0 one CTA (or
+                            CTA pair) per (tile, frequency group) item; > 0 at most that many
+                            CTAs, each looping over the items (persistent). gwc_autotune may
+                            change it */
 } gwc_options;
 
 /* GWC_QP_SECANT: iterate the G_dH W0 QP equation (eq quasiparticle_equation with the shifted
@@ -159,9 +160,17 @@ gwc_status gwc_workspace_bytes(const gwc_system* sys, const gwc_options* opt, in
  * With core_idx, eps, o_ov and o_core all NULL the system gives sizes only: the context is
  * allocated with that capacity and holds no system until gwc_load (serving slots sized for the
  * largest request of a class); the other entry points return GWC_ERR_INVALID_ARG until then.
- * In the BF16 and BF16X3 modes the complex dielectric matrices are factored by the tensor-core
- * kernel (3xTF32 trailing updates, FP32-accurate); the environment variable GWC_FACTOR=simt,
- * read here, keeps them on the FP32 SIMT kernel instead (for comparisons). */
+ * Kernel choice of the BF16 and BF16X3 modes (defaults, and the environment variables, read here,
+ * that keep an earlier kernel for A/B comparisons):
+ *   - chi0 on CTA pairs (tcgen05 cta_group::2, 256 x 128 tiles); GWC_CHI0_KERNEL=single keeps the
+ *     one-CTA 128 x 128 kernel.
+ *   - complex dielectric matrices factored per 64-column panel: one panel launch (one CTA per
+ *     matrix) and one batched tcgen05 trailing update over all matrices (3xTF32, FP32-accurate),
+ *     panels in pairs with a one-panel lookahead; GWC_FACTOR=tc keeps the one-CTA-per-matrix
+ *     tensor-core kernel, GWC_FACTOR=simt the FP32 SIMT kernel.
+ *   - imaginary-axis W table: real chi0 builds widened into complex storage, the same split
+ *     factorisation, and the forward substitution of the 33-node table as tcgen05 3xTF32 GEMMs
+ *     (explicit inverse of each 128-row diagonal block); GWC_WTABLE=simt keeps the SIMT solve. */
 gwc_status gwc_create(gwc_ctx** ctx, const gwc_system* sys, const gwc_options* opt, void* stream);
 
 /* Replaces the system of an existing context (serving slots): no device allocation. The new system
