@@ -949,14 +949,14 @@ def run_pentacene(args):
 def run_batch(args):
     """Batched form: molecules j = 0..M-1 (N_states ~ U{100..1300}, seed 1000 + j) generated on the GPU,
     each a request (decoupled spectra of all cores on the relative grid + Hedin QP), all captured into
-    one CUDA graph after autotuning the frequency batch per shape bucket."""
+    one CUDA graph after autotuning the frequency batch and the chi0 tile and launch shapes per shape bucket."""
     import numpy as np
     import torch
 
     from paper_2412_17132_gb300 import gwc, synth
 
     grid = np.linspace(-25.0 / HARTREE_EV, 5.0 / HARTREE_EV, args.omega_points)
-    ctxs, sizes, tuned, ctas_chosen = [], [], [], []
+    ctxs, sizes, tuned, ctas_chosen, tiles_chosen = [], [], [], [], []
     t_setup = time.perf_counter()
     for j in range(args.molecules):
         mol = synth.batch_member_device(j)
@@ -966,6 +966,7 @@ def run_batch(args):
         c.request_plan(grid)
         tuned.append(c.autotune())
         ctas_chosen.append(c.chi0_ctas())
+        tiles_chosen.append(c.chi0_tile())
         ctxs.append(c)
         sizes.append((c.n_states, c.n_aux, c.n_core))
         torch.cuda.empty_cache()
@@ -993,6 +994,7 @@ def run_batch(args):
                                   f"{args.omega_points}-point relative grid, cores = round(0.3 N_occ), QP = eps_n + dH_n",
                       "sizes_states_aux_cores": sizes, "autotuned_batch": tuned,
                       "autotuned_chi0_ctas": ctas_chosen,
+                      "autotuned_chi0_tile": tiles_chosen,
                       "form": ("grouped: per residue chunk one grouped chi0 launch and one grouped LDL^T launch over "
                                "all molecules (" + batch.chi0_shape + "), in one CUDA graph")
                       if batch.grouped else "graph of per-molecule steps on forked streams",

@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define GWC_ABI_VERSION 2
+#define GWC_ABI_VERSION 3
 
 typedef enum {
   GWC_OK = 0,
@@ -117,6 +117,10 @@ typedef struct {
                             CTA pair) per (tile, frequency group) item; > 0 at most that many
                             CTAs, each looping over the items (persistent). gwc_autotune may
                             change it */
+  int chi0_tile;         /* tile shape of the tensor-core polarizability build: 0 256 x 128 tiles
+                            on CTA pairs (tcgen05 cta_group::2), 1 128 x 128 tiles on one CTA
+                            each (less padding of the triangle at small N_aux, a lower MMA rate
+                            per SM). gwc_autotune may change it                                */
 } gwc_options;
 
 /* GWC_QP_SECANT: iterate the G_dH W0 QP equation (eq quasiparticle_equation with the shifted
@@ -162,8 +166,8 @@ gwc_status gwc_workspace_bytes(const gwc_system* sys, const gwc_options* opt, in
  * largest request of a class); the other entry points return GWC_ERR_INVALID_ARG until then.
  * Kernel choice of the BF16 and BF16X3 modes (defaults, and the environment variables, read here,
  * that keep an earlier kernel for A/B comparisons):
- *   - chi0 on CTA pairs (tcgen05 cta_group::2, 256 x 128 tiles); GWC_CHI0_KERNEL=single keeps the
- *     one-CTA 128 x 128 kernel.
+ *   - chi0 on CTA pairs (tcgen05 cta_group::2, 256 x 128 tiles) unless gwc_options.chi0_tile = 1;
+ *     GWC_CHI0_KERNEL=single sets chi0_tile = 1 (the one-CTA 128 x 128 kernel).
  *   - complex dielectric matrices factored per 64-column panel: one panel launch (one CTA per
  *     matrix) and one batched tcgen05 trailing update over all matrices (3xTF32, FP32-accurate),
  *     panels in pairs with a one-panel lookahead; GWC_FACTOR=tc keeps the one-CTA-per-matrix
@@ -365,12 +369,13 @@ gwc_status gwc_request_results_get(const gwc_ctx* ctx, gwc_request_results* out)
 gwc_status gwc_request_copy_results(const gwc_ctx* ctx, double* eps_qp, double* dh, int* iters, double* im_sigma,
                                     double* a, double* nu, void* stream);
 
-/* Launch shape chosen by timing one residue batch (chi0 build, factorisation and contraction of that many
- * frequencies) per candidate: frequencies per batch 16, 32, ... up to one SM wave, whole SM waves and the
- * capacity the context was created with, each with the polarizability build as one CTA per tile item and
- * as a persistent launch of one CTA per SM; the lowest time per frequency wins (cached per shape bucket
- * and precision for the process). Needs a request plan; synchronises `stream`; *chosen receives the batch
- * now used (the chi0 launch shape is in the context's options, gwc_options.chi0_ctas). */
+/* Launch and tile shapes chosen by timing one residue batch (chi0 build, factorisation and contraction of
+ * that many frequencies) per candidate: frequencies per batch 16, 32, ... up to one SM wave, whole SM waves
+ * and the capacity the context was created with; in the tensor-core modes each with both chi0 tile shapes
+ * (256 x 128 on CTA pairs, 128 x 128 on one CTA) and both launch shapes (one CTA or pair per tile item, a
+ * persistent launch of one per SM); the lowest time per frequency wins (cached per shape bucket and
+ * precision for the process). Needs a request plan; synchronises `stream`; *chosen receives the batch now
+ * used (the chi0 shapes are in the context's options, gwc_options.chi0_ctas and chi0_tile). */
 gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen);
 
 /* ---- Batched form: many molecules of uneven size in one CUDA-graph launch ----------------------
@@ -400,7 +405,8 @@ int gwc_batch_is_grouped(const gwc_batch* batch);
  * the persistent chi0 launch, [2] grouped pipelined with one CTA per chi0 item; -1 for a plan not tried. */
 gwc_status gwc_batch_timings(const gwc_batch* batch, float* ms3);
 
-/* The options the context runs with (as created, with what gwc_autotune chose). */
+/* The options the context runs with (as created, with what gwc_autotune chose; chi0_tile reads 1 when the
+ * environment variable GWC_CHI0_KERNEL=single was set at creation). */
 gwc_status gwc_get_options(const gwc_ctx* ctx, gwc_options* out);
 
 /* Synchronises `stream` and reports the first device-side status raised since the

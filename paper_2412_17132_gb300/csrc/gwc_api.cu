@@ -213,6 +213,7 @@ gwc_status validate_options(const gwc_options* o, int n_core) {
   if (o->qp_mode < 0 || o->qp_mode > 2) return fail(nullptr, GWC_ERR_INVALID_ARG, "bad qp_mode");
   if (o->wait_us < 0 || o->wait_us > 60000000) return fail(nullptr, GWC_ERR_INVALID_ARG, "wait_us must be in 0..6e7");
   if (o->chi0_ctas < 0) return fail(nullptr, GWC_ERR_INVALID_ARG, "chi0_ctas must be >= 0");
+  if (o->chi0_tile < 0 || o->chi0_tile > 1) return fail(nullptr, GWC_ERR_INVALID_ARG, "chi0_tile must be 0 or 1");
   (void)n_core;
   return GWC_OK;
 }
@@ -618,6 +619,7 @@ gwc_status gwc_default_options(gwc_options* o) {
   o->qp_mode = GWC_QP_SECANT;
   o->wait_us = 0;
   o->chi0_ctas = 0;
+  o->chi0_tile = 0;
   return GWC_OK;
 }
 
@@ -651,10 +653,6 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
     const char* fe = std::getenv("GWC_FACTOR");
     ctx->factor_tc = !(fe && std::strcmp(fe, "simt") == 0);
     ctx->factor_split = ctx->factor_tc && !(fe && std::strcmp(fe, "tc") == 0);
-    // tensor-core chi0 kernel: CTA pairs (cta_group::2, 256 x 128 tiles); GWC_CHI0_KERNEL=single keeps the
-    // one-CTA 128 x 128 kernel (A/B measurements)
-    const char* ck = std::getenv("GWC_CHI0_KERNEL");
-    ctx->chi0_pair = !(ck && std::strcmp(ck, "single") == 0);
   }
   ctx->n_states = s->n_states;
   ctx->n_occ = s->n_occ;
@@ -663,6 +661,12 @@ gwc_status gwc_create(gwc_ctx** out, const gwc_system* s, const gwc_options* o, 
   ctx->n_core = s->n_core;
   ctx->n_ov = s->n_occ * ctx->n_virt;
   ctx->opt = *o;
+  {
+    // GWC_CHI0_KERNEL=single keeps the one-CTA 128 x 128 chi0 kernel whatever the options say (A/B measurements)
+    const char* ck = std::getenv("GWC_CHI0_KERNEL");
+    if (ck && std::strcmp(ck, "single") == 0) ctx->opt.chi0_tile = 1;
+    ctx->chi0_pair = ctx->opt.chi0_tile == 0;
+  }
   ctx->wait_ns = o->wait_us > 0 ? 1000ull * (unsigned long long)o->wait_us : 1000000000ull;
   if (o->group_of_core) ctx->h_group.assign(o->group_of_core, o->group_of_core + s->n_core);
   ctx->opt.group_of_core = nullptr;
@@ -1472,24 +1476,36 @@ gwc_status gwc_request_copy_results(const gwc_ctx* ctx, double* eps_qp, double* 
   return GWC_OK;
 }
 
-// ---- autotuner: frequencies per batch, timed on the request step, cached per shape bucket ------------
+// ---- autotuner: frequencies per batch and chi0 tile/launch shapes, timed on residue batches, cached per shape bucket
 namespace {
 std::mutex g_tune_mutex;
-// (n_aux/128, n_ov/4096, n_core, prec) -> (frequencies per batch, chi0 CTAs: 0 one per item, else persistent)
-std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
+struct TuneChoice {
+  int batch;      // frequencies per batch
+  int chi0_ctas;  // 0: one CTA (pair) per chi0 item, else persistent
+  int chi0_tile;  // 0: 256 x 128 pair tiles, 1: 128 x 128 one-CTA tiles
+};
+// (n_aux/128, n_ov/4096, n_core, prec, tile shapes allowed) -> choice
+std::map<std::tuple<int, int, int, int, int>, TuneChoice> g_tune_cache;
 }  // namespace
 
 gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
   if (!ctx) return fail(nullptr, GWC_ERR_INVALID_ARG, "ctx is NULL");
   if (ctx->req_n_omega <= 0) return fail(ctx, GWC_ERR_INVALID_ARG, "no request plan (call gwc_request_plan first)");
   cudaStream_t st = (cudaStream_t)stream;
-  const auto key = std::make_tuple((ctx->n_aux + 127) / 128, (ctx->n_ov + 4095) / 4096, ctx->n_core, ctx->opt.prec);
+  const bool tc = ctx->opt.prec == GWC_PREC_BF16 || ctx->opt.prec == GWC_PREC_BF16X3 || ctx->opt.prec == GWC_PREC_BF16X3_F64;
+  // both tile shapes are candidates unless GWC_CHI0_KERNEL=single pinned the one-CTA kernel
+  const char* ck = std::getenv("GWC_CHI0_KERNEL");
+  const bool both_tiles = tc && !(ck && std::strcmp(ck, "single") == 0);
+  const auto key = std::make_tuple((ctx->n_aux + 127) / 128, (ctx->n_ov + 4095) / 4096, ctx->n_core, ctx->opt.prec,
+                                   both_tiles ? 2 : 1);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      ctx->batch = std::min(it->second.first, ctx->batch_cap);
-      ctx->opt.chi0_ctas = it->second.second;
+      ctx->batch = std::min(it->second.batch, ctx->batch_cap);
+      ctx->opt.chi0_ctas = it->second.chi0_ctas;
+      ctx->opt.chi0_tile = it->second.chi0_tile;
+      ctx->chi0_pair = ctx->opt.chi0_tile == 0;
       if (chosen) *chosen = ctx->batch;
       return GWC_OK;
     }
@@ -1510,15 +1526,17 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
   for (int f = ctx->n_sm; f < ctx->batch_cap; f += ctx->n_sm) cands.push_back(f);
   cands.push_back(ctx->batch_cap);
   const int np = ctx->req_n_pairs;
-  const bool tc = ctx->opt.prec == GWC_PREC_BF16 || ctx->opt.prec == GWC_PREC_BF16X3 || ctx->opt.prec == GWC_PREC_BF16X3_F64;
-  const int saved_ctas = ctx->opt.chi0_ctas;
-  int best_ctas = saved_ctas;
+  const int saved_ctas = ctx->opt.chi0_ctas, saved_tile = ctx->opt.chi0_tile;
+  int best_ctas = saved_ctas, best_tile = saved_tile;
   for (int f : cands) {
     if (res != GWC_OK || np <= 0) break;
     const int nb = std::min(f, np);
     ctx->batch = nb;
-    for (int shape = 0; shape < (tc ? 2 : 1) && res == GWC_OK; ++shape) {
+    for (int cand = 0; cand < (tc ? (both_tiles ? 4 : 2) : 1) && res == GWC_OK; ++cand) {
+      const int shape = cand & 1;
       ctx->opt.chi0_ctas = tc ? (shape == 0 ? 0 : ctx->n_sm) : saved_ctas;
+      ctx->opt.chi0_tile = both_tiles ? (cand >> 1) : saved_tile;
+      ctx->chi0_pair = ctx->opt.chi0_tile == 0;
       res = residue_batches(ctx, nb, ctx->d_req_z, ctx->d_req_rows, ctx->n_core, ctx->d_req_w, nullptr, st);
       if (res != GWC_OK) break;
       cudaEventRecord(e0, st);
@@ -1532,6 +1550,7 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
         best_per = per;
         best = f;
         best_ctas = ctx->opt.chi0_ctas;
+        best_tile = ctx->opt.chi0_tile;
       }
     }
     if (nb < f) break;  // fewer pairs than the candidate: larger batches change nothing
@@ -1541,10 +1560,12 @@ gwc_status gwc_autotune(gwc_ctx* ctx, void* stream, int* chosen) {
   ctx->opt.profile = saved_profile;
   ctx->batch = best;
   ctx->opt.chi0_ctas = best_ctas;
+  ctx->opt.chi0_tile = best_tile;
+  ctx->chi0_pair = best_tile == 0;
   if (res != GWC_OK) return res;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = std::make_pair(best, best_ctas);
+    g_tune_cache[key] = TuneChoice{best, best_ctas, best_tile};
   }
   if (chosen) *chosen = best;
   return GWC_OK;

@@ -54,6 +54,9 @@ class System(ctypes.Structure):
     ]
 
 
+ABI_VERSION = 3  # GWC_ABI_VERSION of the gwc.h these structures mirror
+
+
 class Options(ctypes.Structure):
     _fields_ = [
         ("eta", ctypes.c_double),
@@ -71,6 +74,7 @@ class Options(ctypes.Structure):
         ("qp_mode", ctypes.c_int),
         ("wait_us", ctypes.c_int),
         ("chi0_ctas", ctypes.c_int),
+        ("chi0_tile", ctypes.c_int),
     ]
 
 
@@ -148,6 +152,8 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        if L.gwc_abi_version() != ABI_VERSION:  # the structures below mirror this version's layout
+            raise RuntimeError(f"libgwc.so has ABI {L.gwc_abi_version()}, this binding {ABI_VERSION}: rebuild it")
         _LIB = L
     return _LIB
 
@@ -239,7 +245,7 @@ class Context:
 
     def __init__(self, eps, n_occ, core_idx, o_ov, o_core, *, vxc=None, eps_f=math.nan, eta=1e-3, n_im=32, xi0=1.0,
                  prec="bf16x3", dec="diag", groups=None, n_t=1 << 16, t_max=2000.0, max_qp_iter=50, qp_tol=1e-7,
-                 batch=0, profile=False, qp_mode="secant", wait_us=0, chi0_ctas=0, stream=None):
+                 batch=0, profile=False, qp_mode="secant", wait_us=0, chi0_ctas=0, chi0_tile=0, stream=None):
         self._ctx = ctypes.c_void_p()
         host = isinstance(eps, np.ndarray)
         self._keep = []
@@ -263,6 +269,7 @@ class Context:
         opt.qp_mode = QP[qp_mode]
         opt.wait_us = int(wait_us)
         opt.chi0_ctas = int(chi0_ctas)
+        opt.chi0_tile = int(chi0_tile)
         self.opt = opt
         self.prec = prec
         _check(lib().gwc_create(ctypes.byref(self._ctx), ctypes.byref(sysd), ctypes.byref(opt), _stream(stream)), None)
@@ -469,6 +476,13 @@ class Context:
         o = Options()
         _check(lib().gwc_get_options(self._ctx, ctypes.byref(o)), self._ctx)
         return o.chi0_ctas
+
+    def chi0_tile(self) -> int:
+        """The context's polarizability tile shape (gwc_options.chi0_tile: 0 256 x 128 CTA-pair tiles, 1 128 x 128
+        one-CTA tiles) after gwc_autotune."""
+        o = Options()
+        _check(lib().gwc_get_options(self._ctx, ctypes.byref(o)), self._ctx)
+        return o.chi0_tile
 
     def sync(self, stream=None):
         _check(lib().gwc_sync(self._ctx, _stream(stream)), self._ctx)

@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(libgwc):
 
 
 def test_abi_version_and_strings(libgwc):
-    assert libgwc.gwc_abi_version() == 2
+    assert libgwc.gwc_abi_version() == 3
     assert libgwc.gwc_status_string(4) == b"singular dielectric matrix"
 
 
@@ -54,6 +54,7 @@ def test_default_options(libgwc):
 
     o = gwc.default_options()
     assert o.eta == 1e-3 and o.n_im == 32 and o.n_t == 1 << 16 and o.prec == gwc.PREC["bf16x3"]
+    assert o.chi0_ctas == 0 and o.chi0_tile == 0
 
 
 def _sys(n_states=20, n_occ=4, n_aux=10, n_core=1, core=None):
@@ -94,7 +95,8 @@ def test_create_rejects_bad_sizes_without_gpu(libgwc, kw):
     assert libgwc.gwc_last_error(None)
 
 
-@pytest.mark.parametrize("field,val", [("eta", 0.0), ("n_im", 0), ("n_t", 1000), ("max_qp_iter", 1), ("prec", 9)])
+@pytest.mark.parametrize("field,val", [("eta", 0.0), ("n_im", 0), ("n_t", 1000), ("max_qp_iter", 1), ("prec", 9),
+                                       ("chi0_ctas", -1), ("chi0_tile", 2), ("chi0_tile", -1)])
 def test_create_rejects_bad_options_without_gpu(libgwc, field, val):
     from paper_2412_17132_gb300 import gwc
 

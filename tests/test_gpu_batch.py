@@ -111,12 +111,27 @@ def test_autotune_picks_a_valid_batch(gwc):
     chosen = ctx.autotune()
     assert chosen in (16, 32, 64, 128)
     assert ctx.chi0_ctas() in (0, torch.cuda.get_device_properties(0).multi_processor_count)
+    tile = ctx.chi0_tile()
+    assert tile in (0, 1)
     ctx.request_step()
     ctx.sync()
+    eq, dh, _, im, _, _ = [t.cpu().numpy() for t in ctx.request_results()]
     # the second context of the same shape bucket reuses the cached choice
     ctx2 = gwc.Context.from_molecule(mol, prec="bf16x3", qp_mode="hedin", batch=128)
     ctx2.request_plan(_rel_grid())
     assert ctx2.autotune() == chosen
+    assert ctx2.chi0_tile() == tile and ctx2.chi0_ctas() == ctx.chi0_ctas()
+    # the other tile shape gives the same step (both FP32-accurate; only the summation order differs)
+    ctx3 = gwc.Context.from_molecule(mol, prec="bf16x3", qp_mode="hedin", batch=128, chi0_tile=1 - tile)
+    assert ctx3.chi0_tile() == 1 - tile
+    ctx3.request_plan(_rel_grid())
+    ctx3.request_step()
+    ctx3.sync()
+    eq3, dh3, _, im3, _, _ = [t.cpu().numpy() for t in ctx3.request_results()]
+    assert np.max(np.abs(dh3 - dh)) <= 1e-5 * max(1.0, np.max(np.abs(dh)))
+    assert np.max(np.abs(im3 - im)) <= 1e-4 * np.max(np.abs(im))
+    for c in (ctx, ctx2, ctx3):
+        c.close()
 
 
 def test_persistent_chi0_equals_one_cta_per_item(gwc):

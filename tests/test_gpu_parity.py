@@ -119,6 +119,30 @@ def test_chi0_both_tensor_core_kernels(gwc, monkeypatch, kernel, n_aux, n_states
     ctx.close()
 
 
+def test_chi0_tile_option_selects_the_kernel(gwc, monkeypatch):
+    """gwc_options.chi0_tile picks the 256 x 128 CTA-pair tiles (0) or the 128 x 128 one-CTA tiles (1); both
+    match the oracle, and GWC_CHI0_KERNEL=single overrides the option at creation."""
+    monkeypatch.delenv("GWC_CHI0_KERNEL", raising=False)
+    mol = synth.small(n_states=37, n_occ=9, n_core=1, n_aux=300, seed=311)
+    zs = [complex(0.0, 1.1), complex(2.3, 1e-3)]
+    z = torch.tensor([[v.real, v.imag] for v in zs], dtype=torch.float64, device="cuda")
+    delta = G.transition_energies(mol.eps, mol.n_occ)
+    for tile in (0, 1):
+        ctx = gwc.Context.from_molecule(mol, prec="bf16x3", chi0_tile=tile)
+        assert ctx.chi0_tile() == tile
+        out = _cplx(ctx.build_chi0(z))
+        assert ctx.sync_status() == 0
+        for f, v in enumerate(zs):
+            dv = G.d_factor(delta, v)
+            absterm = np.abs(mol.o_ov) @ (np.abs(dv)[:, None] * np.abs(mol.o_ov).T)
+            assert np.max(np.abs(out[f] - G.chi0(mol.o_ov, delta, v))) <= 2e-5 * np.max(absterm)
+        ctx.close()
+    monkeypatch.setenv("GWC_CHI0_KERNEL", "single")
+    ctx = gwc.Context.from_molecule(mol, prec="bf16x3", chi0_tile=0)
+    assert ctx.chi0_tile() == 1
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 1e-4), ("bf16x3", 2e-3), ("bf16x3f64", 2e-3)])
 def test_screen_matches_oracle(gwc, tiny, prec, tol):
     ctx = gwc.Context.from_molecule(tiny, prec=prec)
