@@ -1,10 +1,12 @@
-"""Per-kernel timing of the three dominant kernels through the C-ABI, at a chosen width.
+"""Per-kernel timing of the three dominant kernel groups through the C-ABI, at a chosen width.
 
-The polarizability build (chi0_tc_kernel), the complex-symmetric factorisation (ldlt_tc_kernel) and the
-W-table forward substitution (ldlt_solve_kernel) of one context, timed by the library's own CUDA events
-(`profile=True`): `gwc_screen` on `--freqs` complex frequencies z = w + i eta per call (one chi0 launch,
-one LDL^T launch, one border solve), then one imaginary-axis W table (the real chi0 build, the real
-factorisation and the 33-node solve). The default width is the pentacene-sized one (N_aux = 4500,
+The polarizability build (chi0_pair_kernel, or chi0_tc_kernel with GWC_CHI0_KERNEL=single), the
+complex-symmetric factorisation (per 64-column panel: ldlt_panel_kernel, ldlt_planes_kernel and the
+batched ldlt_update_kernel; GWC_FACTOR=tc the one-CTA ldlt_tc_kernel) and the W-table forward
+substitution (wtable_gemm_kernel; GWC_WTABLE=simt the SIMT ldlt_solve_kernel) of one context, timed by
+the library's own CUDA events (`profile=True`): `gwc_screen` on `--freqs` complex frequencies
+z = w + i eta per call (one chi0 launch, one factorisation, one border solve), then one imaginary-axis
+W table (the real chi0 builds, the factorisations and the 33-node solve). The default width is the pentacene-sized one (N_aux = 4500,
 N_occ = 73) with fewer virtual states (N_states = 350: N_ov = 20 221), so that a launch holds a few GB
 and profiles in seconds; `--n-states 1300` gives the full pentacene N_ov = 89 571.
 
