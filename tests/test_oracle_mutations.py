@@ -207,3 +207,52 @@ def test_wac_valence_margins_swapped(monkeypatch):
 
     monkeypatch.setattr(G, "wac_reference_points", ref)
     _fails(P.test_wac_reference_points_follow_the_printed_parameters)
+
+
+def test_continued_fraction_with_the_wrong_reference_point(monkeypatch):
+    def ev(a, zref, z):  # level p paired with z_p instead of z_{p-1}
+        z = np.asarray(z, dtype=np.complex128)
+        t = np.ones_like(z)
+        for p in range(a.size - 1, 0, -1):
+            t = 1.0 + a[p] * (z - zref[min(p, zref.size - 1)]) / t
+        return a[0] / t
+
+    monkeypatch.setattr(G, "thiele_eval", ev)
+    _fails(P.test_thiele_interpolates_and_reproduces_rational_functions)
+
+
+def test_g0w0_renormalisation_with_the_slope_sign_flipped(monkeypatch):
+    orig = G.g0w0_graphical_solutions
+
+    def sols(*args):  # Z = 1/(1 + dRe Sigma/dw) instead of 1/(1 - dRe Sigma/dw)
+        return [(x, 1.0 / (2.0 - 1.0 / z)) for x, z in orig(*args)]
+
+    monkeypatch.setattr(G, "g0w0_graphical_solutions", sols)
+    _fails(P.test_g0w0_graphical_solutions_single_pole_closed_form)
+
+
+def test_beta_without_the_one_over_pi(monkeypatch):
+    def spectrum(omega_rel, im_sigma, eta, n_t, t_max, direct=False):  # beta = |Im Sigma|, 1/pi dropped
+        dt = t_max / n_t
+        ct = G.cumulant_ct(omega_rel, np.abs(im_sigma), dt * np.arange(n_t))
+        return G.spectrum_from_cumulant(ct, dt, eta, direct=direct)
+
+    monkeypatch.setattr(G, "gwc_spectrum", spectrum)
+    _fails(P.test_spectrum_poisson_closed_form, 0.5)
+
+
+def test_exchange_summed_over_every_state(monkeypatch):
+    monkeypatch.setattr(G.System, "sigma_x", lambda self: -np.einsum("icp,icp->c", self.o_core, self.o_core))
+    _fails(P.test_sigma_x_brute_force)
+
+
+def test_residue_prefactor_with_the_occupations_swapped(monkeypatch):
+    orig = G.residue_prefactor
+    monkeypatch.setattr(G, "residue_prefactor", lambda eps_m, omega, eps_f: -orig(eps_m, omega, eps_f))
+    _fails(P.test_sigma_cd_matches_time_ordered_sop, _small_sop())
+
+
+def test_pair_response_at_the_conjugate_frequency(monkeypatch):
+    orig = G.d_factor
+    monkeypatch.setattr(G, "d_factor", lambda delta, z: orig(delta, np.conj(complex(z))))
+    _fails(P.test_w_ri_solve_equals_sum_over_poles, _small_sop(), 2.5 + 1e-3j)
