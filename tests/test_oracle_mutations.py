@@ -256,3 +256,16 @@ def test_pair_response_at_the_conjugate_frequency(monkeypatch):
     orig = G.d_factor
     monkeypatch.setattr(G, "d_factor", lambda delta, z: orig(delta, np.conj(complex(z))))
     _fails(P.test_w_ri_solve_equals_sum_over_poles, _small_sop(), 2.5 + 1e-3j)
+
+
+def test_w_rebuilt_from_the_g_energies(monkeypatch):
+    orig = G.System.with_g_energies
+
+    def with_g(self, eps_g, eps_f=None):  # evGW instead of evGW0: W from the QP energies too
+        other = orig(self, eps_g, eps_f)
+        other.delta = G.transition_energies(other.eps_g, self.n_occ)
+        other._w_im = None
+        return other
+
+    monkeypatch.setattr(G.System, "with_g_energies", with_g)
+    _fails(P.test_evgw0_sigma_matches_sum_over_poles_with_qp_energies)
