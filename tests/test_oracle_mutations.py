@@ -269,3 +269,17 @@ def test_w_rebuilt_from_the_g_energies(monkeypatch):
 
     monkeypatch.setattr(G.System, "with_g_energies", with_g)
     _fails(P.test_evgw0_sigma_matches_sum_over_poles_with_qp_energies)
+
+
+def test_trapezoid_endpoints_with_full_weight(monkeypatch):
+    def weights(omega):  # interior rule at the ends too: w_0 = d_0 and w_{n-1} = d_{n-2}
+        d = np.diff(omega)
+        w = np.zeros_like(omega)
+        w[:-1] += 0.5 * d
+        w[1:] += 0.5 * d
+        w[0] += 0.5 * d[0]
+        w[-1] += 0.5 * d[-1]
+        return w
+
+    monkeypatch.setattr(G, "trapezoid_weights", weights)
+    _fails(P.test_trapezoid_weights_integrate_linear_functions_exactly)

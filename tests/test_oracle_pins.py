@@ -465,6 +465,18 @@ def test_group_decoupling_uses_each_members_own_residue_frequency():
 # ----------------------------------------------------------------------------------------
 
 
+def test_trapezoid_weights_integrate_linear_functions_exactly():
+    # the Landau integral's quadrature (Eq. landau_cumulant_truncated) on a non-uniform grid: exact for
+    # a + b w, so the weights sum to the grid's length and their first moment is (w_max^2 - w_min^2)/2
+    rng = np.random.default_rng(17)
+    w = np.sort(rng.uniform(-1.3, 0.4, 57))
+    wq = G.trapezoid_weights(w)
+    lo, hi = w[0], w[-1]
+    assert abs(np.sum(wq) - (hi - lo)) < 1e-14
+    assert abs(np.sum(wq * (0.7 - 2.1 * w)) - (0.7 * (hi - lo) - 2.1 * (hi**2 - lo**2) / 2)) < 1e-13
+    assert np.all(wq > 0)
+
+
 def test_sigma_x_brute_force():
     m = synth.small(n_states=10, n_occ=4, n_core=2, n_aux=6, seed=2)
     s = G.System.from_molecule(m)
