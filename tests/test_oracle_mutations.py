@@ -283,3 +283,36 @@ def test_trapezoid_endpoints_with_full_weight(monkeypatch):
 
     monkeypatch.setattr(G, "trapezoid_weights", weights)
     _fails(P.test_trapezoid_weights_integrate_linear_functions_exactly)
+
+
+def test_near_pole_subtraction_without_its_sign(monkeypatch):
+    def imag_axis_term(self, omega):  # + W(i0)/2 whatever the side of the pole, instead of sgn(a) W(i0)/2
+        tab, w0 = self.w_imag_table()
+        out = np.zeros(self.n_core)
+        for m in range(self.n_states):
+            a = omega - self.eps_g[m]
+            if a == 0.0:
+                continue
+            kern = self.w_xi * a / (a * a + self.xi**2) / math.pi
+            out += kern @ (tab[:, m, :] - w0[m][None, :]) + 0.5 * w0[m]
+        return out
+
+    monkeypatch.setattr(G.System, "imag_axis_term", imag_axis_term)
+    _fails(P.test_sigma_cd_matches_time_ordered_sop, _small_sop())
+
+
+def test_residue_frequency_without_its_absolute_value(monkeypatch):
+    def residue_term(self, omega):  # W at (eps_m - w) + i eta, negative below the state
+        out = np.zeros(self.n_core, dtype=np.complex128)
+        per_m = {}
+        for m in range(self.n_states):
+            f = G.residue_prefactor(self.eps_g[m], omega, self.eps_f)
+            if f == 0.0:
+                continue
+            w = self.w_residue(m, self.eps_g[m] - omega)
+            per_m[m] = (f, w)
+            out += f * w
+        return out, per_m
+
+    monkeypatch.setattr(G.System, "residue_term", residue_term)
+    _fails(P.test_sigma_cd_matches_time_ordered_sop, _small_sop())

@@ -139,7 +139,10 @@ def test_sigma_cd_matches_time_ordered_sop(small_sop):
     m, _, om, _, rho = small_sop
     s = G.System.from_molecule(m, n_im=800)
     eps_f = s.eps_f
-    for w in (m.eps[0] - 0.9, m.eps[0] - 0.31, m.eps[0] + 0.05):
+    # below and at the core level (occupied residues), and above virtual levels (virtual residues; the
+    # last one excites the lowest RPA pole through the residue of the lowest virtual state)
+    for w in (m.eps[0] - 0.9, m.eps[0] - 0.31, m.eps[0] + 0.05, m.eps[m.n_occ] + 0.05, m.eps[m.n_occ + 2] + 0.3,
+              m.eps[m.n_occ] + float(np.min(om))):
         cd = s.sigma_c(float(w))[0][0]
         sp = S.sigma_c_sop(m.eps, eps_f, rho, om, float(w), m.eta)
         bound = sum(np.sum(rho[mm] ** 2 * 2 * m.eta / (abs(m.eps[mm] - w) + om) ** 2) for mm in range(m.n_states))
