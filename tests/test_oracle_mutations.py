@@ -316,3 +316,21 @@ def test_residue_frequency_without_its_absolute_value(monkeypatch):
 
     monkeypatch.setattr(G.System, "residue_term", residue_term)
     _fails(P.test_sigma_cd_matches_time_ordered_sop, _small_sop())
+
+
+def test_group_members_with_the_cores_prefactor(monkeypatch):
+    def grp(self, omega, groups, cores=None):  # f of core n for every member instead of each member's own f_i
+        groups = [int(g) for g in groups]
+        out = np.zeros(self.n_core)
+        todo = range(self.n_core) if cores is None else [int(c) for c in cores]
+        for c in todo:
+            f = G.residue_prefactor(self.eps_g[self.core_idx[c]], omega, self.eps_f)
+            for c2, i in enumerate(self.core_idx):
+                if groups[c2] != groups[c] or f == 0.0:
+                    continue
+                pi = G.chi0(self.o_ov, self.delta, complex(abs(self.eps_g[i] - omega), self.eta))
+                out[c] += f * G.screened_wc(pi, self.o_core[int(i), c][:, None])[0].imag
+        return out
+
+    monkeypatch.setattr(G.System, "im_sigma_dec_group", grp)
+    _fails(P.test_group_decoupling_uses_each_members_own_prefactor)
