@@ -334,3 +334,14 @@ def test_group_members_with_the_cores_prefactor(monkeypatch):
 
     monkeypatch.setattr(G.System, "im_sigma_dec_group", grp)
     _fails(P.test_group_decoupling_uses_each_members_own_prefactor)
+
+
+def test_gdh_spectrum_without_the_static_part(monkeypatch):
+    def gdh(omega_common, sigma_c, eps_n, dh, sigma_x, vxc):  # v^xc - Sigma^x left out of the denominator
+        w = omega_common + dh
+        re = w - eps_n - sigma_c.real
+        im = sigma_c.imag
+        return w, np.abs(im) / (re * re + im * im) / math.pi
+
+    monkeypatch.setattr(G, "gdh_spectrum", gdh)
+    _fails(P.test_gw_spectral_function_of_the_three_level_model, 0.2)

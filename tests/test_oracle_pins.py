@@ -526,16 +526,19 @@ def test_peak_finder_on_parabola():
 # ----------------------------------------------------------------------------------------
 
 
-def test_gw_spectral_function_of_the_three_level_model():
-    # With Sigma^c(w) = rho^2/(w - eps_c + Omega - i eta) (eq sigma_spectral for the model) and
-    # v^xc = Sigma^x, G has the two poles x = (-Omega +- sqrt(Omega^2 + 4 rho^2))/2 (x = w - eps_c):
-    # one QP peak and one satellite below it, with weights (x_+ + Omega)/(x_+ - x_-) and the rest.
-    om, rho, eta, ec = 0.5, 0.2, 1e-4, -10.0
+@pytest.mark.parametrize("static", [0.0, 0.2])
+def test_gw_spectral_function_of_the_three_level_model(static):
+    # With Sigma^c(w) = rho^2/(w - eps_c + Omega - i eta) (eq sigma_spectral for the model) and a static
+    # part s = Sigma^x - v^xc, G has the two poles x (x = w - eps_c) with (x - s)(x + Omega) = rho^2,
+    # x = (-(Omega - s) +- sqrt((Omega - s)^2 + 4 (s Omega + rho^2)))/2: one QP peak and one satellite
+    # below it, with weights (x_+ + Omega)/(x_+ - x_-) and the rest. eta = 1e-3 makes the QP peak's width
+    # Z rho^2 eta/(x_+ + Omega)^2 several grid steps wide, so that the sums over the grid hold its mass.
+    om, rho, eta, ec = 0.5, 0.2, 1e-3, -10.0
     w = np.linspace(ec - 1.5, ec + 0.5, 200001)
     sig = rho**2 / (w - ec + om - 1j * eta)
-    ww, a = G.gdh_spectrum(w, sig, ec, 0.0, -3.0, -3.0)
-    disc = math.sqrt(om * om + 4 * rho * rho)
-    xp, xm = (-om + disc) / 2, (-om - disc) / 2
+    ww, a = G.gdh_spectrum(w, sig, ec, 0.0, -3.0, -3.0 - static)
+    disc = math.sqrt((om - static) ** 2 + 4 * (static * om + rho * rho))
+    xp, xm = (-(om - static) + disc) / 2, (-(om - static) - disc) / 2
     pk = sorted(p for p, h in G.find_peaks(ww - ec, a, 1e-3))
     assert len(pk) == 2
     assert abs(pk[1] - xp) < 2e-5 and abs(pk[0] - xm) < 2e-5
