@@ -402,6 +402,28 @@ def test_gdh_spectral_function_matches_oracle(gwc, tiny, tiny_oracle):
     assert np.max(np.abs(a[0].cpu().numpy() - a_ref)) <= 1e-6 * np.max(a_ref)
 
 
+def test_gdh_spectral_function_with_vxc_matches_oracle(gwc):
+    """The same with v^xc given (a static part Sigma^x - v^xc in G's denominator), three cores, FP64 path."""
+    mol = synth.small(n_states=40, n_occ=6, n_core=3, n_aux=50, seed=17)
+    vxc = np.array([-0.4, -0.35, -0.3])
+    ctx = gwc.Context(torch.as_tensor(mol.eps, device="cuda"), mol.n_occ, mol.core_idx, torch.as_tensor(mol.o_ov, device="cuda"),
+                      torch.as_tensor(mol.o_core, device="cuda"), vxc=torch.as_tensor(vxc, device="cuda"), prec="fp64",
+                      eta=mol.eta, n_im=mol.n_im)
+    grid = np.linspace(float(mol.eps[mol.core_idx[0]]) - 1.0, float(mol.eps[mol.core_idx[0]]) + 0.2, 41)
+    sig, _, _ = ctx.sigma_core(grid)
+    _, dh, _ = ctx.qp_solve()
+    a, w = ctx.gdh_spectrum(torch.as_tensor(grid, device="cuda"), sig, dh)
+    ctx.sync()
+    s = G.System.from_molecule(mol, vxc=vxc)
+    ref_sig, _ = s.sigma_c_grid(grid)
+    dh_ref, sx = s.hedin_shift(), s.sigma_x()
+    assert abs(sx[0] - vxc[0]) > 0.05  # a static part is present
+    for c in range(3):
+        w_ref, a_ref = G.gdh_spectrum(grid, ref_sig[c], float(mol.eps[mol.core_idx[c]]), dh_ref[c], sx[c], vxc[c])
+        assert np.max(np.abs(w[c].cpu().numpy() - w_ref)) < 1e-9
+        assert np.max(np.abs(a[c].cpu().numpy() - a_ref)) <= 1e-6 * np.max(a_ref)
+
+
 def test_cdwac_exact_for_few_poles_and_matches_oracle(gwc):
     """CD-WAC on the GPU: equals CD (GPU) and the oracle's CD-WAC when W has few poles (the fit is exact)."""
     mol = synth.small(n_states=4, n_occ=2, n_core=1, n_aux=6, seed=13, n_high=1, n_omega=9)
