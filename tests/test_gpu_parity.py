@@ -322,6 +322,27 @@ def test_group_decoupling_fp64(gwc):
         assert np.max(np.abs(dec[:, j] - ref)) < 1e-9, (j, dec[:, j], ref)
 
 
+def test_group_decoupling_members_apart_fp64(gwc):
+    """Two group members 1.4 Ha apart: between them the lower member (its own prefactor 0) adds nothing,
+    although its residue frequency sits on the lowest RPA pole; below both, both members add."""
+    import test_oracle_pins as P
+    from oracle import sop as S
+
+    eps, n_occ, core_idx, o_ov, o_core, eta = P.two_members_apart_system()
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda").contiguous()  # noqa: E731
+    ctx = gwc.Context(dev(eps), n_occ, core_idx, dev(o_ov), dev(o_core), eta=eta, n_im=8, prec="fp64", dec="group",
+                      groups=[0, 0])
+    s = G.System(eps, n_occ, core_idx, o_ov, o_core, eta, n_im=8)
+    om, _ = S.casida_sop(s.o_ov, s.delta)
+    ws = np.array([eps[0] - 0.3, eps[0] + float(np.min(om)), 0.5 * (eps[0] + eps[1]), eps[1] - float(np.min(om))])
+    _, dec, _ = ctx.sigma_core(ws)
+    ctx.sync()
+    dec = dec.cpu().numpy()
+    for j, w in enumerate(ws):
+        ref = s.im_sigma_dec_group(float(w), [0, 0])
+        assert np.max(np.abs(dec[:, j] - ref)) < 1e-9 * max(1.0, np.max(np.abs(ref))), (j, dec[:, j], ref)
+
+
 def test_group_decoupling_mirrored_cores_fp64(gwc):
     """Two symmetry-equivalent (degenerate, mirrored) cores and a third one in its own group."""
     import test_oracle_pins as P

@@ -463,12 +463,10 @@ def test_group_decoupling_uses_each_members_own_residue_frequency():
         assert np.max(np.abs(got - s.sigma_c(float(w))[1])) > 1e-3 * np.max(np.abs(got))
 
 
-def test_group_decoupling_uses_each_members_own_prefactor():
-    # members 1.4 Ha apart: at w = eps_0 + Omega_0 (above member 0, below member 1) member 0 has f_0 = 0 and
-    # adds nothing, although its residue frequency |eps_0 - w| = Omega_0 sits on the lowest RPA pole; the
-    # prefactor of core 1 (f_1 = -1) applied to it would add a Lorentzian peak of height rho^2/eta
-    rng = np.random.default_rng(61)
-    n_states, n_occ, n_aux = 14, 5, 9
+def two_members_apart_system(seed=61, n_states=14, n_occ=5, n_aux=9):
+    """Two occupied cores (states 0 and 1) 1.4 Ha apart, one symmetry group; the lowest RPA pole lies
+    below their separation. Returns (eps, n_occ, core_idx, o_ov, o_core, eta)."""
+    rng = np.random.default_rng(seed)
     eps = np.sort(np.concatenate([[-10.4, -9.0], rng.uniform(-1.0, -0.25, n_occ - 2),
                                   rng.uniform(0.0, 3.0, n_states - n_occ)]))
     o = rng.normal(0.0, 0.05, (n_aux, n_states, n_states))
@@ -477,7 +475,15 @@ def test_group_decoupling_uses_each_members_own_prefactor():
     o[:, :, :2] *= 3.0
     o_ov = np.ascontiguousarray(o[:, :n_occ, n_occ:].reshape(n_aux, -1))
     o_core = np.ascontiguousarray(o[:, :, :2].transpose(1, 2, 0))
-    s = G.System(eps, n_occ, np.array([0, 1]), o_ov, o_core, 1e-3, n_im=8)
+    return eps, n_occ, np.array([0, 1]), o_ov, o_core, 1e-3
+
+
+def test_group_decoupling_uses_each_members_own_prefactor():
+    # members 1.4 Ha apart: at w = eps_0 + Omega_0 (above member 0, below member 1) member 0 has f_0 = 0 and
+    # adds nothing, although its residue frequency |eps_0 - w| = Omega_0 sits on the lowest RPA pole; the
+    # prefactor of core 1 (f_1 = -1) applied to it would add a Lorentzian peak of height rho^2/eta
+    eps, n_occ, core_idx, o_ov, o_core, eta = two_members_apart_system()
+    s = G.System(eps, n_occ, core_idx, o_ov, o_core, eta, n_im=8)
     om, _ = S.casida_sop(s.o_ov, s.delta)
     w = float(eps[0] + np.min(om))
     assert eps[0] < w < eps[1]
