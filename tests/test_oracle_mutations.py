@@ -345,3 +345,23 @@ def test_gdh_spectrum_without_the_static_part(monkeypatch):
 
     monkeypatch.setattr(G, "gdh_spectrum", gdh)
     _fails(P.test_gw_spectral_function_of_the_three_level_model, 0.2)
+
+
+def test_evgw0_without_the_fermi_level_check(monkeypatch):
+    def ev(system, tol=1e-8, max_iter=100, on_fail="return"):  # iterates on past a change of occupations
+        n = system.n_states
+        sx, vxc = system.sigma_x(), system.v_xc()
+        e = system.eps.copy()
+        for it in range(1, max_iter + 1):
+            s = system.with_g_energies(e)
+            new = np.array([system.eps[c] + sx[c] - vxc[c] + s.sigma_c(float(e[c]))[0][c].real for c in range(n)])
+            done = np.max(np.abs(new - e)) < tol
+            e = new
+            if done:
+                return e, it
+        if on_fail == "raise":
+            raise G.NotConverged("max_iter")
+        return e, max_iter
+
+    monkeypatch.setattr(G, "evgw0", ev)
+    _fails(P.test_evgw0_stops_when_a_state_crosses_the_fermi_level)

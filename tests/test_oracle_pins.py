@@ -731,3 +731,20 @@ def test_evgw0_converges_to_a_fixed_point():
 def test_evgw0_rejects_a_core_only_system(tiny_mol):
     with pytest.raises(ValueError):
         G.evgw0(G.System.from_molecule(tiny_mol))
+
+
+def test_evgw0_stops_when_a_state_crosses_the_fermi_level():
+    # reading of the iteration: an iterate whose occupied QP energy reaches the midpoint of the QP HOMO
+    # and LUMO ends the scheme without convergence (the occupations of G would change). A v^xc 1 Ha below
+    # Sigma^x for the HOMO lifts its first iterate above the LUMO: the scheme returns that iterate after
+    # one step, or raises NotConverged
+    s0 = _all_state_system()
+    v = s0.sigma_x().copy()
+    v[s0.n_occ - 1] -= 1.0
+    s = G.System(s0.eps, s0.n_occ, s0.core_idx, s0.o_ov, s0.o_core, s0.eta, n_im=s0.n_im, vxc=v)
+    e1 = s.eps + s.hedin_shift()
+    assert e1[s.n_occ - 1] > e1[s.n_occ]
+    e, it = G.evgw0(s)
+    assert it == 1 and np.max(np.abs(e - e1)) < 1e-12
+    with pytest.raises(G.NotConverged):
+        G.evgw0(s, on_fail="raise")
